@@ -1,0 +1,161 @@
+/* lcp_gb300.h -- C ABI of the GB300 (sm_103a) collision-resolution library.
+ *
+ * The library solves, per time step, the linear complementarity problem
+ *     0 <= x  perp  A x + b >= 0,     A = D^T M D,   b = (Phi + dt D^T U_nc) / dt
+ * of the paper's Sec. 3, Eqs. (LCP) and (defAandb), for M rigid spheres in
+ * Stokes flow.  x holds the normal contact-force magnitudes of the n contacts,
+ * D maps them to per-body forces/torques, and M is the mobility of Sec. 2
+ * (U = M F), applied as P M_stk P^T (Fig. 1): a second-kind boundary-integral
+ * solve by GMRES whose every iteration is an O(N^2) stresslet sum over all
+ * surface nodes.  The solvers are Mono-PQN (Algorithm 1, with Algorithm 2 and
+ * the weighted prox of Proposition 1) and Bi-PQN (Algorithm 4) with a
+ * Rotne-Prager-Yamakawa low-fidelity operator.
+ *
+ * Conventions (all entry points):
+ *  - Plain C types only.  Host pointers are read/written synchronously;
+ *    "_dev" variants take device pointers and run on the context's stream.
+ *  - Per-body vectors are [M][6] = (Fx, Fy, Fz, Tx, Ty, Tz) for forces and
+ *    (Ux, Uy, Uz, Wx, Wy, Wz) for velocities (Sec. 2, definition of U and F).
+ *  - Node vectors are [N][3] with N = M * n_theta * n_phi, body-major; inside
+ *    a body node q = j * n_phi + k (t_j = cos(theta_j) ascending Gauss-Legendre
+ *    node, phi_k = 2 pi k / n_phi).
+ *  - Contacts are in the caller's order, or in lexicographic (i, j) order
+ *    when the library detects them.  x[l] is the force magnitude of contact l.
+ *  - The library owns every device buffer of a context and frees it in
+ *    lcp_destroy.  Caller buffers are never freed or retained.
+ *  - Every entry point returns an lcp_status; nothing aborts or traps.  On
+ *    error, lcp_last_error(ctx) returns a message (thread-local for NULL ctx).
+ */
+#ifndef LCP_GB300_H
+#define LCP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LCP_OK = 0,
+  LCP_ERR_INVALID_ARG = -1,   /* bad size, pointer or option */
+  LCP_ERR_OOM = -2,           /* device allocation failed */
+  LCP_ERR_CUDA = -3,          /* a CUDA call failed; see lcp_last_error */
+  LCP_ERR_NOT_CONVERGED = -4, /* iteration limit hit; outputs hold the best iterate */
+  LCP_ERR_NUMERICAL = -5,     /* NaN/Inf or a breakdown (e.g. non-positive curvature) */
+  LCP_ERR_TIMEOUT = -6,       /* a bounded device wait expired */
+  LCP_ERR_REJECTED = -8       /* admission refused (memory budget) */
+} lcp_status;
+
+enum { LCP_FP64 = 0, LCP_MIXED = 1 };          /* precision of the stresslet sums */
+enum { LCP_MONO_PQN = 0, LCP_BI_PQN = 1 };     /* Algorithm 1 / Algorithm 4 */
+enum { LCP_HIGH = 0, LCP_LOW_RPY = 1 };        /* mobility fidelity */
+
+typedef struct {
+  int n_theta, n_phi;       /* node grid per sphere; n_phi must be even */
+  double radius;            /* hydrodynamic radius a of the boundary-integral surfaces */
+  double contact_radius;    /* steric radius: gap_l = |c_j - c_i| - 2 contact_radius */
+  double viscosity;         /* mu */
+  double dt;                /* time step of Eq. (dvi) */
+  double delta;             /* collisional threshold of Eq. (collisional-set) */
+  int precision;            /* LCP_FP64 or LCP_MIXED */
+  double gmres_tol;         /* relative residual of each mobility solve */
+  int gmres_restart;        /* Krylov basis size m of GMRES(m) */
+  int gmres_maxit;          /* total GMRES iterations per solve */
+  double inner_tol;         /* LCP_MIXED: relative tolerance of each FP32-operator GMRES */
+  int ir_maxit;             /* LCP_MIXED: maximum refinement sweeps */
+  int kmax;                 /* PQN outer iteration limit */
+  int kmax_inner;           /* Bi-PQN subproblem / low-fidelity init iteration limit */
+  int memory;               /* quasi-Newton pairs kept (FIFO beyond) */
+  int ssn_maxit;            /* semi-smooth Newton iterations per prox */
+  double forcing;           /* Bi-PQN subproblem tolerance = max(0.1 tol, forcing * kkt) */
+  void* cuda_stream;        /* cudaStream_t to run on; NULL = the legacy default stream */
+} lcp_config;
+
+typedef struct {
+  int i, j;                 /* bodies, i < j */
+  double normal[3];         /* (c_j - c_i) / |c_j - c_i| */
+  double gap;               /* |c_j - c_i| - 2 contact_radius */
+} lcp_contact;
+
+typedef struct {
+  int converged;            /* 1 if ||min(x, A x + b)||_2 <= tol */
+  int iterations;           /* outer PQN iterations */
+  int hi_mvps, lo_mvps;     /* high-/low-fidelity matrix-vector products with A */
+  int inner_iterations;     /* Bi-PQN: subproblem iterations, summed */
+  int gmres_iterations;     /* GMRES iterations of all high-fidelity solves, summed */
+  int fp64_applies;         /* FP64 stresslet applications */
+  int fp32_applies;         /* FP32 stresslet applications */
+  double kkt_abs;           /* ||min(x, g)||_2 with the final gradient g */
+  double kkt_dot;           /* <x, g> (the test of Algorithms 1 and 4) */
+  double e_mvps;            /* hi + lo * (mean lo time / mean hi time), Sec. 6 */
+  double hi_mvp_seconds;    /* mean wall time of one high-fidelity MVP */
+  double lo_mvp_seconds;    /* mean wall time of one low-fidelity MVP */
+  double seconds;           /* wall time of the solve */
+} lcp_stats;
+
+typedef struct lcp_ctx lcp_ctx;   /* opaque, library-owned */
+
+/* Fills cfg with defaults (grid 9 x 18, a = 1, contact radius 1.25, mu = 1,
+ * dt = 0.01, delta = 0.05, FP64, GMRES tol 1e-12, restart 60, ...). */
+void lcp_default_config(lcp_config* cfg);
+
+/* Builds a context for one configuration (Sec. 3, Eqs. collisional-set, LCP,
+ * defAandb).  centers: host [M*3].  axes: host [M*3] unit Janus axes, or NULL
+ * for no active slip.  contacts: n_contacts caller contacts (host), or NULL to
+ * detect every pair with gap <= delta on the GPU (lexicographic order).
+ * Computes the quadrature, the contact matrix D (CSR both ways), the
+ * non-collisional velocity U_nc (one slip-driven mobility solve) and
+ * b = gap / dt + D^T U_nc.  Allocates all device state; *out receives the
+ * context (NULL on failure, message via lcp_last_error(NULL)). */
+int lcp_setup(const lcp_config* cfg, int n_bodies, const double* centers, const double* axes,
+              int n_contacts, const lcp_contact* contacts, lcp_ctx** out);
+
+/* Frees every device buffer of the context.  NULL is ignored. */
+void lcp_destroy(lcp_ctx* ctx);
+
+/* Message of the last failure on ctx (or of the calling thread's last failed
+ * lcp_setup when ctx is NULL).  Valid until the next call on ctx. */
+const char* lcp_last_error(const lcp_ctx* ctx);
+
+/* Sizes: bodies M, nodes N, contacts n. */
+int lcp_sizes(const lcp_ctx* ctx, int* n_bodies, int* n_nodes, int* n_contacts);
+
+/* Copies the contacts (host [n]), b (host [n]) or U_nc (host [M*6]). */
+int lcp_get_contacts(lcp_ctx* ctx, lcp_contact* out);
+int lcp_get_b(lcp_ctx* ctx, double* b);
+int lcp_get_unc(lcp_ctx* ctx, double* U_nc);
+
+/* U = M F (Sec. 2, Eq. mobility).  FT, UO: host [M*6].  include_slip adds the
+ * Janus slip-driven part (U_nc for FT = 0).  fidelity: LCP_HIGH (boundary
+ * integral, GMRES, precision of the context) or LCP_LOW_RPY (pairwise RPY). */
+int mobility_apply(lcp_ctx* ctx, const double* FT, double* UO, int include_slip, int fidelity);
+/* Same on device pointers FT [M*6], UO [M*6], on the context's stream. */
+int mobility_apply_dev(lcp_ctx* ctx, const double* FT, double* UO, int include_slip, int fidelity);
+
+/* One matrix-vector product A[x] = D^T M D x (Sec. 3, Eq. defAandb) of the
+ * given fidelity.  Host x [n], Ax [n]. */
+int lcp_apply_A(lcp_ctx* ctx, const double* x, double* Ax, int fidelity);
+
+/* Solves 0 <= x perp A x + b >= 0 by Mono-PQN (Algorithm 1) or Bi-PQN
+ * (Algorithm 4) to ||min(x, A x + b)||_2 <= tol.  x0: host [n] initial guess
+ * (projected onto x >= 0) or NULL for 0.  x: host [n] result.  st: optional.
+ * Returns LCP_ERR_NOT_CONVERGED (x = last iterate) if kmax is reached. */
+int lcp_solve(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st);
+/* Same with device pointers x0 (or NULL) and x, both [n] FP64. */
+int lcp_solve_dev(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st);
+
+/* Building blocks of the mobility solve, on device pointers and the context's
+ * stream (used by the parity tests):
+ *   lcp_stokes_apply_dev: out = (K + P) phi, phi/out [N*3], precision
+ *     LCP_FP64 or LCP_MIXED (FP32 pair sums, compensated accumulation);
+ *   lcp_stokes_rhs_dev: rhs = s - S[F, T] at the nodes, FT [M*6], rhs [N*3];
+ *   lcp_rigid_velocity_dev: UO = -(rigid coefficients of P phi), UO [M*6]. */
+int lcp_stokes_apply_dev(lcp_ctx* ctx, const double* phi, double* out, int precision);
+int lcp_stokes_rhs_dev(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs);
+int lcp_rigid_velocity_dev(lcp_ctx* ctx, const double* phi, double* UO);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,130 @@
+// Shared device helpers and the internal context of the collision-resolution
+// library.  Everything here is GPU-side infrastructure; the arithmetic of the
+// method lives in the kernels of the other translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lcp_gb300.h"
+
+#define LCP_PI 3.14159265358979323846
+
+// ------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum in a fixed order (deterministic).  `red` must hold
+// blockDim.x / 32 doubles.  Every thread receives the result.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[0] = t;
+  }
+  __syncthreads();
+  t = red[0];
+  __syncthreads();
+  return t;
+}
+
+// ------------------------------------------------------------ host side
+struct GmresWork;
+
+struct PqnDev {   // quasi-Newton state of one PQN run, all device pointers
+  int n, rmax;
+  double *x, *g, *p, *Ap, *xt, *xh, *extra, *lop;   // [n]
+  double *S, *Y, *U, *V;                             // [rmax][n]
+  double *UU, *UV, *VV;                              // [rmax][rmax]
+  int* r;                                            // pairs held
+  double* scal;                                      // scalar slots (see pqn.cu)
+};
+
+struct lcp_ctx {
+  lcp_config cfg;
+  cudaStream_t stream = nullptr;
+  int M = 0, ns = 0, N = 0, n = 0;
+  // geometry
+  double* tmpl64 = nullptr;   // [ns][8]: xi(3), wn(3) = -(3/4pi) w n, w, 0
+  float* tmpl32 = nullptr;    // SoA [6][ns]: xi x,y,z, wn x,y,z
+  double* ginv = nullptr;     // [36] inverse Gram matrix of the rigid modes
+  double* centers = nullptr;  // [M][3]
+  float* centers32 = nullptr; // [M][8]: hi(3), pad, lo(3), pad
+  double* axes = nullptr;     // [M][3] or null
+  // contacts
+  int *ci = nullptr, *cj = nullptr;
+  double *cnrm = nullptr, *gap = nullptr, *b = nullptr;
+  int *bc_ptr = nullptr, *bc_idx = nullptr;
+  double* U_nc = nullptr;     // [M][6]
+  // mobility solve workspace
+  int m = 0, splits = 1;
+  double *V = nullptr, *H = nullptr;  // Krylov basis [(m+1)][3N], Hessenberg etc.
+  double *phi = nullptr, *rhs = nullptr, *res = nullptr, *wv = nullptr, *dphi = nullptr;
+  float* phi32 = nullptr;
+  double* partial = nullptr;  // [splits][N][3]
+  double* coef = nullptr;     // [M][6]
+  double* dotp = nullptr;     // dot-product partials
+  double* FT = nullptr;       // [M][6]
+  double* UO = nullptr;       // [M][6]
+  double* dscal = nullptr;    // device scalars
+  double* hscal = nullptr;    // pinned host mirror
+  int dot_blocks = 0;
+  // PQN
+  PqnDev pq_outer{}, pq_inner{};
+  double *Uh = nullptr, *Vh = nullptr;   // Bi-PQN high-fidelity corrections [kmax][n]
+  int nh = 0;
+  double *tmp_n = nullptr, *tmp_n2 = nullptr, *tmp_n3 = nullptr;
+  std::vector<void*> allocs;
+  std::string err;
+  // counters of the current solve
+  int c_gmres = 0, c_fp64 = 0, c_fp32 = 0;
+};
+
+#define LCP_CUDA(call)                                                            \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);              \
+      return LCP_ERR_CUDA;                                                        \
+    }                                                                             \
+  } while (0)
+
+#define LCP_TRY(expr)                  \
+  do {                                 \
+    int s_ = (expr);                   \
+    if (s_ != LCP_OK) return s_;       \
+  } while (0)
+
+// Internal launch helpers implemented in the .cu files.
+int geometry_build(lcp_ctx* ctx);
+int contacts_detect(lcp_ctx* ctx, int* n_out);
+int contacts_upload(lcp_ctx* ctx, int n, const lcp_contact* c);
+int contacts_csr(lcp_ctx* ctx);
+int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision);
+int stokes_rhs(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs);
+int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef);
+int mobility_solve(lcp_ctx* ctx, const double* FT, int include_slip, double* UO);
+int scatter_D(lcp_ctx* ctx, const double* x, double* FT);
+int gather_Dt(lcp_ctx* ctx, const double* UO, double* out, const double* add);
+int rpy_apply(lcp_ctx* ctx, const double* FT, double* UO);
+int mvp_high(lcp_ctx* ctx, const double* x, double* Ax);
+int mvp_low(lcp_ctx* ctx, const double* x, double* Ax);
+int pqn_alloc(lcp_ctx* ctx, PqnDev* pq, int n, int rmax);
+int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st);
+void* ctx_alloc(lcp_ctx* ctx, size_t bytes);

@@ -1,0 +1,400 @@
+// Mobility solves: restarted GMRES with FP64 Arnoldi (classical Gram-Schmidt
+// applied twice) on (K + P) phi = rhs, in FP64 or as GMRES iterative
+// refinement with FP32 stresslet sums (the paper fixes GMRES with tolerance
+// eps_gmres for its traction BIE, Sec. 5.1 and Sec. 6); the contact matrix D
+// and its transpose (Sec. 3); and the Rotne-Prager-Yamakawa low-fidelity
+// mobility.
+#include <cmath>
+
+#include "common.cuh"
+
+int stokes_velocity(lcp_ctx* ctx, const double* phi, double* UO);
+
+namespace {
+constexpr int DOT_THREADS = 256;
+}
+
+// partial[k * G + b] = sum over block b's chunk of V[k][i] * w[i]; the last
+// block to finish reduces the partials in block order into out[k].
+__global__ void __launch_bounds__(DOT_THREADS)
+k_dots(int L, int nv, const double* __restrict__ V, size_t ldv, const double* __restrict__ w,
+       double* __restrict__ partial, double* __restrict__ out, unsigned int* __restrict__ counter) {
+  __shared__ double red[DOT_THREADS / 32];
+  __shared__ bool last;
+  const int G = gridDim.x;
+  const int chunk = (L + G - 1) / G;
+  const int i0 = blockIdx.x * chunk, i1 = min(L, i0 + chunk);
+  for (int k = 0; k < nv; k++) {
+    const double* v = V + (size_t)k * ldv;
+    double s = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += v[i] * w[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) partial[(size_t)k * G + blockIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(G - 1));
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < G; b++) s += ((volatile double*)partial)[(size_t)k * G + b];
+    out[k] = s;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// w -= sum_k h[k] V[k]
+__global__ void k_update(int L, int nv, const double* __restrict__ V, size_t ldv, const double* __restrict__ h,
+                         double* __restrict__ w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  double s = w[i];
+  for (int k = 0; k < nv; k++) s -= h[k] * V[(size_t)k * ldv + i];
+  w[i] = s;
+}
+
+// y = a * x (+ y if accumulate)
+__global__ void k_scale(int L, const double* __restrict__ x, const double* __restrict__ a, double* __restrict__ y,
+                        int invert, int accumulate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  const double s = invert ? 1.0 / a[0] : a[0];
+  y[i] = accumulate ? y[i] + s * x[i] : s * x[i];
+}
+
+__global__ void k_sub(int L, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L) c[i] = a[i] - b[i];
+}
+__global__ void k_add(int L, const double* __restrict__ a, double* __restrict__ c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L) c[i] += a[i];
+}
+
+// GMRES bookkeeping on the device (one thread).  Work layout (doubles):
+// H[(m+1) * m] column j at H + j * (m+1); cs[m]; sn[m]; g[m+1]; y[m];
+// h1[m+1]; h2[m+1]; hn[1]; inv[1]; beta[1].
+struct GW {
+  double *H, *cs, *sn, *g, *y, *h1, *h2, *hn, *beta;
+};
+__device__ GW gw_map(double* base, int m) {
+  GW w;
+  w.H = base;
+  w.cs = w.H + (size_t)(m + 1) * m;
+  w.sn = w.cs + m;
+  w.g = w.sn + m;
+  w.y = w.g + (m + 1);
+  w.h1 = w.y + m;
+  w.h2 = w.h1 + (m + 1);
+  w.hn = w.h2 + (m + 1);
+  w.beta = w.hn + 1;
+  return w;
+}
+
+// Start of a cycle: beta = sqrt(hn); g = (beta, 0, ...); status[0] = beta.
+__global__ void k_gmres_start(double* base, int m, double* status) {
+  GW w = gw_map(base, m);
+  const double beta = sqrt(w.hn[0]);
+  w.beta[0] = beta;
+  for (int k = 0; k <= m; k++) w.g[k] = 0.0;
+  w.g[0] = beta;
+  status[0] = beta;
+}
+
+// Column j of H from the two Gram-Schmidt passes, Givens rotations, new
+// residual estimate |g[j+1]| into status[0]; hn becomes 1/H[j+1][j].
+__global__ void k_gmres_column(double* base, int m, int j, double* status) {
+  GW w = gw_map(base, m);
+  double* Hj = w.H + (size_t)j * (m + 1);
+  for (int k = 0; k <= j; k++) Hj[k] = w.h1[k] + w.h2[k];
+  const double hnext = sqrt(w.hn[0]);
+  Hj[j + 1] = hnext;
+  for (int k = 0; k < j; k++) {
+    const double a = Hj[k], b = Hj[k + 1];
+    Hj[k] = w.cs[k] * a + w.sn[k] * b;
+    Hj[k + 1] = -w.sn[k] * a + w.cs[k] * b;
+  }
+  const double a = Hj[j], b = Hj[j + 1];
+  const double r = sqrt(a * a + b * b);
+  w.cs[j] = a / r;
+  w.sn[j] = b / r;
+  Hj[j] = r;
+  Hj[j + 1] = 0.0;
+  w.g[j + 1] = -w.sn[j] * w.g[j];
+  w.g[j] = w.cs[j] * w.g[j];
+  w.hn[0] = hnext > 0.0 ? 1.0 / hnext : 0.0;
+  status[0] = fabs(w.g[j + 1]);
+  status[1] = hnext;
+}
+
+// Back substitution H y = g for the first k columns.
+__global__ void k_gmres_solve(double* base, int m, int k) {
+  GW w = gw_map(base, m);
+  for (int r = k - 1; r >= 0; r--) {
+    double s = w.g[r];
+    for (int c = r + 1; c < k; c++) s -= w.H[(size_t)c * (m + 1) + r] * w.y[c];
+    w.y[r] = s / w.H[(size_t)r * (m + 1) + r];
+  }
+}
+
+// phi += sum_k y[k] V[k]
+__global__ void k_gmres_update(int L, int k, const double* __restrict__ V, size_t ldv, const double* __restrict__ y,
+                               double* __restrict__ phi) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  double s = phi[i];
+  for (int c = 0; c < k; c++) s += y[c] * V[(size_t)c * ldv + i];
+  phi[i] = s;
+}
+
+// ----------------------------------------------------------- D and D^T
+// F_i = sum over contacts l of body i of (-n_l or +n_l) x_l; torques 0 (spheres).
+__global__ void k_scatter(int M, const int* __restrict__ ptr, const int* __restrict__ idx,
+                          const double* __restrict__ cnrm, const double* __restrict__ x, double* __restrict__ FT) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+  for (int e = ptr[i]; e < ptr[i + 1]; e++) {
+    const int code = idx[e];
+    const int l = code >> 1;
+    const double s = (code & 1) ? x[l] : -x[l];
+    f0 += s * cnrm[3 * l];
+    f1 += s * cnrm[3 * l + 1];
+    f2 += s * cnrm[3 * l + 2];
+  }
+  double* o = FT + 6 * i;
+  o[0] = f0; o[1] = f1; o[2] = f2; o[3] = 0.0; o[4] = 0.0; o[5] = 0.0;
+}
+
+// (D^T U)_l = n_l . (U_j - U_i) (+ add_l)
+__global__ void k_gather(int n, const int* __restrict__ ci, const int* __restrict__ cj,
+                         const double* __restrict__ cnrm, const double* __restrict__ UO,
+                         const double* __restrict__ add, double* __restrict__ out) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  const double* ui = UO + 6 * ci[l];
+  const double* uj = UO + 6 * cj[l];
+  double v = cnrm[3 * l] * (uj[0] - ui[0]) + cnrm[3 * l + 1] * (uj[1] - ui[1]) + cnrm[3 * l + 2] * (uj[2] - ui[2]);
+  if (add) v += add[l];
+  out[l] = v;
+}
+
+// ----------------------------------------------------------- RPY
+// One warp per target body; lanes stride over source bodies; fixed reduction.
+__global__ void k_rpy(int M, double a, double mu, const double* __restrict__ c, const double* __restrict__ FT,
+                      double* __restrict__ UO) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= M) return;
+  double u[6] = {0, 0, 0, 0, 0, 0};
+  const double k8 = 1.0 / (8.0 * LCP_PI * mu);
+  for (int j = lane; j < M; j += 32) {
+    const double* f = FT + 6 * j;
+    if (j == i) {
+      const double st = 1.0 / (6.0 * LCP_PI * mu * a), sr = 1.0 / (8.0 * LCP_PI * mu * a * a * a);
+      for (int d = 0; d < 3; d++) { u[d] += st * f[d]; u[3 + d] += sr * f[3 + d]; }
+      continue;
+    }
+    const double rx = c[3 * i] - c[3 * j], ry = c[3 * i + 1] - c[3 * j + 1], rz = c[3 * i + 2] - c[3 * j + 2];
+    const double r = sqrt(rx * rx + ry * ry + rz * rz);
+    const double hx = rx / r, hy = ry / r, hz = rz / r;
+    const double a2r2 = a * a / (r * r);
+    const double ct = k8 / r * (1.0 + 2.0 * a2r2 / 3.0), cp = k8 / r * (1.0 - 2.0 * a2r2);
+    const double hF = hx * f[0] + hy * f[1] + hz * f[2];
+    u[0] += ct * f[0] + cp * hF * hx;
+    u[1] += ct * f[1] + cp * hF * hy;
+    u[2] += ct * f[2] + cp * hF * hz;
+    const double r3 = k8 / (r * r * r);
+    // U_i += (T_j x r) / (8 pi mu r^3) ; Omega_i += (F_j x r) / (8 pi mu r^3)
+    u[0] += r3 * (f[4] * rz - f[5] * ry);
+    u[1] += r3 * (f[5] * rx - f[3] * rz);
+    u[2] += r3 * (f[3] * ry - f[4] * rx);
+    u[3] += r3 * (f[1] * rz - f[2] * ry);
+    u[4] += r3 * (f[2] * rx - f[0] * rz);
+    u[5] += r3 * (f[0] * ry - f[1] * rx);
+    // Omega_i += (3 h h^T - I) T_j / (16 pi mu r^3)
+    const double hT = hx * f[3] + hy * f[4] + hz * f[5];
+    const double rr = 0.5 * r3;
+    u[3] += rr * (3.0 * hT * hx - f[3]);
+    u[4] += rr * (3.0 * hT * hy - f[4]);
+    u[5] += rr * (3.0 * hT * hz - f[5]);
+  }
+#pragma unroll
+  for (int d = 0; d < 6; d++) u[d] = warp_sum(u[d]);
+  if (lane == 0)
+    for (int d = 0; d < 6; d++) UO[6 * i + d] = u[d];
+}
+
+// ------------------------------------------------------------------ host side
+static int blocks_for(int L, int t) { return (L + t - 1) / t; }
+
+static int dots(lcp_ctx* ctx, int L, int nv, const double* V, size_t ldv, const double* w, double* out) {
+  k_dots<<<ctx->dot_blocks, DOT_THREADS, 0, ctx->stream>>>(L, nv, V, ldv, w, ctx->dotp, out,
+                                                            (unsigned int*)(ctx->dscal + 60));
+  LCP_CUDA(cudaGetLastError());
+  return LCP_OK;
+}
+
+static int read_status(lcp_ctx* ctx, double* vals, int count) {
+  LCP_CUDA(cudaMemcpyAsync(ctx->hscal, ctx->dscal, sizeof(double) * count, cudaMemcpyDeviceToHost, ctx->stream));
+  LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < count; k++) vals[k] = ctx->hscal[k];
+  return LCP_OK;
+}
+
+// Restarted GMRES(m) on (K + P) phi = rhs with operator precision `prec`.
+// phi holds the initial guess (zero_init: assume phi = 0 and skip the first
+// residual apply).  Stops when the residual estimate <= tol_abs or after
+// maxit iterations.  Returns the iterations used in *its, the last residual
+// estimate in *res_out.
+static int gmres(lcp_ctx* ctx, const double* rhs, double* phi, int zero_init, double tol_abs, int prec,
+                 int maxit, int* its, double* res_out) {
+  const int L = 3 * ctx->N, m = ctx->m;
+  const size_t ldv = (size_t)L;
+  double* base = ctx->H;
+  // offsets of the scalar slots inside the work array (host mirror of gw_map)
+  const size_t oH = 0, ocs = oH + (size_t)(m + 1) * m, osn = ocs + m, og = osn + m, oy = og + (m + 1),
+               oh1 = oy + m, oh2 = oh1 + (m + 1), ohn = oh2 + (m + 1);
+  double* h1 = base + oh1;
+  double* h2 = base + oh2;
+  double* hn = base + ohn;
+  double* y = base + oy;
+  (void)og;
+  int total = 0;
+  double res = 0.0;
+  bool first = true;
+  const int T = 256;
+  for (;;) {
+    // r = rhs - A phi into V[0]
+    if (first && zero_init) {
+      LCP_CUDA(cudaMemcpyAsync(ctx->V, rhs, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+      LCP_TRY(stokes_apply(ctx, phi, ctx->wv, prec));
+      k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->wv, ctx->V);
+    }
+    first = false;
+    LCP_TRY(dots(ctx, L, 1, ctx->V, ldv, ctx->V, hn));
+    k_gmres_start<<<1, 1, 0, ctx->stream>>>(base, m, ctx->dscal);
+    double st[2];
+    LCP_TRY(read_status(ctx, st, 1));
+    res = st[0];
+    if (!(res == res)) { ctx->err = "GMRES: NaN residual"; return LCP_ERR_NUMERICAL; }
+    if (res <= tol_abs || total >= maxit) break;
+    k_scale<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, ctx->V, base + ohn + 1, ctx->V, 1, 0);  // V0 /= beta
+    int j = 0;
+    for (; j < m; j++) {
+      double* vj = ctx->V + (size_t)j * ldv;
+      double* vn = ctx->V + (size_t)(j + 1) * ldv;
+      LCP_TRY(stokes_apply(ctx, vj, vn, prec));
+      total++;
+      LCP_TRY(dots(ctx, L, j + 1, ctx->V, ldv, vn, h1));
+      k_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j + 1, ctx->V, ldv, h1, vn);
+      LCP_TRY(dots(ctx, L, j + 1, ctx->V, ldv, vn, h2));
+      k_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j + 1, ctx->V, ldv, h2, vn);
+      LCP_TRY(dots(ctx, L, 1, vn, ldv, vn, hn));
+      k_gmres_column<<<1, 1, 0, ctx->stream>>>(base, m, j, ctx->dscal);
+      k_scale<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, vn, hn, vn, 0, 0);   // v_{j+1} = w / H[j+1][j]
+      LCP_TRY(read_status(ctx, st, 2));
+      res = st[0];
+      if (!(res == res)) { ctx->err = "GMRES: NaN residual"; return LCP_ERR_NUMERICAL; }
+      if (res <= tol_abs || total >= maxit || st[1] == 0.0) { j++; break; }
+    }
+    k_gmres_solve<<<1, 1, 0, ctx->stream>>>(base, m, j);
+    k_gmres_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j, ctx->V, ldv, y, phi);
+    LCP_CUDA(cudaGetLastError());
+    if (res <= tol_abs || total >= maxit) break;
+  }
+  *its = total;
+  *res_out = res;
+  return LCP_OK;
+}
+
+static int norm2(lcp_ctx* ctx, const double* v, int L, double* out) {
+  double* slot = ctx->dscal + 8;
+  LCP_TRY(dots(ctx, L, 1, v, (size_t)L, v, slot));
+  LCP_CUDA(cudaMemcpyAsync(ctx->hscal + 8, slot, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+  *out = std::sqrt(ctx->hscal[8]);
+  return LCP_OK;
+}
+
+// Solve (K + P) phi = rhs to ||rhs - (K + P) phi|| <= gmres_tol ||rhs||.
+// FP64: GMRES on the FP64 operator.  MIXED: iterative refinement, each sweep
+// a GMRES on the FP32 operator for the FP64 residual, to inner_tol relative.
+int density_solve(lcp_ctx* ctx, const double* rhs, double* phi) {
+  const int L = 3 * ctx->N;
+  const int T = 256;
+  double bn = 0.0;
+  LCP_TRY(norm2(ctx, rhs, L, &bn));
+  LCP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * L, ctx->stream));
+  if (bn == 0.0) return LCP_OK;
+  const double tol = ctx->cfg.gmres_tol * bn;
+  int its = 0;
+  double res = 0.0;
+  if (ctx->cfg.precision == LCP_FP64) {
+    LCP_TRY(gmres(ctx, rhs, phi, 1, tol, LCP_FP64, ctx->cfg.gmres_maxit, &its, &res));
+    ctx->c_gmres += its;
+    if (res > tol) {
+      ctx->err = "GMRES did not reach its tolerance";
+      return LCP_ERR_NOT_CONVERGED;
+    }
+    return LCP_OK;
+  }
+  // mixed precision: phi = 0, r = rhs
+  LCP_CUDA(cudaMemcpyAsync(ctx->res, rhs, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+  double rn = bn;
+  for (int sweep = 0; sweep < ctx->cfg.ir_maxit; sweep++) {
+    LCP_CUDA(cudaMemsetAsync(ctx->dphi, 0, sizeof(double) * L, ctx->stream));
+    const double tin = std::max(ctx->cfg.inner_tol * rn, 0.5 * tol);
+    LCP_TRY(gmres(ctx, ctx->res, ctx->dphi, 1, tin, LCP_MIXED, ctx->cfg.gmres_maxit, &its, &res));
+    ctx->c_gmres += its;
+    k_add<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, ctx->dphi, phi);
+    LCP_TRY(stokes_apply(ctx, phi, ctx->wv, LCP_FP64));
+    k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->wv, ctx->res);
+    LCP_TRY(norm2(ctx, ctx->res, L, &rn));
+    if (!(rn == rn)) { ctx->err = "refinement: NaN residual"; return LCP_ERR_NUMERICAL; }
+    if (rn <= tol) return LCP_OK;
+  }
+  ctx->err = "iterative refinement did not reach the GMRES tolerance";
+  return LCP_ERR_NOT_CONVERGED;
+}
+
+int mobility_solve(lcp_ctx* ctx, const double* FT, int include_slip, double* UO) {
+  LCP_TRY(stokes_rhs(ctx, FT, include_slip, ctx->rhs));
+  LCP_TRY(density_solve(ctx, ctx->rhs, ctx->phi));
+  return stokes_velocity(ctx, ctx->phi, UO);
+}
+
+int scatter_D(lcp_ctx* ctx, const double* x, double* FT) {
+  k_scatter<<<blocks_for(ctx->M, 128), 128, 0, ctx->stream>>>(ctx->M, ctx->bc_ptr, ctx->bc_idx, ctx->cnrm, x, FT);
+  LCP_CUDA(cudaGetLastError());
+  return LCP_OK;
+}
+
+int gather_Dt(lcp_ctx* ctx, const double* UO, double* out, const double* add) {
+  if (ctx->n == 0) return LCP_OK;
+  k_gather<<<blocks_for(ctx->n, 128), 128, 0, ctx->stream>>>(ctx->n, ctx->ci, ctx->cj, ctx->cnrm, UO, add, out);
+  LCP_CUDA(cudaGetLastError());
+  return LCP_OK;
+}
+
+int rpy_apply(lcp_ctx* ctx, const double* FT, double* UO) {
+  k_rpy<<<blocks_for(ctx->M * 32, 128), 128, 0, ctx->stream>>>(ctx->M, ctx->cfg.radius, ctx->cfg.viscosity,
+                                                                 ctx->centers, FT, UO);
+  LCP_CUDA(cudaGetLastError());
+  return LCP_OK;
+}
+
+int mvp_high(lcp_ctx* ctx, const double* x, double* Ax) {
+  LCP_TRY(scatter_D(ctx, x, ctx->FT));
+  LCP_TRY(mobility_solve(ctx, ctx->FT, 0, ctx->UO));
+  return gather_Dt(ctx, ctx->UO, Ax, nullptr);
+}
+
+int mvp_low(lcp_ctx* ctx, const double* x, double* Ax) {
+  LCP_TRY(scatter_D(ctx, x, ctx->FT));
+  LCP_TRY(rpy_apply(ctx, ctx->FT, ctx->UO));
+  return gather_Dt(ctx, ctx->UO, Ax, nullptr);
+}

@@ -1,0 +1,421 @@
+// Boundary-integral operator kernels: the stresslet pair sum K (the hot path),
+// the rigid projector P, the Stokeslet/rotlet right-hand side and the rigid
+// velocities.  Sec. 2 / Fig. 1 of the paper: M ~ P M_stk P^T, where every
+// application of M_stk is a GMRES solve whose iterations apply K + P.
+//
+//   (K phi)_p = sum_{q != p} w_q T(x_p - x_q, n_q)(phi_q - phi_p),
+//   T(r, n) v = -(3 / 4 pi) r (r . n)(r . v) / |r|^5.
+//
+// Layout: node vectors [N][3] FP64, body-major.  All spheres share one
+// quadrature template, so a source tile is one body: the template (xi, w n)
+// stays in shared memory for the whole kernel and only the density of the
+// source body is staged per tile.  Positions are body-relative,
+// r = ((c_i - c_j) + xi_p) - xi_q with c_i - c_j formed from hi/lo parts,
+// which keeps FP32 differences accurate for nodes of touching spheres.
+#include "common.cuh"
+
+namespace {
+
+constexpr int PAIR_THREADS = 256;
+constexpr int PAIR_CHUNK = 8;     // source bodies staged per shared-memory tile
+constexpr float EPS32 = 1e-30f;   // r = 0 only for q = p; then rn = rd = 0 and the term is 0
+constexpr double EPS64 = 1e-300;
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Two sources (packed in the halves of float2 operands) against one target.
+__device__ __forceinline__ void pair2(const float2 ex, const float2 ey, const float2 ez,
+                                      const float2 nfx, const float2 nfy, const float2 nfz,
+                                      const float2 nxq, const float2 nyq, const float2 nzq,
+                                      const float2 wx, const float2 wy, const float2 wz,
+                                      const float2 fx, const float2 fy, const float2 fz,
+                                      float2& ax, float2& ay, float2& az) {
+  const float2 eps = make_float2(EPS32, EPS32);
+  const float2 rx = __fadd2_rn(ex, nxq);
+  const float2 ry = __fadd2_rn(ey, nyq);
+  const float2 rz = __fadd2_rn(ez, nzq);
+  float2 r2 = __ffma2_rn(rx, rx, eps);
+  r2 = __ffma2_rn(ry, ry, r2);
+  r2 = __ffma2_rn(rz, rz, r2);
+  const float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+  const float2 i2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+  float2 rn = __fmul2_rn(rx, wx);
+  rn = __ffma2_rn(ry, wy, rn);
+  rn = __ffma2_rn(rz, wz, rn);
+  const float2 dx = __fadd2_rn(fx, nfx);
+  const float2 dy = __fadd2_rn(fy, nfy);
+  const float2 dz = __fadd2_rn(fz, nfz);
+  float2 rd = __fmul2_rn(rx, dx);
+  rd = __ffma2_rn(ry, dy, rd);
+  rd = __ffma2_rn(rz, dz, rd);
+  const float2 a = __fmul2_rn(rn, i2);
+  const float2 b = __fmul2_rn(rd, i2);
+  const float2 c = __fmul2_rn(a, b);
+  const float2 s = __fmul2_rn(c, ir);
+  ax = __ffma2_rn(s, rx, ax);
+  ay = __ffma2_rn(s, ry, ay);
+  az = __ffma2_rn(s, rz, az);
+}
+
+}  // namespace
+
+// FP32 stresslet sum.  Grid (target blocks, source splits); one target per
+// thread; sources two at a time in packed FP32x2 arithmetic.  Per-body (tile)
+// sums in FP32, Kahan-compensated FP32 across tiles, written as FP64 partials
+// partial[split][p][3].  ns_pad is ns rounded up to 4; padded sources carry
+// zero weight.
+__global__ void __launch_bounds__(PAIR_THREADS)
+k_pair32(int N, int ns, int ns_pad, int M, int bodies_per_split, const float* __restrict__ tmpl32,
+         const float* __restrict__ c32, const float* __restrict__ phi32, double* __restrict__ partial) {
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  float* s_nx = sm;                    // -xi, per template node (padded)
+  float* s_ny = s_nx + ns_pad;
+  float* s_nz = s_ny + ns_pad;
+  float* s_wx = s_nz + ns_pad;         // -(3/4pi) w n
+  float* s_wy = s_wx + ns_pad;
+  float* s_wz = s_wy + ns_pad;
+  float* s_f = s_wz + ns_pad;          // [3][PAIR_CHUNK][ns_pad] source densities
+
+  const int split = blockIdx.y;
+  const int jb0 = split * bodies_per_split;
+  const int jb1 = min(M, jb0 + bodies_per_split);
+  for (int q = threadIdx.x; q < ns_pad; q += blockDim.x) {
+    const bool real = q < ns;
+    s_nx[q] = real ? -tmpl32[q] : -1.0e3f;
+    s_ny[q] = real ? -tmpl32[ns + q] : 0.f;
+    s_nz[q] = real ? -tmpl32[2 * ns + q] : 0.f;
+    s_wx[q] = real ? tmpl32[3 * ns + q] : 0.f;
+    s_wy[q] = real ? tmpl32[4 * ns + q] : 0.f;
+    s_wz[q] = real ? tmpl32[5 * ns + q] : 0.f;
+  }
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pc = p < N ? p : N - 1;
+  const int bi = pc / ns, qi = pc % ns;
+  const float xpx = tmpl32[qi], xpy = tmpl32[ns + qi], xpz = tmpl32[2 * ns + qi];
+  const float4 cih = *reinterpret_cast<const float4*>(c32 + 8 * bi);
+  const float4 cil = *reinterpret_cast<const float4*>(c32 + 8 * bi + 4);
+  const float fpx = phi32[3 * pc], fpy = phi32[3 * pc + 1], fpz = phi32[3 * pc + 2];
+  const float2 nfx = make_float2(-fpx, -fpx), nfy = make_float2(-fpy, -fpy), nfz = make_float2(-fpz, -fpz);
+  float sx = 0.f, sy = 0.f, sz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+
+  for (int jc = jb0; jc < jb1; jc += PAIR_CHUNK) {
+    const int nb = min(PAIR_CHUNK, jb1 - jc);
+    __syncthreads();
+    // stage densities of bodies jc .. jc+nb-1 (contiguous in phi32), SoA in smem
+    const int cnt = nb * ns;
+    const float* src = phi32 + 3 * (size_t)jc * ns;
+    for (int t = threadIdx.x; t < 3 * cnt; t += blockDim.x) {
+      const int node = t / 3, d = t - 3 * node;
+      const int b = node / ns, q = node - b * ns;
+      s_f[(d * PAIR_CHUNK + b) * ns_pad + q] = src[t];
+    }
+    for (int t = threadIdx.x; t < nb * (ns_pad - ns); t += blockDim.x) {
+      const int b = t / (ns_pad - ns), q = ns + t % (ns_pad - ns);
+      for (int d = 0; d < 3; d++) s_f[(d * PAIR_CHUNK + b) * ns_pad + q] = 0.f;
+    }
+    __syncthreads();
+    for (int b = 0; b < nb; b++) {
+      const int j = jc + b;
+      const float4 cjh = *reinterpret_cast<const float4*>(c32 + 8 * j);
+      const float4 cjl = *reinterpret_cast<const float4*>(c32 + 8 * j + 4);
+      const float ex1 = ((cih.x - cjh.x) + (cil.x - cjl.x)) + xpx;
+      const float ey1 = ((cih.y - cjh.y) + (cil.y - cjl.y)) + xpy;
+      const float ez1 = ((cih.z - cjh.z) + (cil.z - cjl.z)) + xpz;
+      const float2 ex = make_float2(ex1, ex1), ey = make_float2(ey1, ey1), ez = make_float2(ez1, ez1);
+      const float* fxb = s_f + (0 * PAIR_CHUNK + b) * ns_pad;
+      const float* fyb = s_f + (1 * PAIR_CHUNK + b) * ns_pad;
+      const float* fzb = s_f + (2 * PAIR_CHUNK + b) * ns_pad;
+      float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+#pragma unroll 1
+      for (int q = 0; q < ns_pad; q += 4) {
+        const float4 X = *reinterpret_cast<const float4*>(s_nx + q);
+        const float4 Y = *reinterpret_cast<const float4*>(s_ny + q);
+        const float4 Z = *reinterpret_cast<const float4*>(s_nz + q);
+        const float4 WX = *reinterpret_cast<const float4*>(s_wx + q);
+        const float4 WY = *reinterpret_cast<const float4*>(s_wy + q);
+        const float4 WZ = *reinterpret_cast<const float4*>(s_wz + q);
+        const float4 FX = *reinterpret_cast<const float4*>(fxb + q);
+        const float4 FY = *reinterpret_cast<const float4*>(fyb + q);
+        const float4 FZ = *reinterpret_cast<const float4*>(fzb + q);
+        pair2(ex, ey, ez, nfx, nfy, nfz, make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+              make_float2(WX.x, WX.y), make_float2(WY.x, WY.y), make_float2(WZ.x, WZ.y),
+              make_float2(FX.x, FX.y), make_float2(FY.x, FY.y), make_float2(FZ.x, FZ.y), ax, ay, az);
+        pair2(ex, ey, ez, nfx, nfy, nfz, make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+              make_float2(WX.z, WX.w), make_float2(WY.z, WY.w), make_float2(WZ.z, WZ.w),
+              make_float2(FX.z, FX.w), make_float2(FY.z, FY.w), make_float2(FZ.z, FZ.w), ax, ay, az);
+      }
+      kahan_add(sx, kx, ax.x + ax.y);
+      kahan_add(sy, ky, ay.x + ay.y);
+      kahan_add(sz, kz, az.x + az.y);
+    }
+  }
+  if (p < N) {
+    double* o = partial + ((size_t)split * N + p) * 3;
+    o[0] = (double)sx - (double)kx;
+    o[1] = (double)sy - (double)ky;
+    o[2] = (double)sz - (double)kz;
+  }
+}
+
+// FP64 stresslet sum, same decomposition, one target per thread.
+__global__ void __launch_bounds__(PAIR_THREADS)
+k_pair64(int N, int ns, int M, int bodies_per_split, const double* __restrict__ tmpl64,
+         const double* __restrict__ centers, const double* __restrict__ phi, double* __restrict__ partial) {
+  extern __shared__ double smd[];
+  double* s_t = smd;                       // [ns][6]: xi(3), wn(3)
+  double* s_f = s_t + 6 * ns;              // [PAIR_CHUNK][ns][3]
+  const int split = blockIdx.y;
+  const int jb0 = split * bodies_per_split;
+  const int jb1 = min(M, jb0 + bodies_per_split);
+  for (int t = threadIdx.x; t < 6 * ns; t += blockDim.x) s_t[t] = tmpl64[8 * (t / 6) + t % 6];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pc = p < N ? p : N - 1;
+  const int bi = pc / ns, qi = pc % ns;
+  const double xpx = tmpl64[8 * qi], xpy = tmpl64[8 * qi + 1], xpz = tmpl64[8 * qi + 2];
+  const double cix = centers[3 * bi], ciy = centers[3 * bi + 1], ciz = centers[3 * bi + 2];
+  const double fpx = phi[3 * pc], fpy = phi[3 * pc + 1], fpz = phi[3 * pc + 2];
+  double ax = 0.0, ay = 0.0, az = 0.0;
+  for (int jc = jb0; jc < jb1; jc += PAIR_CHUNK) {
+    const int nb = min(PAIR_CHUNK, jb1 - jc);
+    __syncthreads();
+    const double* src = phi + 3 * (size_t)jc * ns;
+    for (int t = threadIdx.x; t < 3 * nb * ns; t += blockDim.x) s_f[t] = src[t];
+    __syncthreads();
+    for (int b = 0; b < nb; b++) {
+      const int j = jc + b;
+      const double ex = (cix - centers[3 * j]) + xpx;
+      const double ey = (ciy - centers[3 * j + 1]) + xpy;
+      const double ez = (ciz - centers[3 * j + 2]) + xpz;
+      const double* fb = s_f + 3 * b * ns;
+#pragma unroll 2
+      for (int q = 0; q < ns; q++) {
+        const double* tq = s_t + 6 * q;
+        const double rx = ex - tq[0], ry = ey - tq[1], rz = ez - tq[2];
+        const double r2 = fma(rz, rz, fma(ry, ry, fma(rx, rx, EPS64)));
+        const double ir = rsqrt(r2);
+        const double i2 = ir * ir;
+        const double rn = rx * tq[3] + ry * tq[4] + rz * tq[5];
+        const double dx = fb[3 * q] - fpx, dy = fb[3 * q + 1] - fpy, dz = fb[3 * q + 2] - fpz;
+        const double rd = rx * dx + ry * dy + rz * dz;
+        const double s = ((rn * i2) * (rd * i2)) * ir;
+        ax = fma(s, rx, ax);
+        ay = fma(s, ry, ay);
+        az = fma(s, rz, az);
+      }
+    }
+  }
+  if (p < N) {
+    double* o = partial + ((size_t)split * N + p) * 3;
+    o[0] = ax;
+    o[1] = ay;
+    o[2] = az;
+  }
+}
+
+// Rigid coefficients of P phi per body: c = G^{-1} [sum w phi ; sum w xi x phi].
+// One warp per body; fixed reduction order.
+__global__ void k_moments(int M, int ns, const double* __restrict__ tmpl64, const double* __restrict__ phi,
+                          const double* __restrict__ ginv, double* __restrict__ coef) {
+  const int body = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (body >= M) return;
+  double m[6] = {0, 0, 0, 0, 0, 0};
+  for (int q = lane; q < ns; q += 32) {
+    const double* o = tmpl64 + 8 * q;
+    const double* f = phi + 3 * ((size_t)body * ns + q);
+    const double w = o[6];
+    m[0] += w * f[0];
+    m[1] += w * f[1];
+    m[2] += w * f[2];
+    m[3] += w * (o[1] * f[2] - o[2] * f[1]);
+    m[4] += w * (o[2] * f[0] - o[0] * f[2]);
+    m[5] += w * (o[0] * f[1] - o[1] * f[0]);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; k++) m[k] = warp_sum(m[k]);
+  if (lane == 0) {
+    for (int k = 0; k < 6; k++) {
+      double s = 0.0;
+      for (int l = 0; l < 6; l++) s += ginv[6 * k + l] * m[l];
+      coef[6 * body + k] = s;
+    }
+  }
+}
+
+// out_p = sum over splits of the pair partials + (P phi)_p, (P phi)_p = t_i + w_i x xi_p.
+__global__ void k_finish(int N, int ns, int splits, const double* __restrict__ partial,
+                         const double* __restrict__ coef, const double* __restrict__ tmpl64,
+                         double* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int s = 0; s < splits; s++) {
+    const double* o = partial + ((size_t)s * N + p) * 3;
+    a0 += o[0];
+    a1 += o[1];
+    a2 += o[2];
+  }
+  const int i = p / ns, q = p % ns;
+  const double* c = coef + 6 * i;
+  const double* xi = tmpl64 + 8 * q;
+  a0 += c[0] + (c[4] * xi[2] - c[5] * xi[1]);
+  a1 += c[1] + (c[5] * xi[0] - c[3] * xi[2]);
+  a2 += c[2] + (c[3] * xi[1] - c[4] * xi[0]);
+  out[3 * p] = a0;
+  out[3 * p + 1] = a1;
+  out[3 * p + 2] = a2;
+}
+
+__global__ void k_to_f32(int L, const double* __restrict__ x, float* __restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < L) y[t] = __double2float_rn(x[t]);
+}
+
+// rhs_p = s_p - sum_j [G(x_p - c_j) F_j + R(x_p - c_j) T_j]; Stokeslet
+// G(r) = (I/|r| + r r^T/|r|^3)/(8 pi mu), rotlet R(r) T = (T x r)/(8 pi mu |r|^3),
+// Janus slip s = -(I - n n^T) e on n . e >= 0.
+__global__ void k_rhs(int N, int ns, int M, double a, double mu, const double* __restrict__ tmpl64,
+                      const double* __restrict__ centers, const double* __restrict__ FT,
+                      const double* __restrict__ axes, double* __restrict__ rhs) {
+  __shared__ double s_c[128 * 3];
+  __shared__ double s_ft[128 * 6];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pc = p < N ? p : N - 1;
+  const int i = pc / ns, q = pc % ns;
+  const double* xi = tmpl64 + 8 * q;
+  const double cix = centers[3 * i], ciy = centers[3 * i + 1], ciz = centers[3 * i + 2];
+  double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+  const double k = 1.0 / (8.0 * LCP_PI * mu);
+  for (int j0 = 0; j0 < M; j0 += 128) {
+    const int nb = min(128, M - j0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) s_c[t] = centers[3 * j0 + t];
+    for (int t = threadIdx.x; t < 6 * nb; t += blockDim.x) s_ft[t] = FT[6 * j0 + t];
+    __syncthreads();
+    for (int b = 0; b < nb; b++) {
+      const double rx = (cix - s_c[3 * b]) + xi[0];
+      const double ry = (ciy - s_c[3 * b + 1]) + xi[1];
+      const double rz = (ciz - s_c[3 * b + 2]) + xi[2];
+      const double r2 = rx * rx + ry * ry + rz * rz;
+      const double ir = 1.0 / sqrt(r2);
+      const double ir3 = ir * ir * ir;
+      const double* f = s_ft + 6 * b;
+      const double rF = rx * f[0] + ry * f[1] + rz * f[2];
+      u0 += k * (f[0] * ir + rx * rF * ir3) + k * (f[4] * rz - f[5] * ry) * ir3;
+      u1 += k * (f[1] * ir + ry * rF * ir3) + k * (f[5] * rx - f[3] * rz) * ir3;
+      u2 += k * (f[2] * ir + rz * rF * ir3) + k * (f[3] * ry - f[4] * rx) * ir3;
+    }
+  }
+  if (p >= N) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  if (axes) {
+    const double nx = xi[0] / a, ny = xi[1] / a, nz = xi[2] / a;
+    const double ex = axes[3 * i], ey = axes[3 * i + 1], ez = axes[3 * i + 2];
+    const double ne = nx * ex + ny * ey + nz * ez;
+    if (ne >= 0.0) {
+      s0 = -(ex - ne * nx);
+      s1 = -(ey - ne * ny);
+      s2 = -(ez - ne * nz);
+    }
+  }
+  rhs[3 * p] = s0 - u0;
+  rhs[3 * p + 1] = s1 - u1;
+  rhs[3 * p + 2] = s2 - u2;
+}
+
+__global__ void k_neg(int L, const double* __restrict__ x, double* __restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < L) y[t] = -x[t];
+}
+
+// ------------------------------------------------------------------ host side
+static int pair_splits(const lcp_ctx* ctx) {
+  const int tblocks = (ctx->N + PAIR_THREADS - 1) / PAIR_THREADS;
+  int sm = 152;
+  int want = (4 * sm + tblocks - 1) / tblocks;
+  if (want < 1) want = 1;
+  if (want > ctx->M) want = ctx->M;
+  return want;
+}
+
+int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef) {
+  const int threads = 128;
+  const int blocks = (ctx->M * 32 + threads - 1) / threads;
+  k_moments<<<blocks, threads, 0, ctx->stream>>>(ctx->M, ctx->ns, ctx->tmpl64, phi, ctx->ginv, coef);
+  LCP_CUDA(cudaGetLastError());
+  return LCP_OK;
+}
+
+int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
+  const int N = ctx->N, ns = ctx->ns, M = ctx->M;
+  int splits = pair_splits(ctx);
+  if (splits > ctx->splits) splits = ctx->splits;
+  const int bps = (M + splits - 1) / splits;
+  splits = (M + bps - 1) / bps;
+  dim3 grid((N + PAIR_THREADS - 1) / PAIR_THREADS, splits);
+  LCP_TRY(stokes_coefs(ctx, phi, ctx->coef));
+  if (precision == LCP_MIXED) {
+    k_to_f32<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(3 * N, phi, ctx->phi32);
+    const int ns_pad = (ns + 3) & ~3;
+    const size_t smem = sizeof(float) * (6 * ns_pad + 3 * PAIR_CHUNK * ns_pad);
+    k_pair32<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, ns_pad, M, bps, ctx->tmpl32, ctx->centers32,
+                                                        ctx->phi32, ctx->partial);
+    ctx->c_fp32++;
+  } else {
+    const size_t smem = sizeof(double) * (6 * ns + 3 * PAIR_CHUNK * ns);
+    k_pair64<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, M, bps, ctx->tmpl64, ctx->centers, phi,
+                                                        ctx->partial);
+    ctx->c_fp64++;
+  }
+  k_finish<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ns, splits, ctx->partial, ctx->coef, ctx->tmpl64, out);
+  LCP_CUDA(cudaGetLastError());
+  return LCP_OK;
+}
+
+int stokes_rhs(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs) {
+  const int N = ctx->N;
+  k_rhs<<<(N + 127) / 128, 128, 0, ctx->stream>>>(N, ctx->ns, ctx->M, ctx->cfg.radius, ctx->cfg.viscosity,
+                                                  ctx->tmpl64, ctx->centers, FT,
+                                                  include_slip ? ctx->axes : nullptr, rhs);
+  LCP_CUDA(cudaGetLastError());
+  return LCP_OK;
+}
+
+int stokes_velocity(lcp_ctx* ctx, const double* phi, double* UO) {
+  LCP_TRY(stokes_coefs(ctx, phi, ctx->coef));
+  k_neg<<<(6 * ctx->M + 127) / 128, 128, 0, ctx->stream>>>(6 * ctx->M, ctx->coef, UO);
+  LCP_CUDA(cudaGetLastError());
+  return LCP_OK;
+}
+
+int stokes_max_splits(const lcp_ctx* ctx) { return pair_splits(ctx); }
+
+size_t stokes_pair_smem(int ns, int precision) {
+  const int ns_pad = (ns + 3) & ~3;
+  return precision == LCP_MIXED ? sizeof(float) * (6 * ns_pad + 3 * PAIR_CHUNK * ns_pad)
+                                : sizeof(double) * (6 * ns + 3 * PAIR_CHUNK * ns);
+}
+
+int stokes_configure(lcp_ctx* ctx) {
+  const size_t s32 = stokes_pair_smem(ctx->ns, LCP_MIXED), s64 = stokes_pair_smem(ctx->ns, LCP_FP64);
+  if (s64 > 48 * 1024) LCP_CUDA(cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
+  if (s32 > 48 * 1024) LCP_CUDA(cudaFuncSetAttribute(k_pair32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
+  return LCP_OK;
+}

@@ -1,0 +1,190 @@
+"""Python binding of the C ABI (include/lcp_gb300.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Host arrays are
+NumPy FP64; ``*_dev`` functions take CUDA tensors (or raw device pointers) and
+run on the context's stream.  No computation happens here: a missing or
+failing library raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import (LCP_BI_PQN, LCP_FP64, LCP_HIGH, LCP_LOW_RPY, LCP_MIXED,  # noqa: F401
+                   LCP_MONO_PQN, LCP_OK, LCP_ERR_NOT_CONVERGED, STATUS_NAMES)
+
+
+class LcpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _lib():
+    return _abi.load()
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a, shape=None) -> np.ndarray:
+    out = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        out = out.reshape(shape)
+    return out
+
+
+def _devptr(t) -> int:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"):
+        raise ValueError("device buffers must be contiguous CUDA float64 tensors")
+    return t.data_ptr()
+
+
+def _check(status: int, ctx=None, allow=(LCP_OK,)):
+    if status not in allow:
+        msg = _lib().lcp_last_error(ctx)
+        raise LcpError(status, msg.decode() if msg else "")
+    return status
+
+
+def lcp_default_config(**overrides) -> _abi.lcp_config:
+    cfg = _abi.lcp_config()
+    _lib().lcp_default_config(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def lcp_setup(cfg: _abi.lcp_config, centers, axes=None, contacts=None):
+    """Returns the opaque context handle (an int)."""
+    c = _f64(centers, (-1, 3))
+    M = c.shape[0]
+    a = None if axes is None else _f64(axes, (M, 3))
+    cont = None
+    nc = 0
+    if contacts is not None:
+        nc = len(contacts)
+        cont = (_abi.lcp_contact * max(nc, 1))()
+        for l, (i, j, nrm, gap) in enumerate(contacts):
+            cont[l].i, cont[l].j, cont[l].gap = int(i), int(j), float(gap)
+            for d in range(3):
+                cont[l].normal[d] = float(nrm[d])
+    out = ctypes.c_void_p()
+    st = _lib().lcp_setup(ctypes.byref(cfg), M, _dptr(c), None if a is None else _dptr(a), nc, cont,
+                          ctypes.byref(out))
+    _check(st, None)
+    return out.value
+
+
+def lcp_destroy(ctx) -> None:
+    if ctx:
+        _lib().lcp_destroy(ctx)
+
+
+def lcp_last_error(ctx) -> str:
+    m = _lib().lcp_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def lcp_sizes(ctx):
+    M, N, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib().lcp_sizes(ctx, ctypes.byref(M), ctypes.byref(N), ctypes.byref(n)), ctx)
+    return M.value, N.value, n.value
+
+
+def lcp_get_contacts(ctx):
+    """Returns (pairs [n,2] int, normals [n,3], gaps [n])."""
+    _, _, n = lcp_sizes(ctx)
+    buf = (_abi.lcp_contact * max(n, 1))()
+    _check(_lib().lcp_get_contacts(ctx, buf), ctx)
+    pairs = np.array([(buf[l].i, buf[l].j) for l in range(n)], dtype=np.int64).reshape(-1, 2)
+    normals = np.array([list(buf[l].normal) for l in range(n)]).reshape(-1, 3)
+    gaps = np.array([buf[l].gap for l in range(n)])
+    return pairs, normals, gaps
+
+
+def lcp_get_b(ctx) -> np.ndarray:
+    _, _, n = lcp_sizes(ctx)
+    out = np.empty(n)
+    _check(_lib().lcp_get_b(ctx, _dptr(out)), ctx)
+    return out
+
+
+def lcp_get_unc(ctx) -> np.ndarray:
+    M, _, _ = lcp_sizes(ctx)
+    out = np.empty(6 * M)
+    _check(_lib().lcp_get_unc(ctx, _dptr(out)), ctx)
+    return out
+
+
+def mobility_apply(ctx, FT, include_slip: bool = False, fidelity: int = LCP_HIGH) -> np.ndarray:
+    M, _, _ = lcp_sizes(ctx)
+    f = _f64(FT, (6 * M,))
+    out = np.empty(6 * M)
+    _check(_lib().mobility_apply(ctx, _dptr(f), _dptr(out), int(include_slip), int(fidelity)), ctx)
+    return out
+
+
+def mobility_apply_dev(ctx, FT, UO, include_slip: bool = False, fidelity: int = LCP_HIGH) -> None:
+    _check(_lib().mobility_apply_dev(ctx, _devptr(FT), _devptr(UO), int(include_slip), int(fidelity)), ctx)
+
+
+def lcp_apply_A(ctx, x, fidelity: int = LCP_HIGH) -> np.ndarray:
+    _, _, n = lcp_sizes(ctx)
+    xv = _f64(x, (n,))
+    out = np.empty(n)
+    _check(_lib().lcp_apply_A(ctx, _dptr(xv), _dptr(out), int(fidelity)), ctx)
+    return out
+
+
+def lcp_solve(ctx, method: int, tol: float, x0=None, allow_not_converged: bool = False):
+    """Returns (x, stats dict, status)."""
+    _, _, n = lcp_sizes(ctx)
+    x = np.empty(n)
+    st = _abi.lcp_stats()
+    x0v = None if x0 is None else _f64(x0, (n,))
+    status = _lib().lcp_solve(ctx, int(method), float(tol), None if x0v is None else _dptr(x0v), _dptr(x),
+                              ctypes.byref(st))
+    allow = (LCP_OK, LCP_ERR_NOT_CONVERGED) if allow_not_converged else (LCP_OK,)
+    _check(status, ctx, allow)
+    return x, st.as_dict(), status
+
+
+def lcp_solve_dev(ctx, method: int, tol: float, x0, x, allow_not_converged: bool = False):
+    """x0 (or None) and x are CUDA float64 tensors [n]; returns (stats dict, status)."""
+    st = _abi.lcp_stats()
+    status = _lib().lcp_solve_dev(ctx, int(method), float(tol), _devptr(x0), _devptr(x), ctypes.byref(st))
+    allow = (LCP_OK, LCP_ERR_NOT_CONVERGED) if allow_not_converged else (LCP_OK,)
+    _check(status, ctx, allow)
+    return st.as_dict(), status
+
+
+def lcp_stokes_apply_dev(ctx, phi, out, precision: int = LCP_FP64) -> None:
+    _check(_lib().lcp_stokes_apply_dev(ctx, _devptr(phi), _devptr(out), int(precision)), ctx)
+
+
+def lcp_stokes_rhs_dev(ctx, FT, include_slip: bool, rhs) -> None:
+    _check(_lib().lcp_stokes_rhs_dev(ctx, _devptr(FT), int(include_slip), _devptr(rhs)), ctx)
+
+
+def lcp_rigid_velocity_dev(ctx, phi, UO) -> None:
+    _check(_lib().lcp_rigid_velocity_dev(ctx, _devptr(phi), _devptr(UO)), ctx)
+
+
+def config_for(instance, precision: int = LCP_FP64, **overrides) -> _abi.lcp_config:
+    """Config of a workload instance (grid, radii, dt, delta) with overrides."""
+    cfg = lcp_default_config(n_theta=instance.n_theta, n_phi=instance.n_phi, radius=instance.radius,
+                             contact_radius=instance.contact_radius, viscosity=instance.viscosity,
+                             dt=instance.dt, delta=instance.delta, precision=precision)
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg

@@ -1,0 +1,43 @@
+"""Shared test helpers: oracle data for a workload instance (CPU, FP64)."""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+
+from oracle.bie import DenseMobility, janus_slip, stokeslet_rotlet_rhs
+from oracle.contacts import contact_matrix, detect_contacts
+from oracle.lcp import lcp_data, pgs
+from oracle.rpy import rpy_matrix
+from workloads import make_instance
+
+
+@functools.lru_cache(maxsize=8)
+def dense_case(name: str, index: int):
+    """Instance plus its dense oracle: mobility, D, U_nc, A, b, A_hat, LCP solution."""
+    inst = make_instance(name, index)
+    mob = DenseMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, mu=inst.viscosity)
+    pairs, normals, gaps = detect_contacts(inst.centers, inst.contact_radius, inst.delta)
+    D = contact_matrix(inst.n_bodies, pairs, normals)
+    U_nc = mob.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes)
+    Mob = mob.matrix()
+    A, b = lcp_data(D, Mob, U_nc, gaps, inst.dt)
+    Ahat = D.T @ rpy_matrix(inst.centers, a=inst.radius, mu=inst.viscosity) @ D
+    xs = pgs(A, b)
+    return dict(inst=inst, mob=mob, pairs=pairs, normals=normals, gaps=gaps, D=D, U_nc=U_nc, Mob=Mob,
+                A=A, b=b, Ahat=Ahat, x=xs)
+
+
+def active_set(x, g, scale=1.0):
+    """Indices with x_l > 1e-9 max(1, ||x||_inf); ambiguous ones (both tiny) excluded."""
+    thr = 1e-9 * max(1.0, np.abs(x).max() if x.size else 1.0) * scale
+    act = set(np.nonzero(x > thr)[0].tolist())
+    amb = set(np.nonzero((np.abs(x) <= thr) & (np.abs(g) <= thr))[0].tolist())
+    return act, amb
+
+
+def rhs_oracle(mob: DenseMobility, FT, axes=None):
+    r = stokeslet_rotlet_rhs(mob.x, mob.centers, np.asarray(FT, float), mob.mu)
+    if axes is not None:
+        r = r + janus_slip(mob.n, mob.body, np.asarray(axes, float))
+    return r.reshape(-1)

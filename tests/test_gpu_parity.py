@@ -1,0 +1,219 @@
+"""GPU parity: every step of the hot path through the C ABI against the FP64 oracle.
+
+Tolerances (relative, max-norm over the compared vector):
+  FP64 stresslet apply             1e-12   (rounding order only)
+  FP32 stresslet apply (unrefined) 1e-4    (the mixed-mode bound of the spec; measured ~1e-6)
+  mobility solve, FP64 and mixed   1e-9    (GMRES tol 1e-12 on a well-conditioned second-kind system)
+  RPY, D, D^T, b                   1e-12 / 1e-9
+  LCP solutions: same active set as the oracle and ||min(x, A x + b)||_2 <= 10 tol with the
+  oracle's A and b (the GPU operator differs from the oracle's by ~1e-11).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2604_10089_gb300 as L  # noqa: E402
+from oracle.bie import DenseMobility  # noqa: E402
+from oracle.lcp import kkt_abs  # noqa: E402
+from oracle.mf import MatrixFreeMobility  # noqa: E402
+from oracle.rpy import rpy_matrix  # noqa: E402
+from workloads import make_instance  # noqa: E402
+
+from .cases import active_set, dense_case, rhs_oracle  # noqa: E402
+
+DEV = "cuda"
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def c1():
+    case = dense_case("spheres8_grid7x14", 1)
+    inst = case["inst"]
+    ctx = L.lcp_setup(L.config_for(inst), inst.centers, inst.axes)
+    yield case, ctx
+    L.lcp_destroy(ctx)
+
+
+def test_contacts_and_b_match_oracle(c1):
+    case, ctx = c1
+    pairs, normals, gaps = L.lcp_get_contacts(ctx)
+    np.testing.assert_array_equal(pairs, case["pairs"])
+    np.testing.assert_allclose(normals, case["normals"], atol=1e-15)
+    np.testing.assert_allclose(gaps, case["gaps"], atol=1e-14)
+    assert rel(L.lcp_get_unc(ctx), case["U_nc"]) <= 1e-9
+    assert rel(L.lcp_get_b(ctx), case["b"]) <= 1e-9
+
+
+@pytest.mark.parametrize("precision,tol", [(L.LCP_FP64, 1e-12), (L.LCP_MIXED, 1e-4)])
+def test_stresslet_apply(c1, precision, tol):
+    case, ctx = c1
+    mob = case["mob"]
+    phi = np.random.default_rng(3).standard_normal(mob.x.shape[0] * 3)
+    ref = (mob.K + mob.P) @ phi
+    dphi = torch.tensor(phi, device=DEV)
+    out = torch.empty_like(dphi)
+    L.lcp_stokes_apply_dev(ctx, dphi, out, precision)
+    err = rel(out.cpu().numpy(), ref)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("name,index", [("spheres64_grid9x18", 0)])
+@pytest.mark.parametrize("precision,tol", [(L.LCP_FP64, 1e-12), (L.LCP_MIXED, 1e-4)])
+def test_stresslet_apply_many_tiles(name, index, precision, tol):
+    """10 368 nodes: 41 target blocks with a ragged tail and several source splits."""
+    inst = make_instance(name, index)
+    ctx = L.lcp_setup(L.config_for(inst), inst.centers, None)
+    try:
+        mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius)
+        phi = np.random.default_rng(5).standard_normal(mf.x.shape[0] * 3)
+        ref = mf.apply_operator(phi)
+        dphi = torch.tensor(phi, device=DEV)
+        out = torch.empty_like(dphi)
+        L.lcp_stokes_apply_dev(ctx, dphi, out, precision)
+        assert rel(out.cpu().numpy(), ref) <= tol
+    finally:
+        L.lcp_destroy(ctx)
+
+
+def test_rhs_and_rigid_velocity(c1):
+    case, ctx = c1
+    mob, inst = case["mob"], case["inst"]
+    FT = np.random.default_rng(4).standard_normal(6 * inst.n_bodies)
+    dFT = torch.tensor(FT, device=DEV)
+    rhs = torch.empty(mob.x.shape[0] * 3, dtype=torch.float64, device=DEV)
+    L.lcp_stokes_rhs_dev(ctx, dFT, True, rhs)
+    assert rel(rhs.cpu().numpy(), rhs_oracle(mob, FT, inst.axes)) <= 1e-13
+    phi = np.random.default_rng(6).standard_normal(mob.x.shape[0] * 3)
+    UO = torch.empty(6 * inst.n_bodies, dtype=torch.float64, device=DEV)
+    L.lcp_rigid_velocity_dev(ctx, torch.tensor(phi, device=DEV), UO)
+    from oracle.bie import rigid_velocities
+    assert rel(UO.cpu().numpy(), rigid_velocities(phi, mob.parts)) <= 1e-13
+
+
+@pytest.mark.parametrize("precision", [L.LCP_FP64, L.LCP_MIXED])
+def test_mobility_matches_dense_lu(c1, precision):
+    case, _ = c1
+    inst, mob = case["inst"], case["mob"]
+    ctx = L.lcp_setup(L.config_for(inst, precision), inst.centers, inst.axes)
+    try:
+        FT = np.random.default_rng(7).standard_normal(6 * inst.n_bodies)
+        U = L.mobility_apply(ctx, FT, include_slip=False)
+        assert rel(U, case["Mob"] @ FT) <= 1e-9
+        Us = L.mobility_apply(ctx, np.zeros(6 * inst.n_bodies), include_slip=True)
+        assert rel(Us, case["U_nc"]) <= 1e-9
+    finally:
+        L.lcp_destroy(ctx)
+
+
+def test_single_sphere_drag_and_torque():
+    cfg = L.lcp_default_config(n_theta=7, n_phi=14, radius=0.9, viscosity=1.7)
+    ctx = L.lcp_setup(cfg, [[0.1, 0.2, -0.3]])
+    try:
+        U = L.mobility_apply(ctx, [1.0, -2.0, 0.5, 0.3, 0.0, -1.0])
+        a, mu = 0.9, 1.7
+        expect = np.array([1.0, -2.0, 0.5]) / (6 * np.pi * mu * a)
+        np.testing.assert_allclose(U[:3], expect, rtol=1e-10)
+        np.testing.assert_allclose(U[3:], np.array([0.3, 0.0, -1.0]) / (8 * np.pi * mu * a ** 3), rtol=1e-10, atol=1e-14)
+        assert L.lcp_sizes(ctx)[2] == 0
+    finally:
+        L.lcp_destroy(ctx)
+
+
+def test_rpy_and_apply_A(c1):
+    case, ctx = c1
+    inst = case["inst"]
+    FT = np.random.default_rng(8).standard_normal(6 * inst.n_bodies)
+    U = L.mobility_apply(ctx, FT, fidelity=L.LCP_LOW_RPY)
+    assert rel(U, rpy_matrix(inst.centers, a=inst.radius) @ FT) <= 1e-13
+    x = np.abs(np.random.default_rng(9).standard_normal(case["b"].size))
+    assert rel(L.lcp_apply_A(ctx, x, L.LCP_HIGH), case["A"] @ x) <= 1e-9
+    assert rel(L.lcp_apply_A(ctx, x, L.LCP_LOW_RPY), case["Ahat"] @ x) <= 1e-12
+
+
+def check_solution(case, x, tol):
+    A, b, xs = case["A"], case["b"], case["x"]
+    g = A @ x + b
+    assert kkt_abs(x, g) <= 10 * tol, kkt_abs(x, g)
+    act, amb = active_set(x, g)
+    act_ref, amb_ref = active_set(xs, A @ xs + b)
+    assert act - amb_ref == act_ref - amb, (sorted(act), sorted(act_ref))
+    assert np.abs(x - xs).max() <= 1e-5 * max(1.0, np.abs(xs).max())
+
+
+@pytest.mark.parametrize("index", [0, 1, 2, 3])
+@pytest.mark.parametrize("method", [L.LCP_MONO_PQN, L.LCP_BI_PQN])
+@pytest.mark.parametrize("precision", [L.LCP_FP64, L.LCP_MIXED])
+def test_lcp_solve_matches_oracle(index, method, precision):
+    case = dense_case("spheres8_grid7x14", index)
+    inst = case["inst"]
+    ctx = L.lcp_setup(L.config_for(inst, precision), inst.centers, inst.axes)
+    try:
+        x, st, status = L.lcp_solve(ctx, method, inst.tol)
+        assert status == L.LCP_OK and st["converged"] == 1
+        check_solution(case, x, inst.tol)
+        assert st["hi_mvps"] >= 1
+        if method == L.LCP_BI_PQN:
+            assert st["lo_mvps"] >= 1
+    finally:
+        L.lcp_destroy(ctx)
+
+
+def test_lcp_solve_device_pointers_and_warm_start():
+    case = dense_case("spheres8_grid7x14", 2)
+    inst = case["inst"]
+    ctx = L.lcp_setup(L.config_for(inst), inst.centers, inst.axes)
+    try:
+        n = case["b"].size
+        x = torch.empty(n, dtype=torch.float64, device=DEV)
+        st, _ = L.lcp_solve_dev(ctx, L.LCP_MONO_PQN, inst.tol, None, x)
+        check_solution(case, x.cpu().numpy(), inst.tol)
+        # warm start at the solution: one MVP, no iteration
+        x2 = torch.empty_like(x)
+        st2, _ = L.lcp_solve_dev(ctx, L.LCP_MONO_PQN, inst.tol, x, x2)
+        assert st2["hi_mvps"] == 1 and st2["iterations"] == 0
+    finally:
+        L.lcp_destroy(ctx)
+
+
+def test_caller_contacts_in_caller_order():
+    case = dense_case("spheres8_grid7x14", 3)
+    inst = case["inst"]
+    perm = np.random.default_rng(1).permutation(case["b"].size)
+    contacts = [(case["pairs"][l][0], case["pairs"][l][1], case["normals"][l], case["gaps"][l]) for l in perm]
+    ctx = L.lcp_setup(L.config_for(inst), inst.centers, inst.axes, contacts=contacts)
+    try:
+        assert rel(L.lcp_get_b(ctx), case["b"][perm]) <= 1e-9
+        x, st, _ = L.lcp_solve(ctx, L.LCP_MONO_PQN, inst.tol)
+        np.testing.assert_allclose(x, case["x"][perm], atol=1e-5 * max(1, case["x"].max()))
+    finally:
+        L.lcp_destroy(ctx)
+
+
+def test_no_contacts_and_trivial_lcp():
+    inst = make_instance("spheres8_grid7x14", 0)
+    ctx = L.lcp_setup(L.config_for(inst, delta=-1.0), inst.centers, inst.axes)
+    try:
+        assert L.lcp_sizes(ctx)[2] == 0
+        x, st, _ = L.lcp_solve(ctx, L.LCP_BI_PQN, 1e-8)
+        assert x.size == 0 and st["converged"] == 1
+    finally:
+        L.lcp_destroy(ctx)
+    # no slip: b = gap / dt > 0, so x = 0 after the first MVP
+    ctx = L.lcp_setup(L.config_for(inst), inst.centers, None)
+    try:
+        x, st, _ = L.lcp_solve(ctx, L.LCP_MONO_PQN, 1e-8)
+        assert np.all(x == 0.0) and st["hi_mvps"] == 1
+    finally:
+        L.lcp_destroy(ctx)
+
+
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(L.LcpError):
+        L.lcp_setup(L.lcp_default_config(n_phi=13), [[0, 0, 0]])
+    with pytest.raises(L.LcpError):
+        L.lcp_setup(L.lcp_default_config(contact_radius=0.5), [[0, 0, 0]])
