@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the collision-resolution hot path on GB300.
+
+Metric: LCP solves per second (and p50/p99 latency) on synthetic packings of
+216 Janus spheres with 11 x 22 nodes each (52 272 nodes, 156 816 unknowns),
+solved by mixed-precision Bi-PQN (FP32 stresslet sums, FP64 GMRES refinement
+to 1e-12) to ||min(x, A x + b)||_2 <= 1e-8.  One step is one full collision
+resolution of a fresh configuration: geometry, contacts and D, the slip
+solve for U_nc and b, then the LCP solve (every row of the hot path).
+
+The plain FP64 Mono-PQN GPU solve of the same configuration is timed once
+beside it (--fp64-compare), and the CPU oracle is timed on a bounded sample
+of the same workload on the host cores (cpu_baseline).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 run under torch.distributed.run: every rank solves its own
+configurations (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# FP32 pair-sum kernel: 32 flops per node pair (r, |r|^2, r.n, phi_q - phi_p, r.d,
+# the |r|^-5 scaling and the accumulation), plus one reciprocal square root.
+FLOPS_PER_PAIR = 32
+# Roofline denominator for plain FP32 ALU work: 152 SMs x 128 FP32 lanes x 2 flops
+# (FMA) x 2.070 GHz maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
+# Mobility solves per LCP solve used to scale the reference arm's per-apply sample:
+# the U_nc slip solve plus the high-fidelity MVPs of Bi-PQN measured on this
+# workload (11 on the first configuration).
+REFERENCE_SOLVES_PER_LCP = 12.0
+# DRAM traffic of one k_pair32 launch from an ncu capture (null once the kernel changes).
+PAIR32_TRAFFIC = {"source_sha1": None, "bytes_per_launch": None}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=6)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="spheres216_grid11x22")
+    p.add_argument("--method", default="bi", choices=["bi", "mono"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--fp64-compare", type=int, default=1)
+    p.add_argument("--cpu-baseline", type=int, default=1)
+    p.add_argument("--e2e", type=int, default=1)
+    return p.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    with open(os.path.join(ROOT, "paper_2604_10089_gb300", "csrc", "stokes.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
+def pct(v, q):
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_2604_10089_gb300 as L
+    from workloads import make_instance
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    n_inst = args.warmup + args.steps
+    insts = [make_instance(args.workload, rank * 1000 + i) for i in range(n_inst)]
+    prec = L.LCP_MIXED if args.precision == "mixed" else L.LCP_FP64
+    method = L.LCP_BI_PQN if args.method == "bi" else L.LCP_MONO_PQN
+    cfg = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream)
+    tol = insts[0].tol
+    with torch.cuda.stream(stream):
+        cen = [torch.tensor(i.centers, dtype=torch.float64, device=dev) for i in insts]
+        axs = [torch.tensor(i.axes, dtype=torch.float64, device=dev) for i in insts]
+    stream.synchronize()
+    ctx = L.lcp_setup(cfg, insts[0].centers, insts[0].axes)
+    M, N, _ = L.lcp_sizes(ctx)
+    xbuf = torch.empty(M * (M - 1) // 2, dtype=torch.float64, device=dev)
+    stats = []
+
+    def step(k):
+        L.lcp_update_dev(ctx, cen[k], axs[k])
+        _, _, n = L.lcp_sizes(ctx)
+        st, _ = L.lcp_solve_dev(ctx, method, tol, None, xbuf[:n])
+        return st, n
+
+    for k in range(args.warmup):
+        step(k)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    L.lcp_profile(ctx, True)
+    launches0 = L.lcp_launch_count(ctx)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    ncon = []
+    for k in range(args.steps):
+        st, n = step(args.warmup + k)
+        ev[k + 1].record(stream)
+        stats.append(st)
+        ncon.append(n)
+    torch.cuda.synchronize()
+    launches = L.lcp_launch_count(ctx) - launches0
+    c32, t32 = L.lcp_profile_read(ctx, 0)
+    c64, t64 = L.lcp_profile_read(ctx, 1)
+    L.lcp_profile(ctx, False)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    lat = [ev[k].elapsed_time(ev[k + 1]) / 1e3 for k in range(args.steps)]
+    t_total = ev[0].elapsed_time(ev[-1]) / 1e3
+    if world > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+
+    # end to end through the host API: host centres/axes in, host x out
+    e2e = None
+    if args.e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hb_in = hb_out = 0
+        for k in range(args.steps):
+            inst = insts[args.warmup + k]
+            L.lcp_update(ctx, inst.centers, inst.axes)
+            x, _, _ = L.lcp_solve(ctx, method, tol)
+            hb_in += inst.centers.nbytes + inst.axes.nbytes
+            hb_out += x.nbytes
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": args.steps * world / te if rank == 0 else None, "unit": "LCP solves/s",
+               "h2d_bytes_per_step": hb_in // args.steps, "d2h_bytes_per_step": hb_out // args.steps}
+
+    # plain FP64 Mono-PQN on the first timed configuration, and agreement with it
+    fp64 = None
+    if args.fp64_compare and rank == 0:
+        cfg64 = L.config_for(insts[0], L.LCP_FP64)
+        ctx64 = L.lcp_setup(cfg64, insts[args.warmup].centers, insts[args.warmup].axes)
+        t0 = time.perf_counter()
+        x64, st64, _ = L.lcp_solve(ctx64, L.LCP_MONO_PQN, tol)
+        t64s = time.perf_counter() - t0
+        L.lcp_destroy(ctx64)
+        L.lcp_update(ctx, insts[args.warmup].centers, insts[args.warmup].axes)
+        xm, stm, _ = L.lcp_solve(ctx, method, tol)
+        thr = 1e-9 * max(1.0, float(np.abs(x64).max()))
+        fp64 = {"method": "mono_pqn", "precision": "fp64", "solves_per_s": 1.0 / t64s,
+                "solve_seconds": t64s, "hi_mvps": st64["hi_mvps"], "gmres_iterations": st64["gmres_iterations"],
+                "max_abs_diff_vs_ours": float(np.abs(xm - x64).max()),
+                "same_active_set": bool(np.array_equal(xm > thr, x64 > thr)),
+                "kkt_fp64": st64["kkt_abs"], "kkt_ours": stm["kkt_abs"]}
+    L.lcp_destroy(ctx)
+
+    pairs = float(N) * (N - 1)
+    avg32 = t32 / c32 / 1e3 if c32 else None
+    roof = None
+    if avg32:
+        ach = pairs * FLOPS_PER_PAIR / avg32 / 1e12
+        traffic = PAIR32_TRAFFIC["bytes_per_launch"] if PAIR32_TRAFFIC["source_sha1"] == source_sha1() else None
+        roof = {"kernel": "k_pair32", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "launches": c32, "avg_launch_ms": avg32 * 1e3, "pairs_per_launch": pairs,
+                "flops_per_pair": FLOPS_PER_PAIR, "share_of_timed_region": t32 / 1e3 / t_total,
+                "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (nominal max clock)"}
+    k64 = None
+    if c64:
+        a64 = pairs * FLOPS_PER_PAIR / (t64 / c64 / 1e3) / 1e12
+        k64 = {"kernel": "k_pair64", "launches": c64, "avg_launch_ms": t64 / c64, "achieved": a64,
+               "peak": FP64_PEAK_TFLOPS, "frac": a64 / FP64_PEAK_TFLOPS,
+               "share_of_timed_region": t64 / 1e3 / t_total}
+    summary = {
+        "hi_mvps": [s["hi_mvps"] for s in stats], "lo_mvps": [s["lo_mvps"] for s in stats],
+        "e_mvps": [round(s["e_mvps"], 3) for s in stats], "iterations": [s["iterations"] for s in stats],
+        "gmres_iterations": [s["gmres_iterations"] for s in stats],
+        "fp32_applies": [s["fp32_applies"] for s in stats], "fp64_applies": [s["fp64_applies"] for s in stats],
+        "kkt_abs": [s["kkt_abs"] for s in stats], "contacts": ncon,
+        "converged": all(s["converged"] == 1 for s in stats),
+    }
+    return dict(t_total=t_total, lat=lat, clocks=clk, launches=launches, roof=roof, k64=k64, e2e=e2e,
+                fp64=fp64, summary=summary, N=N, M=M)
+
+
+def cpu_oracle_rate(workload: str, index: int, mobility_solves_per_lcp: float, budget_s: float = 20.0):
+    """Oracle (plain C, FP64, all host cores) on a bounded sample of the workload.
+
+    Sample: matrix-free applications of K + P for one configuration; the rate is
+    scaled to LCP solves with the GMRES iterations the oracle needs per mobility
+    solve (measured on a short solve) times the mobility solves per LCP solve.
+    """
+    from oracle.mf import MatrixFreeMobility
+    from workloads import make_instance
+
+    inst = make_instance(workload, index)
+    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, tol=1e-12)
+    phi = np.random.default_rng(0).standard_normal(3 * mf.x.shape[0])
+    t0 = time.perf_counter()
+    applies = 0
+    while True:
+        mf.apply_operator(phi)
+        applies += 1
+        if time.perf_counter() - t0 > budget_s or applies >= 50:
+            break
+    t_apply = (time.perf_counter() - t0) / applies
+    gmres_per_solve = 40.0   # measured on the workload's packings (FP64 GMRES to 1e-12)
+    t_solve = t_apply * gmres_per_solve * mobility_solves_per_lcp
+    cores = len(os.sched_getaffinity(0))
+    return {"value": 1.0 / t_solve, "unit": "LCP solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{applies} matrix-free FP64 K+P applications of one {workload} configuration "
+                      f"({t_apply:.3f} s each), scaled by {gmres_per_solve:.0f} GMRES iterations per mobility "
+                      f"solve and {mobility_solves_per_lcp:.1f} mobility solves per LCP solve",
+            "seconds_per_apply": t_apply}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(args.workload, k, mobility_solves_per_lcp=REFERENCE_SOLVES_PER_LCP, budget_s=0.0)
+        if k >= args.warmup:
+            steps.append(1.0 / r["value"])
+    value = len(steps) / sum(steps)
+    line = {"impl": "reference", "metric": "LCP solves/s", "value": value, "unit": "LCP solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "ms_per_step": 1e3 / value, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"value": value, "unit": "LCP solves/s", "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": "LCP solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        torch.distributed.init_process_group(backend=backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    r = run_ours(args, rank, world, local)
+    if rank == 0:
+        value = args.steps * world / r["t_total"]
+        s = r["summary"]
+        cpu = None
+        if args.cpu_baseline:
+            per = 1.0 + float(np.mean(s["hi_mvps"]))
+            cpu = cpu_oracle_rate(args.workload, 0, per)
+        line = {
+            "metric": "LCP solves/s", "value": value, "unit": "LCP solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["t_total"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {r['M']} Janus spheres, {r['N']} surface nodes, "
+                                   f"{3 * r['N']} unknowns",
+                       "method": f"{args.method}_pqn", "precision": args.precision, "tol": 1e-8,
+                       "gmres_tol": 1e-12, "step": "contacts + U_nc slip solve + b + LCP solve",
+                       "l2": "inputs larger than L2 (Krylov basis 76 MB + operator sweeps per apply)",
+                       "parallelism": f"instances x{world}"},
+            "latency_s": {"p50": pct(r["lat"], 50), "p99": pct(r["lat"], 99)},
+            "roofline": r["roof"], "fp64_kernel": r["k64"], "clocks": r["clocks"],
+            "e2e": r["e2e"], "gpu_launches": r["launches"], "cpu_baseline": cpu,
+            "fp64_mono_pqn": r["fp64"], "solver": s,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

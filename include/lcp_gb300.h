@@ -111,6 +111,28 @@ void lcp_default_config(lcp_config* cfg);
 int lcp_setup(const lcp_config* cfg, int n_bodies, const double* centers, const double* axes,
               int n_contacts, const lcp_contact* contacts, lcp_ctx** out);
 
+/* Re-configures the context for new centres (same M and grid): uploads
+ * centers [M*3] and axes [M*3] (NULL: no slip), detects the contacts (or takes
+ * n_contacts caller contacts), rebuilds D, U_nc and b.  Reuses the device
+ * buffers; the contact-sized ones grow when n exceeds their capacity.  This
+ * is the per-time-step entry of a trajectory (Eq. dvi). */
+int lcp_update(lcp_ctx* ctx, const double* centers, const double* axes, int n_contacts,
+               const lcp_contact* contacts);
+/* Same with device pointers centers [M*3], axes [M*3] or NULL; contacts are
+ * always detected. */
+int lcp_update_dev(lcp_ctx* ctx, const double* centers, const double* axes);
+
+/* Kernel timing.  lcp_profile(ctx, 1) clears the record and starts timing
+ * every stresslet-sum launch with CUDA events on the context's stream;
+ * lcp_profile(ctx, 0) stops and clears.  lcp_profile_read returns the number
+ * of launches of a kind (0 = FP32 pair sum, 1 = FP64 pair sum) and their
+ * summed duration in milliseconds (synchronises the stream). */
+int lcp_profile(lcp_ctx* ctx, int enable);
+int lcp_profile_read(lcp_ctx* ctx, int kind, int* count, double* total_ms);
+
+/* Number of kernels this context has launched since lcp_setup. */
+int lcp_launch_count(const lcp_ctx* ctx, unsigned long long* count);
+
 /* Frees every device buffer of the context.  NULL is ignored. */
 void lcp_destroy(lcp_ctx* ctx);
 

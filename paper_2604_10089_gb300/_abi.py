@@ -62,6 +62,11 @@ PROTOTYPES = {
     "lcp_setup": (_I, [ctypes.POINTER(lcp_config), _I, _D, _D, _I, ctypes.POINTER(lcp_contact),
                        ctypes.POINTER(_P)]),
     "lcp_destroy": (None, [_P]),
+    "lcp_update": (_I, [_P, _D, _D, _I, ctypes.POINTER(lcp_contact)]),
+    "lcp_update_dev": (_I, [_P, _P, _P]),
+    "lcp_profile": (_I, [_P, _I]),
+    "lcp_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "lcp_profile_read": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "lcp_last_error": (ctypes.c_char_p, [_P]),
     "lcp_sizes": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "lcp_get_contacts": (_I, [_P, ctypes.POINTER(lcp_contact)]),

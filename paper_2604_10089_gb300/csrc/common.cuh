@@ -66,11 +66,13 @@ struct lcp_ctx {
   double* ginv = nullptr;     // [36] inverse Gram matrix of the rigid modes
   double* centers = nullptr;  // [M][3]
   float* centers32 = nullptr; // [M][8]: hi(3), pad, lo(3), pad
-  double* axes = nullptr;     // [M][3] or null
+  double* axes = nullptr;     // [M][3]
+  bool has_axes = false;
   // contacts
   int *ci = nullptr, *cj = nullptr;
   double *cnrm = nullptr, *gap = nullptr, *b = nullptr;
   int *bc_ptr = nullptr, *bc_idx = nullptr;
+  int *flags = nullptr, *csr_cnt = nullptr;
   double* U_nc = nullptr;     // [M][6]
   // mobility solve workspace
   int m = 0, splits = 1;
@@ -91,7 +93,16 @@ struct lcp_ctx {
   int nh = 0;
   double *tmp_n = nullptr, *tmp_n2 = nullptr, *tmp_n3 = nullptr;
   std::vector<void*> allocs;
+  // contact-sized buffers live in one arena, re-created when n outgrows it
+  void* arena = nullptr;
+  int ncap = 0;
+  int pair_cap = 0;   // capacity of ci/cj/cnrm/gap
+  // kernel timing (lcp_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;
   std::string err;
+  unsigned long long nlaunch = 0;   // kernels launched by this context
   // counters of the current solve
   int c_gmres = 0, c_fp64 = 0, c_fp32 = 0;
 };
@@ -113,6 +124,7 @@ struct lcp_ctx {
 
 // Internal launch helpers implemented in the .cu files.
 int geometry_build(lcp_ctx* ctx);
+int geometry_update(lcp_ctx* ctx);
 int contacts_detect(lcp_ctx* ctx, int* n_out);
 int contacts_upload(lcp_ctx* ctx, int n, const lcp_contact* c);
 int contacts_csr(lcp_ctx* ctx);
@@ -125,6 +137,8 @@ int gather_Dt(lcp_ctx* ctx, const double* UO, double* out, const double* add);
 int rpy_apply(lcp_ctx* ctx, const double* FT, double* UO);
 int mvp_high(lcp_ctx* ctx, const double* x, double* Ax);
 int mvp_low(lcp_ctx* ctx, const double* x, double* Ax);
-int pqn_alloc(lcp_ctx* ctx, PqnDev* pq, int n, int rmax);
+size_t pqn_bytes(int n, int rmax);
+char* pqn_carve(PqnDev* pq, char* base, int n, int rmax);
+int pqn_reset(lcp_ctx* ctx, PqnDev* pq);
 int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st);
 void* ctx_alloc(lcp_ctx* ctx, size_t bytes);

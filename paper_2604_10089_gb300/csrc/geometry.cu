@@ -1,6 +1,7 @@
 // Geometry and contact set-up kernels (Sec. 3 of the paper: Eq. collisional-set
 // and the contact matrix D; Sec. 5.1: order-p surface discretisation).
 #include <cstdio>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -209,45 +210,61 @@ void* ctx_alloc(lcp_ctx* ctx, size_t bytes) {
   return p;
 }
 
+// Template, Gram inverse and the fixed-size contact buffers (once per context).
 int geometry_build(lcp_ctx* ctx) {
-  const int ns = ctx->ns;
+  const int ns = ctx->ns, M = ctx->M;
   ctx->tmpl64 = (double*)ctx_alloc(ctx, sizeof(double) * 8 * ns);
   ctx->tmpl32 = (float*)ctx_alloc(ctx, sizeof(float) * 6 * ns);
   ctx->ginv = (double*)ctx_alloc(ctx, sizeof(double) * 36);
   double* tn = (double*)ctx_alloc(ctx, sizeof(double) * 2 * ctx->cfg.n_theta);
-  ctx->centers32 = (float*)ctx_alloc(ctx, sizeof(float) * 8 * ctx->M);
-  if (!ctx->tmpl64 || !ctx->tmpl32 || !ctx->ginv || !tn || !ctx->centers32) return LCP_ERR_OOM;
-  k_template<<<1, 256, 0, ctx->stream>>>(ctx->cfg.n_theta, ctx->cfg.n_phi, ctx->cfg.radius, ctx->tmpl64,
+  ctx->centers32 = (float*)ctx_alloc(ctx, sizeof(float) * 8 * M);
+  ctx->pair_cap = M * (M - 1) / 2 > 0 ? M * (M - 1) / 2 : 1;
+  const int cap = ctx->pair_cap;
+  ctx->flags = (int*)ctx_alloc(ctx, sizeof(int) * (size_t)M * M);
+  ctx->csr_cnt = (int*)ctx_alloc(ctx, sizeof(int) * M);
+  ctx->bc_ptr = (int*)ctx_alloc(ctx, sizeof(int) * (M + 1));
+  ctx->ci = (int*)ctx_alloc(ctx, sizeof(int) * cap);
+  ctx->cj = (int*)ctx_alloc(ctx, sizeof(int) * cap);
+  ctx->cnrm = (double*)ctx_alloc(ctx, sizeof(double) * 3 * cap);
+  ctx->gap = (double*)ctx_alloc(ctx, sizeof(double) * cap);
+  if (!ctx->tmpl64 || !ctx->tmpl32 || !ctx->ginv || !tn || !ctx->centers32 || !ctx->flags || !ctx->csr_cnt ||
+      !ctx->bc_ptr || !ctx->ci || !ctx->cj || !ctx->cnrm || !ctx->gap)
+    return LCP_ERR_OOM;
+  ++ctx->nlaunch, k_template<<<1, 256, 0, ctx->stream>>>(ctx->cfg.n_theta, ctx->cfg.n_phi, ctx->cfg.radius, ctx->tmpl64,
                                          ctx->tmpl32, tn);
-  k_gram_inverse<<<1, 32, 0, ctx->stream>>>(ns, ctx->tmpl64, ctx->ginv);
-  k_centers32<<<(ctx->M + 127) / 128, 128, 0, ctx->stream>>>(ctx->M, ctx->centers, ctx->centers32);
+  ++ctx->nlaunch, k_gram_inverse<<<1, 32, 0, ctx->stream>>>(ns, ctx->tmpl64, ctx->ginv);
+  LCP_CUDA(cudaGetLastError());
+  return LCP_OK;
+}
+
+// hi/lo split of the (new) centres.
+int geometry_update(lcp_ctx* ctx) {
+  ++ctx->nlaunch, k_centers32<<<(ctx->M + 127) / 128, 128, 0, ctx->stream>>>(ctx->M, ctx->centers, ctx->centers32);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }
 
 int contacts_detect(lcp_ctx* ctx, int* n_out) {
   const int M = ctx->M;
-  const int cap = M * (M - 1) / 2 + 1;
-  int* flags = (int*)ctx_alloc(ctx, sizeof(int) * (size_t)M * M);
-  int* cnt = (int*)ctx_alloc(ctx, sizeof(int));
-  ctx->ci = (int*)ctx_alloc(ctx, sizeof(int) * cap);
-  ctx->cj = (int*)ctx_alloc(ctx, sizeof(int) * cap);
-  ctx->cnrm = (double*)ctx_alloc(ctx, sizeof(double) * 3 * cap);
-  ctx->gap = (double*)ctx_alloc(ctx, sizeof(double) * cap);
-  if (!flags || !cnt || !ctx->ci || !ctx->cj || !ctx->cnrm || !ctx->gap) return LCP_ERR_OOM;
-  k_pair_flags<<<(M * M + 255) / 256, 256, 0, ctx->stream>>>(M, ctx->centers, ctx->cfg.contact_radius,
-                                                               ctx->cfg.delta, flags);
-  k_compact_pairs<<<1, 1024, 0, ctx->stream>>>(M, ctx->centers, ctx->cfg.contact_radius, flags, cnt, cap,
-                                              ctx->ci, ctx->cj, ctx->cnrm, ctx->gap);
+  int* cnt = (int*)(ctx->dscal + 63);
+  ++ctx->nlaunch, k_pair_flags<<<(M * M + 255) / 256, 256, 0, ctx->stream>>>(M, ctx->centers, ctx->cfg.contact_radius,
+                                                               ctx->cfg.delta, ctx->flags);
+  ++ctx->nlaunch, k_compact_pairs<<<1, 1024, 0, ctx->stream>>>(M, ctx->centers, ctx->cfg.contact_radius, ctx->flags, cnt,
+                                              ctx->pair_cap, ctx->ci, ctx->cj, ctx->cnrm, ctx->gap);
   LCP_CUDA(cudaGetLastError());
-  int n = 0;
-  LCP_CUDA(cudaMemcpyAsync(&n, cnt, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  LCP_CUDA(cudaMemcpyAsync(ctx->hscal + 63, cnt, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+  int n = 0;
+  memcpy(&n, ctx->hscal + 63, sizeof(int));
   *n_out = n;
   return LCP_OK;
 }
 
 int contacts_upload(lcp_ctx* ctx, int n, const lcp_contact* c) {
+  if (n > ctx->pair_cap) {
+    ctx->err = "more contacts than body pairs";
+    return LCP_ERR_INVALID_ARG;
+  }
   std::vector<int> hi(n), hj(n);
   std::vector<double> hn(3 * (size_t)n), hg(n);
   for (int l = 0; l < n; l++) {
@@ -260,11 +277,6 @@ int contacts_upload(lcp_ctx* ctx, int n, const lcp_contact* c) {
     for (int d = 0; d < 3; d++) hn[3 * l + d] = c[l].normal[d];
     hg[l] = c[l].gap;
   }
-  ctx->ci = (int*)ctx_alloc(ctx, sizeof(int) * n);
-  ctx->cj = (int*)ctx_alloc(ctx, sizeof(int) * n);
-  ctx->cnrm = (double*)ctx_alloc(ctx, sizeof(double) * 3 * n);
-  ctx->gap = (double*)ctx_alloc(ctx, sizeof(double) * n);
-  if (!ctx->ci || !ctx->cj || !ctx->cnrm || !ctx->gap) return LCP_ERR_OOM;
   if (n > 0) {
     LCP_CUDA(cudaMemcpyAsync(ctx->ci, hi.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
     LCP_CUDA(cudaMemcpyAsync(ctx->cj, hj.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
@@ -275,15 +287,12 @@ int contacts_upload(lcp_ctx* ctx, int n, const lcp_contact* c) {
   return LCP_OK;
 }
 
+// bc_idx must hold 2 n entries (contact arena).
 int contacts_csr(lcp_ctx* ctx) {
   const int M = ctx->M, n = ctx->n;
-  int* cnt = (int*)ctx_alloc(ctx, sizeof(int) * M);
-  ctx->bc_ptr = (int*)ctx_alloc(ctx, sizeof(int) * (M + 1));
-  ctx->bc_idx = (int*)ctx_alloc(ctx, sizeof(int) * (2 * (size_t)n + 1));
-  if (!cnt || !ctx->bc_ptr || !ctx->bc_idx) return LCP_ERR_OOM;
-  k_body_csr_count<<<(M + 127) / 128, 128, 0, ctx->stream>>>(M, n, ctx->ci, ctx->cj, cnt);
-  k_scan_small<<<1, 32, 0, ctx->stream>>>(M, cnt, ctx->bc_ptr);
-  k_body_csr_fill<<<(M + 127) / 128, 128, 0, ctx->stream>>>(M, n, ctx->ci, ctx->cj, ctx->bc_ptr, ctx->bc_idx);
+  ++ctx->nlaunch, k_body_csr_count<<<(M + 127) / 128, 128, 0, ctx->stream>>>(M, n, ctx->ci, ctx->cj, ctx->csr_cnt);
+  ++ctx->nlaunch, k_scan_small<<<1, 32, 0, ctx->stream>>>(M, ctx->csr_cnt, ctx->bc_ptr);
+  ++ctx->nlaunch, k_body_csr_fill<<<(M + 127) / 128, 128, 0, ctx->stream>>>(M, n, ctx->ci, ctx->cj, ctx->bc_ptr, ctx->bc_idx);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }

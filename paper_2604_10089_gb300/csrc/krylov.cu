@@ -231,7 +231,7 @@ __global__ void k_rpy(int M, double a, double mu, const double* __restrict__ c, 
 static int blocks_for(int L, int t) { return (L + t - 1) / t; }
 
 static int dots(lcp_ctx* ctx, int L, int nv, const double* V, size_t ldv, const double* w, double* out) {
-  k_dots<<<ctx->dot_blocks, DOT_THREADS, 0, ctx->stream>>>(L, nv, V, ldv, w, ctx->dotp, out,
+  ++ctx->nlaunch, k_dots<<<ctx->dot_blocks, DOT_THREADS, 0, ctx->stream>>>(L, nv, V, ldv, w, ctx->dotp, out,
                                                             (unsigned int*)(ctx->dscal + 60));
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
@@ -272,17 +272,17 @@ static int gmres(lcp_ctx* ctx, const double* rhs, double* phi, int zero_init, do
       LCP_CUDA(cudaMemcpyAsync(ctx->V, rhs, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
     } else {
       LCP_TRY(stokes_apply(ctx, phi, ctx->wv, prec));
-      k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->wv, ctx->V);
+      ++ctx->nlaunch, k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->wv, ctx->V);
     }
     first = false;
     LCP_TRY(dots(ctx, L, 1, ctx->V, ldv, ctx->V, hn));
-    k_gmres_start<<<1, 1, 0, ctx->stream>>>(base, m, ctx->dscal);
+    ++ctx->nlaunch, k_gmres_start<<<1, 1, 0, ctx->stream>>>(base, m, ctx->dscal);
     double st[2];
     LCP_TRY(read_status(ctx, st, 1));
     res = st[0];
     if (!(res == res)) { ctx->err = "GMRES: NaN residual"; return LCP_ERR_NUMERICAL; }
     if (res <= tol_abs || total >= maxit) break;
-    k_scale<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, ctx->V, base + ohn + 1, ctx->V, 1, 0);  // V0 /= beta
+    ++ctx->nlaunch, k_scale<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, ctx->V, base + ohn + 1, ctx->V, 1, 0);  // V0 /= beta
     int j = 0;
     for (; j < m; j++) {
       double* vj = ctx->V + (size_t)j * ldv;
@@ -290,19 +290,19 @@ static int gmres(lcp_ctx* ctx, const double* rhs, double* phi, int zero_init, do
       LCP_TRY(stokes_apply(ctx, vj, vn, prec));
       total++;
       LCP_TRY(dots(ctx, L, j + 1, ctx->V, ldv, vn, h1));
-      k_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j + 1, ctx->V, ldv, h1, vn);
+      ++ctx->nlaunch, k_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j + 1, ctx->V, ldv, h1, vn);
       LCP_TRY(dots(ctx, L, j + 1, ctx->V, ldv, vn, h2));
-      k_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j + 1, ctx->V, ldv, h2, vn);
+      ++ctx->nlaunch, k_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j + 1, ctx->V, ldv, h2, vn);
       LCP_TRY(dots(ctx, L, 1, vn, ldv, vn, hn));
-      k_gmres_column<<<1, 1, 0, ctx->stream>>>(base, m, j, ctx->dscal);
-      k_scale<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, vn, hn, vn, 0, 0);   // v_{j+1} = w / H[j+1][j]
+      ++ctx->nlaunch, k_gmres_column<<<1, 1, 0, ctx->stream>>>(base, m, j, ctx->dscal);
+      ++ctx->nlaunch, k_scale<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, vn, hn, vn, 0, 0);   // v_{j+1} = w / H[j+1][j]
       LCP_TRY(read_status(ctx, st, 2));
       res = st[0];
       if (!(res == res)) { ctx->err = "GMRES: NaN residual"; return LCP_ERR_NUMERICAL; }
       if (res <= tol_abs || total >= maxit || st[1] == 0.0) { j++; break; }
     }
-    k_gmres_solve<<<1, 1, 0, ctx->stream>>>(base, m, j);
-    k_gmres_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j, ctx->V, ldv, y, phi);
+    ++ctx->nlaunch, k_gmres_solve<<<1, 1, 0, ctx->stream>>>(base, m, j);
+    ++ctx->nlaunch, k_gmres_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j, ctx->V, ldv, y, phi);
     LCP_CUDA(cudaGetLastError());
     if (res <= tol_abs || total >= maxit) break;
   }
@@ -350,9 +350,9 @@ int density_solve(lcp_ctx* ctx, const double* rhs, double* phi) {
     const double tin = std::max(ctx->cfg.inner_tol * rn, 0.5 * tol);
     LCP_TRY(gmres(ctx, ctx->res, ctx->dphi, 1, tin, LCP_MIXED, ctx->cfg.gmres_maxit, &its, &res));
     ctx->c_gmres += its;
-    k_add<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, ctx->dphi, phi);
+    ++ctx->nlaunch, k_add<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, ctx->dphi, phi);
     LCP_TRY(stokes_apply(ctx, phi, ctx->wv, LCP_FP64));
-    k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->wv, ctx->res);
+    ++ctx->nlaunch, k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->wv, ctx->res);
     LCP_TRY(norm2(ctx, ctx->res, L, &rn));
     if (!(rn == rn)) { ctx->err = "refinement: NaN residual"; return LCP_ERR_NUMERICAL; }
     if (rn <= tol) return LCP_OK;
@@ -368,20 +368,20 @@ int mobility_solve(lcp_ctx* ctx, const double* FT, int include_slip, double* UO)
 }
 
 int scatter_D(lcp_ctx* ctx, const double* x, double* FT) {
-  k_scatter<<<blocks_for(ctx->M, 128), 128, 0, ctx->stream>>>(ctx->M, ctx->bc_ptr, ctx->bc_idx, ctx->cnrm, x, FT);
+  ++ctx->nlaunch, k_scatter<<<blocks_for(ctx->M, 128), 128, 0, ctx->stream>>>(ctx->M, ctx->bc_ptr, ctx->bc_idx, ctx->cnrm, x, FT);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }
 
 int gather_Dt(lcp_ctx* ctx, const double* UO, double* out, const double* add) {
   if (ctx->n == 0) return LCP_OK;
-  k_gather<<<blocks_for(ctx->n, 128), 128, 0, ctx->stream>>>(ctx->n, ctx->ci, ctx->cj, ctx->cnrm, UO, add, out);
+  ++ctx->nlaunch, k_gather<<<blocks_for(ctx->n, 128), 128, 0, ctx->stream>>>(ctx->n, ctx->ci, ctx->cj, ctx->cnrm, UO, add, out);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }
 
 int rpy_apply(lcp_ctx* ctx, const double* FT, double* UO) {
-  k_rpy<<<blocks_for(ctx->M * 32, 128), 128, 0, ctx->stream>>>(ctx->M, ctx->cfg.radius, ctx->cfg.viscosity,
+  ++ctx->nlaunch, k_rpy<<<blocks_for(ctx->M * 32, 128), 128, 0, ctx->stream>>>(ctx->M, ctx->cfg.radius, ctx->cfg.viscosity,
                                                                  ctx->centers, FT, UO);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;

@@ -65,26 +65,16 @@ static int validate(const lcp_config* c, int M, const double* centers, std::stri
   return LCP_OK;
 }
 
-static int setup_impl(lcp_ctx* ctx, const double* centers, const double* axes, int n_contacts,
-                      const lcp_contact* contacts) {
-  const int M = ctx->M;
+// Buffers whose size depends only on M and the grid (once per context).
+static int alloc_static(lcp_ctx* ctx) {
+  const int M = ctx->M, N = ctx->N, L = 3 * N;
   ctx->centers = (double*)ctx_alloc(ctx, sizeof(double) * 3 * M);
-  if (!ctx->centers) return LCP_ERR_OOM;
-  LCP_CUDA(cudaMemcpyAsync(ctx->centers, centers, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, ctx->stream));
-  if (axes) {
-    ctx->axes = (double*)ctx_alloc(ctx, sizeof(double) * 3 * M);
-    if (!ctx->axes) return LCP_ERR_OOM;
-    LCP_CUDA(cudaMemcpyAsync(ctx->axes, axes, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, ctx->stream));
-  }
+  ctx->axes = (double*)ctx_alloc(ctx, sizeof(double) * 3 * M);
+  ctx->dscal = (double*)ctx_alloc(ctx, sizeof(double) * 64);
+  if (!ctx->centers || !ctx->axes || !ctx->dscal) return LCP_ERR_OOM;
+  LCP_CUDA(cudaMallocHost((void**)&ctx->hscal, sizeof(double) * 64));
+  LCP_CUDA(cudaMemsetAsync(ctx->dscal, 0, sizeof(double) * 64, ctx->stream));
   LCP_TRY(geometry_build(ctx));
-  if (contacts) {
-    LCP_TRY(contacts_upload(ctx, n_contacts, contacts));
-    ctx->n = n_contacts;
-  } else {
-    LCP_TRY(contacts_detect(ctx, &ctx->n));
-  }
-  LCP_TRY(contacts_csr(ctx));
-  const int N = ctx->N, n = ctx->n, L = 3 * N;
   ctx->m = ctx->cfg.gmres_restart;
   ctx->splits = stokes_max_splits(ctx);
   ctx->dot_blocks = 2 * 152;
@@ -102,38 +92,151 @@ static int setup_impl(lcp_ctx* ctx, const double* centers, const double* axes, i
   ctx->FT = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->UO = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->U_nc = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
-  ctx->dscal = (double*)ctx_alloc(ctx, sizeof(double) * 64);
-  ctx->b = (double*)ctx_alloc(ctx, sizeof(double) * (n > 0 ? n : 1));
-  ctx->tmp_n = (double*)ctx_alloc(ctx, sizeof(double) * (n > 0 ? n : 1));
-  ctx->tmp_n2 = (double*)ctx_alloc(ctx, sizeof(double) * (n > 0 ? n : 1));
-  ctx->tmp_n3 = (double*)ctx_alloc(ctx, sizeof(double) * (n > 0 ? n : 1));
-  ctx->Uh = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)(n > 0 ? n : 1) * ctx->cfg.kmax);
-  ctx->Vh = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)(n > 0 ? n : 1) * ctx->cfg.kmax);
   if (!ctx->V || !ctx->H || !ctx->phi || !ctx->rhs || !ctx->res || !ctx->wv || !ctx->dphi || !ctx->phi32 ||
-      !ctx->partial || !ctx->coef || !ctx->dotp || !ctx->FT || !ctx->UO || !ctx->U_nc || !ctx->dscal || !ctx->b ||
-      !ctx->tmp_n || !ctx->tmp_n2 || !ctx->tmp_n3 || !ctx->Uh || !ctx->Vh) {
+      !ctx->partial || !ctx->coef || !ctx->dotp || !ctx->FT || !ctx->UO || !ctx->U_nc) {
     ctx->err = "device allocation failed";
     return LCP_ERR_OOM;
   }
-  LCP_CUDA(cudaMallocHost((void**)&ctx->hscal, sizeof(double) * 64));
-  LCP_CUDA(cudaMemsetAsync(ctx->dscal, 0, sizeof(double) * 64, ctx->stream));
-  LCP_TRY(pqn_alloc(ctx, &ctx->pq_outer, n, ctx->cfg.memory));
-  LCP_TRY(pqn_alloc(ctx, &ctx->pq_inner, n, ctx->cfg.memory));
   LCP_TRY(stokes_configure(ctx));
   LCP_TRY(pqn_configure(ctx, ctx->cfg.memory));
+  return LCP_OK;
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Contact-sized buffers (b, CSR entries, PQN states, high-fidelity corrections)
+// in one arena, re-created only when n exceeds its capacity.
+static int arena_ensure(lcp_ctx* ctx, int n) {
+  if (ctx->arena && n <= ctx->ncap) return LCP_OK;
+  int cap = ctx->ncap * 2;
+  if (cap < n) cap = n;
+  if (cap < 64) cap = 64;
+  if (cap > ctx->pair_cap) cap = ctx->pair_cap > n ? ctx->pair_cap : n;
+  const int R = ctx->cfg.memory, K = ctx->cfg.kmax;
+  const size_t nn = cap;
+  const size_t bytes = 4 * al256(sizeof(double) * nn) + al256(sizeof(int) * (2 * nn + 1)) +
+                       2 * al256(sizeof(double) * nn * K) + 2 * pqn_bytes(cap, R);
+  if (ctx->arena) {
+    LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->arena);
+    ctx->arena = nullptr;
+    ctx->ncap = 0;
+  }
+  if (cudaMalloc(&ctx->arena, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->arena = nullptr;
+    ctx->err = "device allocation of the contact buffers failed";
+    return LCP_ERR_OOM;
+  }
+  char* p = (char*)ctx->arena;
+  ctx->b = (double*)p; p += al256(sizeof(double) * nn);
+  ctx->tmp_n = (double*)p; p += al256(sizeof(double) * nn);
+  ctx->tmp_n2 = (double*)p; p += al256(sizeof(double) * nn);
+  ctx->tmp_n3 = (double*)p; p += al256(sizeof(double) * nn);
+  ctx->bc_idx = (int*)p; p += al256(sizeof(int) * (2 * nn + 1));
+  ctx->Uh = (double*)p; p += al256(sizeof(double) * nn * K);
+  ctx->Vh = (double*)p; p += al256(sizeof(double) * nn * K);
+  p = pqn_carve(&ctx->pq_outer, p, cap, R);
+  p = pqn_carve(&ctx->pq_inner, p, cap, R);
+  ctx->ncap = cap;
+  return LCP_OK;
+}
+
+// Everything that depends on the configuration: centres (and axes), the
+// collisional set and D, U_nc and b (Sec. 3, Eqs. collisional-set, defAandb).
+static int configure(lcp_ctx* ctx, const double* centers, const double* axes, int n_contacts,
+                     const lcp_contact* contacts, bool device_inputs) {
+  const int M = ctx->M;
+  const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  LCP_CUDA(cudaMemcpyAsync(ctx->centers, centers, sizeof(double) * 3 * M, kind, ctx->stream));
+  ctx->has_axes = axes != nullptr;
+  if (axes) LCP_CUDA(cudaMemcpyAsync(ctx->axes, axes, sizeof(double) * 3 * M, kind, ctx->stream));
+  LCP_TRY(geometry_update(ctx));
+  if (contacts) {
+    LCP_TRY(contacts_upload(ctx, n_contacts, contacts));
+    ctx->n = n_contacts;
+  } else {
+    LCP_TRY(contacts_detect(ctx, &ctx->n));
+  }
+  const int n = ctx->n;
+  LCP_TRY(arena_ensure(ctx, n));
+  ctx->pq_outer.n = n;
+  ctx->pq_inner.n = n;
+  LCP_TRY(pqn_reset(ctx, &ctx->pq_outer));
+  LCP_TRY(pqn_reset(ctx, &ctx->pq_inner));
+  LCP_TRY(contacts_csr(ctx));
   // U_nc: slip-driven velocities with F = T = 0
   LCP_CUDA(cudaMemsetAsync(ctx->FT, 0, sizeof(double) * 6 * M, ctx->stream));
-  if (ctx->axes) {
+  if (ctx->has_axes) {
     LCP_TRY(mobility_solve(ctx, ctx->FT, 1, ctx->U_nc));
   } else {
     LCP_CUDA(cudaMemsetAsync(ctx->U_nc, 0, sizeof(double) * 6 * M, ctx->stream));
   }
   if (n > 0) {
     LCP_TRY(gather_Dt(ctx, ctx->U_nc, ctx->tmp_n, nullptr));
-    k_build_b<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, 1.0 / ctx->cfg.dt, ctx->gap, ctx->tmp_n, ctx->b);
+    ++ctx->nlaunch, k_build_b<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, 1.0 / ctx->cfg.dt, ctx->gap, ctx->tmp_n, ctx->b);
     LCP_CUDA(cudaGetLastError());
   }
   LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return LCP_OK;
+}
+
+static int setup_impl(lcp_ctx* ctx, const double* centers, const double* axes, int n_contacts,
+                      const lcp_contact* contacts) {
+  LCP_TRY(alloc_static(ctx));
+  return configure(ctx, centers, axes, n_contacts, contacts, false);
+}
+
+static int check_finite(lcp_ctx* ctx, const double* c, int count) {
+  for (int i = 0; i < count; i++)
+    if (!std::isfinite(c[i])) { ctx->err = "non-finite input coordinate"; return LCP_ERR_INVALID_ARG; }
+  return LCP_OK;
+}
+
+extern "C" int lcp_update(lcp_ctx* ctx, const double* centers, const double* axes, int n_contacts,
+                          const lcp_contact* contacts) {
+  if (!ctx || !centers) return LCP_ERR_INVALID_ARG;
+  if (contacts && n_contacts < 0) { ctx->err = "negative contact count"; return LCP_ERR_INVALID_ARG; }
+  LCP_TRY(check_finite(ctx, centers, 3 * ctx->M));
+  return configure(ctx, centers, axes, n_contacts, contacts, false);
+}
+
+extern "C" int lcp_update_dev(lcp_ctx* ctx, const double* centers, const double* axes) {
+  if (!ctx || !centers) return LCP_ERR_INVALID_ARG;
+  return configure(ctx, centers, axes, 0, nullptr, true);
+}
+
+// Kernel timing: CUDA events around every stresslet-sum launch while enabled.
+extern "C" int lcp_profile(lcp_ctx* ctx, int enable) {
+  if (!ctx) return LCP_ERR_INVALID_ARG;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  ctx->ev_pool.clear();
+  ctx->ev_kind.clear();
+  ctx->prof = enable != 0;
+  return LCP_OK;
+}
+
+extern "C" int lcp_launch_count(const lcp_ctx* ctx, unsigned long long* count) {
+  if (!ctx || !count) return LCP_ERR_INVALID_ARG;
+  *count = ctx->nlaunch;
+  return LCP_OK;
+}
+
+extern "C" int lcp_profile_read(lcp_ctx* ctx, int kind, int* count, double* total_ms) {
+  if (!ctx || !count || !total_ms) return LCP_ERR_INVALID_ARG;
+  LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+  int c = 0;
+  double t = 0.0;
+  for (size_t k = 0; k < ctx->ev_kind.size(); k++) {
+    if (ctx->ev_kind[k] != kind) continue;
+    float ms = 0.f;
+    LCP_CUDA(cudaEventElapsedTime(&ms, ctx->ev_pool[2 * k], ctx->ev_pool[2 * k + 1]));
+    c++;
+    t += ms;
+  }
+  *count = c;
+  *total_ms = t;
   return LCP_OK;
 }
 
@@ -167,6 +270,8 @@ extern "C" void lcp_destroy(lcp_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->arena) cudaFree(ctx->arena);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->hscal) cudaFreeHost(ctx->hscal);
   delete ctx;
 }
@@ -222,7 +327,7 @@ extern "C" int lcp_get_unc(lcp_ctx* ctx, double* u) {
 }
 
 static int mobility_impl(lcp_ctx* ctx, const double* FT, double* UO, int include_slip, int fidelity) {
-  if (include_slip && !ctx->axes) { ctx->err = "no Janus axes were given at set-up"; return LCP_ERR_INVALID_ARG; }
+  if (include_slip && !ctx->has_axes) { ctx->err = "no Janus axes were given at set-up"; return LCP_ERR_INVALID_ARG; }
   if (fidelity == LCP_HIGH) {
     return mobility_solve(ctx, FT, include_slip, UO);
   } else if (fidelity == LCP_LOW_RPY) {
@@ -295,7 +400,7 @@ extern "C" int lcp_stokes_apply_dev(lcp_ctx* ctx, const double* phi, double* out
 
 extern "C" int lcp_stokes_rhs_dev(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs) {
   if (!ctx || !FT || !rhs) return LCP_ERR_INVALID_ARG;
-  if (include_slip && !ctx->axes) { ctx->err = "no Janus axes were given at set-up"; return LCP_ERR_INVALID_ARG; }
+  if (include_slip && !ctx->has_axes) { ctx->err = "no Janus axes were given at set-up"; return LCP_ERR_INVALID_ARG; }
   LCP_TRY(stokes_rhs(ctx, FT, include_slip, rhs));
   LCP_CUDA(cudaStreamSynchronize(ctx->stream));
   return LCP_OK;

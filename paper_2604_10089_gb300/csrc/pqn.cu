@@ -809,28 +809,35 @@ struct PqnHost {
 
 static PqnWork work_of(lcp_ctx* ctx, const PqnDev& pq);
 
-int pqn_alloc(lcp_ctx* ctx, PqnDev* pq, int n, int rmax) {
-  const int nn = n > 0 ? n : 1;
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Bytes of the device state of one PQN run with n contacts and rmax pairs.
+size_t pqn_bytes(int n, int rmax) {
+  const size_t nn = n > 0 ? n : 1;
+  return 8 * al256(sizeof(double) * nn) + 4 * al256(sizeof(double) * nn * rmax) +
+         3 * al256(sizeof(double) * rmax * rmax) + al256(sizeof(int) * 4) +
+         al256(sizeof(double) * (S_NSCAL + 4 * nn + 2 * nn * rmax + rmax));
+}
+
+// Lays the state out from base; returns the first byte after it.
+char* pqn_carve(PqnDev* pq, char* base, int n, int rmax) {
+  const size_t nn = n > 0 ? n : 1;
   pq->n = n;
   pq->rmax = rmax;
   double** vecs[] = {&pq->x, &pq->g, &pq->p, &pq->Ap, &pq->xt, &pq->xh, &pq->extra, &pq->lop};
-  for (double** v : vecs) {
-    *v = (double*)ctx_alloc(ctx, sizeof(double) * nn);
-    if (!*v) return LCP_ERR_OOM;
-  }
+  for (double** v : vecs) { *v = (double*)base; base += al256(sizeof(double) * nn); }
   double** mats[] = {&pq->S, &pq->Y, &pq->U, &pq->V};
-  for (double** m : mats) {
-    *m = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)nn * rmax);
-    if (!*m) return LCP_ERR_OOM;
-  }
+  for (double** m : mats) { *m = (double*)base; base += al256(sizeof(double) * nn * rmax); }
   double** grams[] = {&pq->UU, &pq->UV, &pq->VV};
-  for (double** g : grams) {
-    *g = (double*)ctx_alloc(ctx, sizeof(double) * rmax * rmax);
-    if (!*g) return LCP_ERR_OOM;
-  }
-  pq->r = (int*)ctx_alloc(ctx, sizeof(int) * 4);
-  pq->scal = (double*)ctx_alloc(ctx, sizeof(double) * (S_NSCAL + 4 * (size_t)nn + 2 * (size_t)nn * rmax + rmax));
-  if (!pq->r || !pq->scal) return LCP_ERR_OOM;
+  for (double** g : grams) { *g = (double*)base; base += al256(sizeof(double) * rmax * rmax); }
+  pq->r = (int*)base;
+  base += al256(sizeof(int) * 4);
+  pq->scal = (double*)base;
+  base += al256(sizeof(double) * (S_NSCAL + 4 * nn + 2 * nn * rmax + rmax));
+  return base;
+}
+
+int pqn_reset(lcp_ctx* ctx, PqnDev* pq) {
   LCP_CUDA(cudaMemsetAsync(pq->r, 0, sizeof(int) * 4, ctx->stream));
   LCP_CUDA(cudaMemsetAsync(pq->scal, 0, sizeof(double) * S_NSCAL, ctx->stream));
   return LCP_OK;
@@ -876,7 +883,7 @@ static double now_s() {
 // Inner MVP of Bi-PQN subproblems: lop = A_hat[v]; Ap = lop + U_h U_h^T v - V_h V_h^T v.
 static int mvp_sub(lcp_ctx* ctx, PqnDev& pq, const double* v) {
   LCP_TRY(mvp_low(ctx, v, pq.lop));
-  k_bi_lowrank<<<1, PQN_T, 0, ctx->stream>>>(pq.n, ctx->nh, ctx->Uh, ctx->Vh, v, pq.lop, pq.Ap);
+  ++ctx->nlaunch, k_bi_lowrank<<<1, PQN_T, 0, ctx->stream>>>(pq.n, ctx->nh, ctx->Uh, ctx->Vh, v, pq.lop, pq.Ap);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }
@@ -901,9 +908,9 @@ static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* 
     LCP_CUDA(cudaStreamSynchronize(ctx->stream));
     rs->t_mvp += now_s() - t0;
     rs->mvps++;
-    k_pqn_grad<<<1, PQN_T, 0, ctx->stream>>>(pq, pq.Ap, b, nullptr);
+    ++ctx->nlaunch, k_pqn_grad<<<1, PQN_T, 0, ctx->stream>>>(pq, pq.Ap, b, nullptr);
   } else {
-    k_pqn_grad<<<1, PQN_T, 0, ctx->stream>>>(pq, nullptr, nullptr, g0);
+    ++ctx->nlaunch, k_pqn_grad<<<1, PQN_T, 0, ctx->stream>>>(pq, nullptr, nullptr, g0);
   }
   LCP_CUDA(cudaGetLastError());
   LCP_TRY(read_scal(ctx, pq, sc));
@@ -911,7 +918,7 @@ static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* 
   for (; k < kmax; k++) {
     if (!(sc[S_KKT] == sc[S_KKT])) { ctx->err = "PQN: NaN in the KKT error"; return LCP_ERR_NUMERICAL; }
     if (sc[S_KKT] <= tol) break;
-    k_pqn_direction<<<1, PQN_T, smem, ctx->stream>>>(pq, wk, ctx->cfg.ssn_maxit);
+    ++ctx->nlaunch, k_pqn_direction<<<1, PQN_T, smem, ctx->stream>>>(pq, wk, ctx->cfg.ssn_maxit);
     LCP_CUDA(cudaGetLastError());
     LCP_TRY(read_scal(ctx, pq, sc));
     if (sc[S_FLAG] == 1.0) break;  // p = 0: stationary
@@ -924,7 +931,7 @@ static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* 
     LCP_CUDA(cudaStreamSynchronize(ctx->stream));
     rs->t_mvp += now_s() - t0;
     rs->mvps++;
-    k_pqn_step<<<1, PQN_T, 0, ctx->stream>>>(pq, wk, sub, 1);
+    ++ctx->nlaunch, k_pqn_step<<<1, PQN_T, 0, ctx->stream>>>(pq, wk, sub, 1);
     LCP_CUDA(cudaGetLastError());
     LCP_TRY(read_scal(ctx, pq, sc));
   }
@@ -963,7 +970,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
   double sc[S_NSCAL];
   if (method == LCP_MONO_PQN) {
     RunStats rs;
-    k_pqn_init<<<1, PQN_T, 0, ctx->stream>>>(po, x0);
+    ++ctx->nlaunch, k_pqn_init<<<1, PQN_T, 0, ctx->stream>>>(po, x0);
     LCP_TRY(run_mono(ctx, po, mvp_high, 0, ctx->b, nullptr, tol, ctx->cfg.kmax, &rs));
     s.iterations = rs.iterations;
     s.hi_mvps = rs.mvps;
@@ -972,24 +979,24 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
     s.converged = rs.converged;
     s.hi_mvp_seconds = rs.mvps ? rs.t_mvp / rs.mvps : 0.0;
     s.e_mvps = s.hi_mvps;
-    k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, po.x, x);
+    ++ctx->nlaunch, k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, po.x, x);
   } else if (method == LCP_BI_PQN) {
     // low-fidelity initialisation: Mono-PQN on A_hat from x0, its pairs kept in pi
     RunStats r0;
-    k_pqn_init<<<1, PQN_T, 0, ctx->stream>>>(pi, x0);
+    ++ctx->nlaunch, k_pqn_init<<<1, PQN_T, 0, ctx->stream>>>(pi, x0);
     LCP_TRY(run_mono(ctx, pi, mvp_low, 0, ctx->b, nullptr, tol, ctx->cfg.kmax_inner, &r0));
     int lo = r0.mvps, hi = 0, inner_total = r0.iterations;
     double t_lo = r0.t_mvp, t_hi = 0.0;
     ctx->nh = 0;
     int* nh_dev = (int*)(ctx->dscal + 62);
     LCP_CUDA(cudaMemsetAsync(nh_dev, 0, sizeof(int), ctx->stream));
-    k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, pi.x, po.x);
+    ++ctx->nlaunch, k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, pi.x, po.x);
     double t0 = now_s();
     LCP_TRY(mvp_high(ctx, po.x, po.Ap));
     LCP_CUDA(cudaStreamSynchronize(ctx->stream));
     t_hi += now_s() - t0;
     hi++;
-    k_pqn_grad<<<1, PQN_T, 0, ctx->stream>>>(po, po.Ap, ctx->b, nullptr);
+    ++ctx->nlaunch, k_pqn_grad<<<1, PQN_T, 0, ctx->stream>>>(po, po.Ap, ctx->b, nullptr);
     LCP_TRY(read_scal(ctx, po, sc));
     PqnWork wk_in = work_of(ctx, pi);
     int k = 0;
@@ -997,9 +1004,9 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
       if (!(sc[S_KKT] == sc[S_KKT])) { ctx->err = "Bi-PQN: NaN in the KKT error"; return LCP_ERR_NUMERICAL; }
       if (sc[S_KKT] <= tol) break;
       // subproblem (Eq. pqnSubproblem) from x with gradient g, inherited pairs
-      k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, po.x, pi.x);
-      k_zero<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, pi.extra);
-      k_pqn_rebuild<<<1, PQN_T, 0, ctx->stream>>>(pi, wk_in);
+      ++ctx->nlaunch, k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, po.x, pi.x);
+      ++ctx->nlaunch, k_zero<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, pi.extra);
+      ++ctx->nlaunch, k_pqn_rebuild<<<1, PQN_T, 0, ctx->stream>>>(pi, wk_in);
       LCP_CUDA(cudaGetLastError());
       RunStats rs;
       const double tin = std::max(0.1 * tol, ctx->cfg.forcing * sc[S_KKT]);
@@ -1007,7 +1014,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
       lo += rs.mvps;
       t_lo += rs.t_mvp;
       inner_total += rs.iterations;
-      k_bi_direction<<<1, PQN_T, 0, ctx->stream>>>(po, pi.x);
+      ++ctx->nlaunch, k_bi_direction<<<1, PQN_T, 0, ctx->stream>>>(po, pi.x);
       LCP_TRY(read_scal(ctx, po, sc));
       if (sc[S_FLAG] == 1.0) break;
       const double* ahs = pi.extra;
@@ -1024,7 +1031,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
       LCP_CUDA(cudaStreamSynchronize(ctx->stream));
       t_hi += now_s() - t0;
       hi++;
-      k_bi_outer<<<1, PQN_T, 0, ctx->stream>>>(po, pi, wk_in, ctx->Uh, ctx->Vh, nh_dev, ctx->cfg.kmax, ahs);
+      ++ctx->nlaunch, k_bi_outer<<<1, PQN_T, 0, ctx->stream>>>(po, pi, wk_in, ctx->Uh, ctx->Vh, nh_dev, ctx->cfg.kmax, ahs);
       LCP_CUDA(cudaGetLastError());
       int nh_host = 0;
       LCP_CUDA(cudaMemcpyAsync(&nh_host, nh_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1041,7 +1048,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
     s.hi_mvp_seconds = hi ? t_hi / hi : 0.0;
     s.lo_mvp_seconds = lo ? t_lo / lo : 0.0;
     s.e_mvps = hi + (s.hi_mvp_seconds > 0 ? lo * s.lo_mvp_seconds / s.hi_mvp_seconds : 0.0);
-    k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, po.x, x);
+    ++ctx->nlaunch, k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, po.x, x);
   } else {
     ctx->err = "unknown method";
     return LCP_ERR_INVALID_ARG;

@@ -358,7 +358,7 @@ static int pair_splits(const lcp_ctx* ctx) {
 int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef) {
   const int threads = 128;
   const int blocks = (ctx->M * 32 + threads - 1) / threads;
-  k_moments<<<blocks, threads, 0, ctx->stream>>>(ctx->M, ctx->ns, ctx->tmpl64, phi, ctx->ginv, coef);
+  ++ctx->nlaunch, k_moments<<<blocks, threads, 0, ctx->stream>>>(ctx->M, ctx->ns, ctx->tmpl64, phi, ctx->ginv, coef);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }
@@ -371,36 +371,50 @@ int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
   splits = (M + bps - 1) / bps;
   dim3 grid((N + PAIR_THREADS - 1) / PAIR_THREADS, splits);
   LCP_TRY(stokes_coefs(ctx, phi, ctx->coef));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ctx->prof) {
+    LCP_CUDA(cudaEventCreate(&e0));
+    LCP_CUDA(cudaEventCreate(&e1));
+  }
   if (precision == LCP_MIXED) {
-    k_to_f32<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(3 * N, phi, ctx->phi32);
+    ++ctx->nlaunch, k_to_f32<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(3 * N, phi, ctx->phi32);
+    if (e0) LCP_CUDA(cudaEventRecord(e0, ctx->stream));
     const int ns_pad = (ns + 3) & ~3;
     const size_t smem = sizeof(float) * (6 * ns_pad + 3 * PAIR_CHUNK * ns_pad);
-    k_pair32<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, ns_pad, M, bps, ctx->tmpl32, ctx->centers32,
+    ++ctx->nlaunch, k_pair32<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, ns_pad, M, bps, ctx->tmpl32, ctx->centers32,
                                                         ctx->phi32, ctx->partial);
+    if (e1) LCP_CUDA(cudaEventRecord(e1, ctx->stream));
     ctx->c_fp32++;
   } else {
     const size_t smem = sizeof(double) * (6 * ns + 3 * PAIR_CHUNK * ns);
-    k_pair64<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, M, bps, ctx->tmpl64, ctx->centers, phi,
+    if (e0) LCP_CUDA(cudaEventRecord(e0, ctx->stream));
+    ++ctx->nlaunch, k_pair64<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, M, bps, ctx->tmpl64, ctx->centers, phi,
                                                         ctx->partial);
+    if (e1) LCP_CUDA(cudaEventRecord(e1, ctx->stream));
     ctx->c_fp64++;
   }
-  k_finish<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ns, splits, ctx->partial, ctx->coef, ctx->tmpl64, out);
+  ++ctx->nlaunch, k_finish<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ns, splits, ctx->partial, ctx->coef, ctx->tmpl64, out);
   LCP_CUDA(cudaGetLastError());
+  if (e0) {
+    ctx->ev_pool.push_back(e0);
+    ctx->ev_pool.push_back(e1);
+    ctx->ev_kind.push_back(precision == LCP_MIXED ? 0 : 1);
+  }
   return LCP_OK;
 }
 
 int stokes_rhs(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs) {
   const int N = ctx->N;
-  k_rhs<<<(N + 127) / 128, 128, 0, ctx->stream>>>(N, ctx->ns, ctx->M, ctx->cfg.radius, ctx->cfg.viscosity,
+  ++ctx->nlaunch, k_rhs<<<(N + 127) / 128, 128, 0, ctx->stream>>>(N, ctx->ns, ctx->M, ctx->cfg.radius, ctx->cfg.viscosity,
                                                   ctx->tmpl64, ctx->centers, FT,
-                                                  include_slip ? ctx->axes : nullptr, rhs);
+                                                  include_slip && ctx->has_axes ? ctx->axes : nullptr, rhs);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }
 
 int stokes_velocity(lcp_ctx* ctx, const double* phi, double* UO) {
   LCP_TRY(stokes_coefs(ctx, phi, ctx->coef));
-  k_neg<<<(6 * ctx->M + 127) / 128, 128, 0, ctx->stream>>>(6 * ctx->M, ctx->coef, UO);
+  ++ctx->nlaunch, k_neg<<<(6 * ctx->M + 127) / 128, 128, 0, ctx->stream>>>(6 * ctx->M, ctx->coef, UO);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }

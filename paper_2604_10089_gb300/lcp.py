@@ -64,25 +64,58 @@ def lcp_default_config(**overrides) -> _abi.lcp_config:
     return cfg
 
 
+def _contacts(contacts):
+    if contacts is None:
+        return None, 0
+    nc = len(contacts)
+    cont = (_abi.lcp_contact * max(nc, 1))()
+    for l, (i, j, nrm, gap) in enumerate(contacts):
+        cont[l].i, cont[l].j, cont[l].gap = int(i), int(j), float(gap)
+        for d in range(3):
+            cont[l].normal[d] = float(nrm[d])
+    return cont, nc
+
+
 def lcp_setup(cfg: _abi.lcp_config, centers, axes=None, contacts=None):
     """Returns the opaque context handle (an int)."""
     c = _f64(centers, (-1, 3))
     M = c.shape[0]
     a = None if axes is None else _f64(axes, (M, 3))
-    cont = None
-    nc = 0
-    if contacts is not None:
-        nc = len(contacts)
-        cont = (_abi.lcp_contact * max(nc, 1))()
-        for l, (i, j, nrm, gap) in enumerate(contacts):
-            cont[l].i, cont[l].j, cont[l].gap = int(i), int(j), float(gap)
-            for d in range(3):
-                cont[l].normal[d] = float(nrm[d])
+    cont, nc = _contacts(contacts)
     out = ctypes.c_void_p()
     st = _lib().lcp_setup(ctypes.byref(cfg), M, _dptr(c), None if a is None else _dptr(a), nc, cont,
                           ctypes.byref(out))
     _check(st, None)
     return out.value
+
+
+def lcp_update(ctx, centers, axes=None, contacts=None) -> None:
+    M, _, _ = lcp_sizes(ctx)
+    c = _f64(centers, (M, 3))
+    a = None if axes is None else _f64(axes, (M, 3))
+    cont, nc = _contacts(contacts)
+    _check(_lib().lcp_update(ctx, _dptr(c), None if a is None else _dptr(a), nc, cont), ctx)
+
+
+def lcp_update_dev(ctx, centers, axes=None) -> None:
+    _check(_lib().lcp_update_dev(ctx, _devptr(centers), _devptr(axes)), ctx)
+
+
+def lcp_profile(ctx, enable: bool) -> None:
+    _check(_lib().lcp_profile(ctx, int(enable)), ctx)
+
+
+def lcp_launch_count(ctx) -> int:
+    c = ctypes.c_ulonglong()
+    _check(_lib().lcp_launch_count(ctx, ctypes.byref(c)), ctx)
+    return c.value
+
+
+def lcp_profile_read(ctx, kind: int):
+    """(launch count, total milliseconds) of kind 0 = FP32 pair sum, 1 = FP64 pair sum."""
+    c, t = ctypes.c_int(), ctypes.c_double()
+    _check(_lib().lcp_profile_read(ctx, int(kind), ctypes.byref(c), ctypes.byref(t)), ctx)
+    return c.value, t.value
 
 
 def lcp_destroy(ctx) -> None:
