@@ -76,6 +76,7 @@ struct lcp_ctx {
   double* U_nc = nullptr;     // [M][6]
   // mobility solve workspace
   int m = 0, splits = 1;
+  int num_sms = 0, occ32 = 0, occ64 = 0;   // pair-kernel grid sizing
   double *V = nullptr, *H = nullptr;  // Krylov basis [(m+1)][3N], Hessenberg etc.
   double *phi = nullptr, *rhs = nullptr, *res = nullptr, *wv = nullptr, *dphi = nullptr;
   float* phi32 = nullptr;

@@ -36,7 +36,7 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->gmres_tol = 1e-12;
   c->gmres_restart = 60;
   c->gmres_maxit = 600;
-  c->inner_tol = 1e-5;
+  c->inner_tol = 1e-6;
   c->ir_maxit = 8;
   c->kmax = 100;
   c->kmax_inner = 100;
@@ -76,6 +76,7 @@ static int alloc_static(lcp_ctx* ctx) {
   LCP_CUDA(cudaMemsetAsync(ctx->dscal, 0, sizeof(double) * 64, ctx->stream));
   LCP_TRY(geometry_build(ctx));
   ctx->m = ctx->cfg.gmres_restart;
+  LCP_TRY(stokes_configure(ctx));
   ctx->splits = stokes_max_splits(ctx);
   ctx->dot_blocks = 2 * 152;
   ctx->V = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)L * (ctx->m + 1));
@@ -97,7 +98,6 @@ static int alloc_static(lcp_ctx* ctx) {
     ctx->err = "device allocation failed";
     return LCP_ERR_OOM;
   }
-  LCP_TRY(stokes_configure(ctx));
   LCP_TRY(pqn_configure(ctx, ctx->cfg.memory));
   return LCP_OK;
 }

@@ -75,13 +75,30 @@ __device__ __forceinline__ void pair2(const float2 ex, const float2 ey, const fl
 
 }  // namespace
 
-// FP32 stresslet sum.  Grid (target blocks, source splits); one target per
-// thread; sources two at a time in packed FP32x2 arithmetic.  Per-body (tile)
-// sums in FP32, Kahan-compensated FP32 across tiles, written as FP64 partials
-// partial[split][p][3].  ns_pad is ns rounded up to 4; padded sources carry
-// zero weight.
+// Work decomposition shared by both pair kernels.  The N x N pair sum is cut
+// into units (target block tb, source body j); the U = ntb * M units are dealt
+// out in contiguous, equal ranges to a grid of G CTAs sized to one full wave
+// (SMs x resident CTAs per SM), so no CTA waits for a second wave.  A CTA
+// writes one partial per target block it touches into slot
+// (c - first CTA touching tb); the finishing kernel sums the slots in order.
+struct Units {
+  int U, G, M;
+  __device__ __forceinline__ int start(int c) const { return (int)(((long long)c * U) / G); }
+  __device__ __forceinline__ int first_cta(int tb) const {
+    const int u = tb * M;
+    int c = (int)(((long long)u * G) / U);
+    while (c + 1 < G && start(c + 1) <= u) c++;
+    while (c > 0 && start(c) > u) c--;
+    return c;
+  }
+};
+
+// FP32 stresslet sum: one target per thread; sources two at a time in packed
+// FP32x2 arithmetic.  Per-body (tile) sums in FP32, Kahan-compensated FP32
+// across tiles, written as FP64 partials partial[slot][p][3].  ns_pad is ns
+// rounded up to 4; padded sources carry zero weight.
 __global__ void __launch_bounds__(PAIR_THREADS)
-k_pair32(int N, int ns, int ns_pad, int M, int bodies_per_split, const float* __restrict__ tmpl32,
+k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
          const float* __restrict__ c32, const float* __restrict__ phi32, double* __restrict__ partial) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
@@ -93,9 +110,6 @@ k_pair32(int N, int ns, int ns_pad, int M, int bodies_per_split, const float* __
   float* s_wz = s_wy + ns_pad;
   float* s_f = s_wz + ns_pad;          // [3][PAIR_CHUNK][ns_pad] source densities
 
-  const int split = blockIdx.y;
-  const int jb0 = split * bodies_per_split;
-  const int jb1 = min(M, jb0 + bodies_per_split);
   for (int q = threadIdx.x; q < ns_pad; q += blockDim.x) {
     const bool real = q < ns;
     s_nx[q] = real ? -tmpl32[q] : -1.0e3f;
@@ -105,127 +119,143 @@ k_pair32(int N, int ns, int ns_pad, int M, int bodies_per_split, const float* __
     s_wy[q] = real ? tmpl32[4 * ns + q] : 0.f;
     s_wz[q] = real ? tmpl32[5 * ns + q] : 0.f;
   }
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int pc = p < N ? p : N - 1;
-  const int bi = pc / ns, qi = pc % ns;
-  const float xpx = tmpl32[qi], xpy = tmpl32[ns + qi], xpz = tmpl32[2 * ns + qi];
-  const float4 cih = *reinterpret_cast<const float4*>(c32 + 8 * bi);
-  const float4 cil = *reinterpret_cast<const float4*>(c32 + 8 * bi + 4);
-  const float fpx = phi32[3 * pc], fpy = phi32[3 * pc + 1], fpz = phi32[3 * pc + 2];
-  const float2 nfx = make_float2(-fpx, -fpx), nfy = make_float2(-fpy, -fpy), nfz = make_float2(-fpz, -fpz);
-  float sx = 0.f, sy = 0.f, sz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
-
-  for (int jc = jb0; jc < jb1; jc += PAIR_CHUNK) {
-    const int nb = min(PAIR_CHUNK, jb1 - jc);
-    __syncthreads();
-    // stage densities of bodies jc .. jc+nb-1 (contiguous in phi32), SoA in smem
-    const int cnt = nb * ns;
-    const float* src = phi32 + 3 * (size_t)jc * ns;
-    for (int t = threadIdx.x; t < 3 * cnt; t += blockDim.x) {
-      const int node = t / 3, d = t - 3 * node;
-      const int b = node / ns, q = node - b * ns;
-      s_f[(d * PAIR_CHUNK + b) * ns_pad + q] = src[t];
-    }
-    for (int t = threadIdx.x; t < nb * (ns_pad - ns); t += blockDim.x) {
-      const int b = t / (ns_pad - ns), q = ns + t % (ns_pad - ns);
-      for (int d = 0; d < 3; d++) s_f[(d * PAIR_CHUNK + b) * ns_pad + q] = 0.f;
-    }
-    __syncthreads();
-    for (int b = 0; b < nb; b++) {
-      const int j = jc + b;
-      const float4 cjh = *reinterpret_cast<const float4*>(c32 + 8 * j);
-      const float4 cjl = *reinterpret_cast<const float4*>(c32 + 8 * j + 4);
-      const float ex1 = ((cih.x - cjh.x) + (cil.x - cjl.x)) + xpx;
-      const float ey1 = ((cih.y - cjh.y) + (cil.y - cjl.y)) + xpy;
-      const float ez1 = ((cih.z - cjh.z) + (cil.z - cjl.z)) + xpz;
-      const float2 ex = make_float2(ex1, ex1), ey = make_float2(ey1, ey1), ez = make_float2(ez1, ez1);
-      const float* fxb = s_f + (0 * PAIR_CHUNK + b) * ns_pad;
-      const float* fyb = s_f + (1 * PAIR_CHUNK + b) * ns_pad;
-      const float* fzb = s_f + (2 * PAIR_CHUNK + b) * ns_pad;
-      float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
-#pragma unroll 1
-      for (int q = 0; q < ns_pad; q += 4) {
-        const float4 X = *reinterpret_cast<const float4*>(s_nx + q);
-        const float4 Y = *reinterpret_cast<const float4*>(s_ny + q);
-        const float4 Z = *reinterpret_cast<const float4*>(s_nz + q);
-        const float4 WX = *reinterpret_cast<const float4*>(s_wx + q);
-        const float4 WY = *reinterpret_cast<const float4*>(s_wy + q);
-        const float4 WZ = *reinterpret_cast<const float4*>(s_wz + q);
-        const float4 FX = *reinterpret_cast<const float4*>(fxb + q);
-        const float4 FY = *reinterpret_cast<const float4*>(fyb + q);
-        const float4 FZ = *reinterpret_cast<const float4*>(fzb + q);
-        pair2(ex, ey, ez, nfx, nfy, nfz, make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
-              make_float2(WX.x, WX.y), make_float2(WY.x, WY.y), make_float2(WZ.x, WZ.y),
-              make_float2(FX.x, FX.y), make_float2(FY.x, FY.y), make_float2(FZ.x, FZ.y), ax, ay, az);
-        pair2(ex, ey, ez, nfx, nfy, nfz, make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
-              make_float2(WX.z, WX.w), make_float2(WY.z, WY.w), make_float2(WZ.z, WZ.w),
-              make_float2(FX.z, FX.w), make_float2(FY.z, FY.w), make_float2(FZ.z, FZ.w), ax, ay, az);
+  const int M = un.M;
+  const int c = blockIdx.x;
+  int u = un.start(c);
+  const int uend = un.start(c + 1);
+  while (u < uend) {
+    const int tb = u / M, jb0 = u - tb * M;
+    const int jb1 = min(M, jb0 + (uend - u));
+    const int slot = c - un.first_cta(tb);
+    u += jb1 - jb0;
+    const int p = tb * blockDim.x + threadIdx.x;
+    const int pc = p < N ? p : N - 1;
+    const int bi = pc / ns, qi = pc - bi * ns;
+    const float xpx = tmpl32[qi], xpy = tmpl32[ns + qi], xpz = tmpl32[2 * ns + qi];
+    const float4 cih = *reinterpret_cast<const float4*>(c32 + 8 * bi);
+    const float4 cil = *reinterpret_cast<const float4*>(c32 + 8 * bi + 4);
+    const float fpx = phi32[3 * pc], fpy = phi32[3 * pc + 1], fpz = phi32[3 * pc + 2];
+    const float2 nfx = make_float2(-fpx, -fpx), nfy = make_float2(-fpy, -fpy), nfz = make_float2(-fpz, -fpz);
+    float sx = 0.f, sy = 0.f, sz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+    for (int jc = jb0; jc < jb1; jc += PAIR_CHUNK) {
+      const int nb = min(PAIR_CHUNK, jb1 - jc);
+      __syncthreads();
+      // stage densities of bodies jc .. jc+nb-1 (contiguous in phi32), SoA in smem
+      const int cnt = nb * ns;
+      const float* src = phi32 + 3 * (size_t)jc * ns;
+      for (int t = threadIdx.x; t < 3 * cnt; t += blockDim.x) {
+        const int node = t / 3, d = t - 3 * node;
+        const int b = node / ns, q = node - b * ns;
+        s_f[(d * PAIR_CHUNK + b) * ns_pad + q] = src[t];
       }
-      kahan_add(sx, kx, ax.x + ax.y);
-      kahan_add(sy, ky, ay.x + ay.y);
-      kahan_add(sz, kz, az.x + az.y);
+      for (int t = threadIdx.x; t < nb * (ns_pad - ns); t += blockDim.x) {
+        const int b = t / (ns_pad - ns), q = ns + t % (ns_pad - ns);
+        for (int d = 0; d < 3; d++) s_f[(d * PAIR_CHUNK + b) * ns_pad + q] = 0.f;
+      }
+      __syncthreads();
+      for (int b = 0; b < nb; b++) {
+        const int j = jc + b;
+        const float4 cjh = *reinterpret_cast<const float4*>(c32 + 8 * j);
+        const float4 cjl = *reinterpret_cast<const float4*>(c32 + 8 * j + 4);
+        const float ex1 = ((cih.x - cjh.x) + (cil.x - cjl.x)) + xpx;
+        const float ey1 = ((cih.y - cjh.y) + (cil.y - cjl.y)) + xpy;
+        const float ez1 = ((cih.z - cjh.z) + (cil.z - cjl.z)) + xpz;
+        const float2 ex = make_float2(ex1, ex1), ey = make_float2(ey1, ey1), ez = make_float2(ez1, ez1);
+        const float* fxb = s_f + (0 * PAIR_CHUNK + b) * ns_pad;
+        const float* fyb = s_f + (1 * PAIR_CHUNK + b) * ns_pad;
+        const float* fzb = s_f + (2 * PAIR_CHUNK + b) * ns_pad;
+        float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+#pragma unroll 1
+        for (int q = 0; q < ns_pad; q += 4) {
+          const float4 X = *reinterpret_cast<const float4*>(s_nx + q);
+          const float4 Y = *reinterpret_cast<const float4*>(s_ny + q);
+          const float4 Z = *reinterpret_cast<const float4*>(s_nz + q);
+          const float4 WX = *reinterpret_cast<const float4*>(s_wx + q);
+          const float4 WY = *reinterpret_cast<const float4*>(s_wy + q);
+          const float4 WZ = *reinterpret_cast<const float4*>(s_wz + q);
+          const float4 FX = *reinterpret_cast<const float4*>(fxb + q);
+          const float4 FY = *reinterpret_cast<const float4*>(fyb + q);
+          const float4 FZ = *reinterpret_cast<const float4*>(fzb + q);
+          pair2(ex, ey, ez, nfx, nfy, nfz, make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+                make_float2(WX.x, WX.y), make_float2(WY.x, WY.y), make_float2(WZ.x, WZ.y),
+                make_float2(FX.x, FX.y), make_float2(FY.x, FY.y), make_float2(FZ.x, FZ.y), ax, ay, az);
+          pair2(ex, ey, ez, nfx, nfy, nfz, make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+                make_float2(WX.z, WX.w), make_float2(WY.z, WY.w), make_float2(WZ.z, WZ.w),
+                make_float2(FX.z, FX.w), make_float2(FY.z, FY.w), make_float2(FZ.z, FZ.w), ax, ay, az);
+        }
+        kahan_add(sx, kx, ax.x + ax.y);
+        kahan_add(sy, ky, ay.x + ay.y);
+        kahan_add(sz, kz, az.x + az.y);
+      }
     }
-  }
-  if (p < N) {
-    double* o = partial + ((size_t)split * N + p) * 3;
-    o[0] = (double)sx - (double)kx;
-    o[1] = (double)sy - (double)ky;
-    o[2] = (double)sz - (double)kz;
+    if (p < N) {
+      double* o = partial + ((size_t)slot * N + p) * 3;
+      o[0] = (double)sx - (double)kx;
+      o[1] = (double)sy - (double)ky;
+      o[2] = (double)sz - (double)kz;
+    }
   }
 }
 
 // FP64 stresslet sum, same decomposition, one target per thread.
 __global__ void __launch_bounds__(PAIR_THREADS)
-k_pair64(int N, int ns, int M, int bodies_per_split, const double* __restrict__ tmpl64,
-         const double* __restrict__ centers, const double* __restrict__ phi, double* __restrict__ partial) {
+k_pair64(int N, int ns, Units un, const double* __restrict__ tmpl64, const double* __restrict__ centers,
+         const double* __restrict__ phi, double* __restrict__ partial) {
   extern __shared__ double smd[];
   double* s_t = smd;                       // [ns][6]: xi(3), wn(3)
   double* s_f = s_t + 6 * ns;              // [PAIR_CHUNK][ns][3]
-  const int split = blockIdx.y;
-  const int jb0 = split * bodies_per_split;
-  const int jb1 = min(M, jb0 + bodies_per_split);
   for (int t = threadIdx.x; t < 6 * ns; t += blockDim.x) s_t[t] = tmpl64[8 * (t / 6) + t % 6];
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int pc = p < N ? p : N - 1;
-  const int bi = pc / ns, qi = pc % ns;
-  const double xpx = tmpl64[8 * qi], xpy = tmpl64[8 * qi + 1], xpz = tmpl64[8 * qi + 2];
-  const double cix = centers[3 * bi], ciy = centers[3 * bi + 1], ciz = centers[3 * bi + 2];
-  const double fpx = phi[3 * pc], fpy = phi[3 * pc + 1], fpz = phi[3 * pc + 2];
-  double ax = 0.0, ay = 0.0, az = 0.0;
-  for (int jc = jb0; jc < jb1; jc += PAIR_CHUNK) {
-    const int nb = min(PAIR_CHUNK, jb1 - jc);
-    __syncthreads();
-    const double* src = phi + 3 * (size_t)jc * ns;
-    for (int t = threadIdx.x; t < 3 * nb * ns; t += blockDim.x) s_f[t] = src[t];
-    __syncthreads();
-    for (int b = 0; b < nb; b++) {
-      const int j = jc + b;
-      const double ex = (cix - centers[3 * j]) + xpx;
-      const double ey = (ciy - centers[3 * j + 1]) + xpy;
-      const double ez = (ciz - centers[3 * j + 2]) + xpz;
-      const double* fb = s_f + 3 * b * ns;
+  const int M = un.M;
+  const int c = blockIdx.x;
+  int u = un.start(c);
+  const int uend = un.start(c + 1);
+  while (u < uend) {
+    const int tb = u / M, jb0 = u - tb * M;
+    const int jb1 = min(M, jb0 + (uend - u));
+    const int slot = c - un.first_cta(tb);
+    u += jb1 - jb0;
+    const int p = tb * blockDim.x + threadIdx.x;
+    const int pc = p < N ? p : N - 1;
+    const int bi = pc / ns, qi = pc - bi * ns;
+    const double xpx = tmpl64[8 * qi], xpy = tmpl64[8 * qi + 1], xpz = tmpl64[8 * qi + 2];
+    const double cix = centers[3 * bi], ciy = centers[3 * bi + 1], ciz = centers[3 * bi + 2];
+    const double fpx = phi[3 * pc], fpy = phi[3 * pc + 1], fpz = phi[3 * pc + 2];
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int jc = jb0; jc < jb1; jc += PAIR_CHUNK) {
+      const int nb = min(PAIR_CHUNK, jb1 - jc);
+      __syncthreads();
+      const double* src = phi + 3 * (size_t)jc * ns;
+      for (int t = threadIdx.x; t < 3 * nb * ns; t += blockDim.x) s_f[t] = src[t];
+      __syncthreads();
+      for (int b = 0; b < nb; b++) {
+        const int j = jc + b;
+        const double ex = (cix - centers[3 * j]) + xpx;
+        const double ey = (ciy - centers[3 * j + 1]) + xpy;
+        const double ez = (ciz - centers[3 * j + 2]) + xpz;
+        const double* fb = s_f + 3 * b * ns;
 #pragma unroll 2
-      for (int q = 0; q < ns; q++) {
-        const double* tq = s_t + 6 * q;
-        const double rx = ex - tq[0], ry = ey - tq[1], rz = ez - tq[2];
-        const double r2 = fma(rz, rz, fma(ry, ry, fma(rx, rx, EPS64)));
-        const double ir = rsqrt(r2);
-        const double i2 = ir * ir;
-        const double rn = rx * tq[3] + ry * tq[4] + rz * tq[5];
-        const double dx = fb[3 * q] - fpx, dy = fb[3 * q + 1] - fpy, dz = fb[3 * q + 2] - fpz;
-        const double rd = rx * dx + ry * dy + rz * dz;
-        const double s = ((rn * i2) * (rd * i2)) * ir;
-        ax = fma(s, rx, ax);
-        ay = fma(s, ry, ay);
-        az = fma(s, rz, az);
+        for (int q = 0; q < ns; q++) {
+          const double* tq = s_t + 6 * q;
+          const double rx = ex - tq[0], ry = ey - tq[1], rz = ez - tq[2];
+          const double r2 = fma(rz, rz, fma(ry, ry, fma(rx, rx, EPS64)));
+          const double ir = rsqrt(r2);
+          const double i2 = ir * ir;
+          const double rn = rx * tq[3] + ry * tq[4] + rz * tq[5];
+          const double dx = fb[3 * q] - fpx, dy = fb[3 * q + 1] - fpy, dz = fb[3 * q + 2] - fpz;
+          const double rd = rx * dx + ry * dy + rz * dz;
+          const double s = ((rn * i2) * (rd * i2)) * ir;
+          ax = fma(s, rx, ax);
+          ay = fma(s, ry, ay);
+          az = fma(s, rz, az);
+        }
       }
     }
-  }
-  if (p < N) {
-    double* o = partial + ((size_t)split * N + p) * 3;
-    o[0] = ax;
-    o[1] = ay;
-    o[2] = az;
+    if (p < N) {
+      double* o = partial + ((size_t)slot * N + p) * 3;
+      o[0] = ax;
+      o[1] = ay;
+      o[2] = az;
+    }
   }
 }
 
@@ -346,13 +376,21 @@ __global__ void k_neg(int L, const double* __restrict__ x, double* __restrict__ 
 }
 
 // ------------------------------------------------------------------ host side
-static int pair_splits(const lcp_ctx* ctx) {
-  const int tblocks = (ctx->N + PAIR_THREADS - 1) / PAIR_THREADS;
-  int sm = 152;
-  int want = (4 * sm + tblocks - 1) / tblocks;
-  if (want < 1) want = 1;
-  if (want > ctx->M) want = ctx->M;
-  return want;
+// One full wave of CTAs for a pair kernel: SMs x resident CTAs per SM, capped
+// by the number of (target block, source body) units.
+static int pair_grid(const lcp_ctx* ctx, int precision) {
+  const int units = ((ctx->N + PAIR_THREADS - 1) / PAIR_THREADS) * ctx->M;
+  const int per_sm = precision == LCP_MIXED ? ctx->occ32 : ctx->occ64;
+  int g = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+  return g < units ? g : units;
+}
+
+// Largest number of CTAs that touch one target block (partial slots needed).
+static int pair_slots(const lcp_ctx* ctx, int grid) {
+  const long long units = (long long)((ctx->N + PAIR_THREADS - 1) / PAIR_THREADS) * ctx->M;
+  const long long per = units / grid;   // every CTA holds per or per + 1 units
+  const long long s = (ctx->M + per - 1) / (per > 0 ? per : 1) + 1;
+  return (int)(s < grid ? s : grid);
 }
 
 int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef) {
@@ -365,12 +403,16 @@ int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef) {
 
 int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
   const int N = ctx->N, ns = ctx->ns, M = ctx->M;
-  int splits = pair_splits(ctx);
-  if (splits > ctx->splits) splits = ctx->splits;
-  const int bps = (M + splits - 1) / splits;
-  splits = (M + bps - 1) / bps;
-  dim3 grid((N + PAIR_THREADS - 1) / PAIR_THREADS, splits);
+  const int ntb = (N + PAIR_THREADS - 1) / PAIR_THREADS;
+  const int grid = pair_grid(ctx, precision);
+  const int slots = pair_slots(ctx, grid);
+  if (slots > ctx->splits) {
+    ctx->err = "internal: pair-sum slots exceed the partial buffer";
+    return LCP_ERR_INVALID_ARG;
+  }
+  Units un{ntb * M, grid, M};
   LCP_TRY(stokes_coefs(ctx, phi, ctx->coef));
+  LCP_CUDA(cudaMemsetAsync(ctx->partial, 0, sizeof(double) * 3 * (size_t)N * slots, ctx->stream));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ctx->prof) {
     LCP_CUDA(cudaEventCreate(&e0));
@@ -378,22 +420,23 @@ int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
   }
   if (precision == LCP_MIXED) {
     ++ctx->nlaunch, k_to_f32<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(3 * N, phi, ctx->phi32);
-    if (e0) LCP_CUDA(cudaEventRecord(e0, ctx->stream));
     const int ns_pad = (ns + 3) & ~3;
     const size_t smem = sizeof(float) * (6 * ns_pad + 3 * PAIR_CHUNK * ns_pad);
-    ++ctx->nlaunch, k_pair32<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, ns_pad, M, bps, ctx->tmpl32, ctx->centers32,
-                                                        ctx->phi32, ctx->partial);
+    if (e0) LCP_CUDA(cudaEventRecord(e0, ctx->stream));
+    ++ctx->nlaunch, k_pair32<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, ns_pad, un, ctx->tmpl32,
+                                                                        ctx->centers32, ctx->phi32, ctx->partial);
     if (e1) LCP_CUDA(cudaEventRecord(e1, ctx->stream));
     ctx->c_fp32++;
   } else {
     const size_t smem = sizeof(double) * (6 * ns + 3 * PAIR_CHUNK * ns);
     if (e0) LCP_CUDA(cudaEventRecord(e0, ctx->stream));
-    ++ctx->nlaunch, k_pair64<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, M, bps, ctx->tmpl64, ctx->centers, phi,
-                                                        ctx->partial);
+    ++ctx->nlaunch, k_pair64<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, un, ctx->tmpl64, ctx->centers,
+                                                                        phi, ctx->partial);
     if (e1) LCP_CUDA(cudaEventRecord(e1, ctx->stream));
     ctx->c_fp64++;
   }
-  ++ctx->nlaunch, k_finish<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ns, splits, ctx->partial, ctx->coef, ctx->tmpl64, out);
+  ++ctx->nlaunch, k_finish<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ns, slots, ctx->partial, ctx->coef,
+                                                                     ctx->tmpl64, out);
   LCP_CUDA(cudaGetLastError());
   if (e0) {
     ctx->ev_pool.push_back(e0);
@@ -419,7 +462,12 @@ int stokes_velocity(lcp_ctx* ctx, const double* phi, double* UO) {
   return LCP_OK;
 }
 
-int stokes_max_splits(const lcp_ctx* ctx) { return pair_splits(ctx); }
+// Partial slots to allocate: the larger of the two kernels' needs.
+int stokes_max_splits(const lcp_ctx* ctx) {
+  const int a = pair_slots(ctx, pair_grid(ctx, LCP_MIXED));
+  const int b = pair_slots(ctx, pair_grid(ctx, LCP_FP64));
+  return a > b ? a : b;
+}
 
 size_t stokes_pair_smem(int ns, int precision) {
   const int ns_pad = (ns + 3) & ~3;
@@ -427,9 +475,15 @@ size_t stokes_pair_smem(int ns, int precision) {
                                 : sizeof(double) * (6 * ns + 3 * PAIR_CHUNK * ns);
 }
 
+// Shared-memory limits and one-wave grid sizes (occupancy) of the pair kernels.
 int stokes_configure(lcp_ctx* ctx) {
   const size_t s32 = stokes_pair_smem(ctx->ns, LCP_MIXED), s64 = stokes_pair_smem(ctx->ns, LCP_FP64);
   if (s64 > 48 * 1024) LCP_CUDA(cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
   if (s32 > 48 * 1024) LCP_CUDA(cudaFuncSetAttribute(k_pair32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
+  int dev = 0;
+  LCP_CUDA(cudaGetDevice(&dev));
+  LCP_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occ32, k_pair32, PAIR_THREADS, s32));
+  LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occ64, k_pair64, PAIR_THREADS, s64));
   return LCP_OK;
 }
