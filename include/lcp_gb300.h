@@ -177,6 +177,30 @@ int lcp_stokes_apply_dev(lcp_ctx* ctx, const double* phi, double* out, int preci
 int lcp_stokes_rhs_dev(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs);
 int lcp_rigid_velocity_dev(lcp_ctx* ctx, const double* phi, double* UO);
 
+/* Allocation-free stresslet apply: out = (K + P) phi for n_bodies spheres of
+ * radius `radius` on an n_theta x n_phi grid, with no context and no memory
+ * allocation of any kind (no cudaMalloc, no cudaFree, no library routine that
+ * allocates).  It is meant for callers that cannot allocate GPU memory:
+ * code running inside an allocator or memory-pool callback, hosts that give
+ * the whole device budget to another component, or real-time loops where an
+ * allocation could block or fail.  The paper has no counterpart; it is the
+ * same operator as lcp_stokes_apply_dev.
+ *   centers [M*3], phi [N*3] and out [N*3] are device pointers (FP64), N =
+ *   n_bodies * n_theta * n_phi; precision LCP_FP64 or LCP_MIXED; cuda_stream
+ *   is a cudaStream_t (NULL = legacy default stream).  Returns after the
+ *   result is complete (synchronises that stream).
+ * Limits (the size of a fixed scratch area of about 1.8 MB compiled into the
+ * library, held on every GPU that loads it until the process exits): at most
+ * 128 bodies, 512 nodes per sphere and 16384 nodes in total, n_phi even.
+ * Larger sizes return LCP_ERR_INVALID_ARG; the message is available from
+ * lcp_last_error(NULL).
+ * The first call on a device looks up the scratch area's device address;
+ * make that first call before any stream capture.  All calls share the
+ * scratch area: calls whose GPU work may overlap (other streams or threads
+ * without ordering) race and must be serialised by the caller. */
+int lcp_stokes_apply_noalloc(int n_bodies, int n_theta, int n_phi, double radius, const double* centers,
+                             const double* phi, double* out, int precision, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,7 @@ PROTOTYPES = {
     "lcp_stokes_apply_dev": (_I, [_P, _P, _P, _I]),
     "lcp_stokes_rhs_dev": (_I, [_P, _P, _I, _P]),
     "lcp_rigid_velocity_dev": (_I, [_P, _P, _P]),
+    "lcp_stokes_apply_noalloc": (_I, [_I, _I, _I, ctypes.c_double, _P, _P, _P, _I, _P]),
 }
 
 _lib = None

@@ -44,6 +44,44 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+// Work decomposition shared by both pair kernels.  The N x N pair sum is cut
+// into units (target block tb, source body j); the U = ntb * M units are dealt
+// out in contiguous, equal ranges to a grid of G CTAs sized to one full wave
+// (SMs x resident CTAs per SM), so no CTA waits for a second wave.  A CTA
+// writes one partial per target block it touches into slot
+// (c - first CTA touching tb); the finishing kernel sums the slots in order.
+struct Units {
+  int U, G, M;
+  __device__ __forceinline__ int start(int c) const { return (int)(((long long)c * U) / G); }
+  __device__ __forceinline__ int first_cta(int tb) const {
+    const int u = tb * M;
+    int c = (int)(((long long)u * G) / U);
+    while (c + 1 < G && start(c + 1) <= u) c++;
+    while (c > 0 && start(c) > u) c--;
+    return c;
+  }
+};
+
+// Pair-sum and projection kernels (stokes.cu), launchable from other files.
+__global__ void k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
+                         const float* __restrict__ c32, const float* __restrict__ phi32, double* __restrict__ partial);
+__global__ void k_pair64(int N, int ns, Units un, const double* __restrict__ tmpl64,
+                         const double* __restrict__ centers, const double* __restrict__ phi,
+                         double* __restrict__ partial);
+__global__ void k_moments(int M, int ns, const double* __restrict__ tmpl64, const double* __restrict__ phi,
+                          const double* __restrict__ ginv, double* __restrict__ coef);
+__global__ void k_finish(int N, int ns, int splits, const double* __restrict__ partial,
+                         const double* __restrict__ coef, const double* __restrict__ tmpl64,
+                         double* __restrict__ out);
+__global__ void k_to_f32(int L, const double* __restrict__ x, float* __restrict__ y);
+// Quadrature template and rigid Gram inverse (geometry.cu).
+__global__ void k_template(int nt, int np, double a, double* tmpl64, float* tmpl32, double* tnodes);
+__global__ void k_gram_inverse(int ns, const double* tmpl64, double* ginv);
+__global__ void k_centers32(int M, const double* c, float* c32);
+constexpr int PAIR_THREADS_PUBLIC = 256;     // block size of the pair kernels
+constexpr int PAIR_CHUNK_PUBLIC = 8;         // source bodies staged per tile
+void lcp_set_thread_error(const std::string& msg);
+
 // ------------------------------------------------------------ host side
 struct GmresWork;
 

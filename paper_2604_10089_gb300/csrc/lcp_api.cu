@@ -16,6 +16,8 @@ int pqn_configure(lcp_ctx* ctx, int rmax);
 
 static thread_local std::string g_setup_error;
 
+void lcp_set_thread_error(const std::string& msg) { g_setup_error = msg; }
+
 // b = gap / dt + D^T U_nc (Eq. defAandb)
 __global__ void k_build_b(int n, double inv_dt, const double* gap, const double* dtu, double* b) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;

@@ -16,8 +16,8 @@
 
 namespace {
 
-constexpr int PAIR_THREADS = 256;
-constexpr int PAIR_CHUNK = 8;     // source bodies staged per shared-memory tile
+constexpr int PAIR_THREADS = PAIR_THREADS_PUBLIC;
+constexpr int PAIR_CHUNK = PAIR_CHUNK_PUBLIC;   // source bodies staged per shared-memory tile
 constexpr float EPS32 = 1e-30f;   // r = 0 only for q = p; then rn = rd = 0 and the term is 0
 constexpr double EPS64 = 1e-300;
 
@@ -74,24 +74,6 @@ __device__ __forceinline__ void pair2(const float2 ex, const float2 ey, const fl
 }
 
 }  // namespace
-
-// Work decomposition shared by both pair kernels.  The N x N pair sum is cut
-// into units (target block tb, source body j); the U = ntb * M units are dealt
-// out in contiguous, equal ranges to a grid of G CTAs sized to one full wave
-// (SMs x resident CTAs per SM), so no CTA waits for a second wave.  A CTA
-// writes one partial per target block it touches into slot
-// (c - first CTA touching tb); the finishing kernel sums the slots in order.
-struct Units {
-  int U, G, M;
-  __device__ __forceinline__ int start(int c) const { return (int)(((long long)c * U) / G); }
-  __device__ __forceinline__ int first_cta(int tb) const {
-    const int u = tb * M;
-    int c = (int)(((long long)u * G) / U);
-    while (c + 1 < G && start(c + 1) <= u) c++;
-    while (c > 0 && start(c) > u) c--;
-    return c;
-  }
-};
 
 // FP32 stresslet sum: one target per thread; sources two at a time in packed
 // FP32x2 arithmetic.  Per-body (tile) sums in FP32, Kahan-compensated FP32

@@ -12,8 +12,9 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import (LCP_BI_PQN, LCP_FP64, LCP_HIGH, LCP_LOW_RPY, LCP_MIXED,  # noqa: F401
-                   LCP_MONO_PQN, LCP_OK, LCP_ERR_NOT_CONVERGED, STATUS_NAMES)
+from ._abi import (LCP_BI_PQN, LCP_ERR_CUDA, LCP_ERR_INVALID_ARG, LCP_ERR_NOT_CONVERGED,  # noqa: F401
+                   LCP_ERR_NUMERICAL, LCP_ERR_OOM, LCP_ERR_REJECTED, LCP_ERR_TIMEOUT, LCP_FP64, LCP_HIGH,
+                   LCP_LOW_RPY, LCP_MIXED, LCP_MONO_PQN, LCP_OK, STATUS_NAMES)
 
 
 class LcpError(RuntimeError):
@@ -211,6 +212,14 @@ def lcp_stokes_rhs_dev(ctx, FT, include_slip: bool, rhs) -> None:
 
 def lcp_rigid_velocity_dev(ctx, phi, UO) -> None:
     _check(_lib().lcp_rigid_velocity_dev(ctx, _devptr(phi), _devptr(UO)), ctx)
+
+
+def lcp_stokes_apply_noalloc(n_bodies, n_theta, n_phi, radius, centers, phi, out,
+                             precision: int = LCP_FP64, stream=None) -> None:
+    """Allocation-free (K + P) phi (no context); centers, phi, out are CUDA float64 tensors."""
+    _check(_lib().lcp_stokes_apply_noalloc(int(n_bodies), int(n_theta), int(n_phi), float(radius),
+                                           _devptr(centers), _devptr(phi), _devptr(out), int(precision),
+                                           stream), None)
 
 
 def config_for(instance, precision: int = LCP_FP64, **overrides) -> _abi.lcp_config:
