@@ -69,6 +69,7 @@ typedef struct {
   int memory;               /* quasi-Newton pairs kept (FIFO beyond) */
   int ssn_maxit;            /* semi-smooth Newton iterations per prox */
   double forcing;           /* Bi-PQN subproblem tolerance = max(0.1 tol, forcing * kkt) */
+  int precondition;         /* 1: flexible GMRES with the isolated-sphere block-diagonal inverse */
   void* cuda_stream;        /* cudaStream_t to run on; NULL = the legacy default stream */
 } lcp_config;
 

@@ -32,7 +32,7 @@ class lcp_config(ctypes.Structure):
                 ("gmres_maxit", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("ir_maxit", ctypes.c_int), ("kmax", ctypes.c_int), ("kmax_inner", ctypes.c_int),
                 ("memory", ctypes.c_int), ("ssn_maxit", ctypes.c_int), ("forcing", ctypes.c_double),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("precondition", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
 
 
 class lcp_contact(ctypes.Structure):

@@ -116,6 +116,8 @@ struct lcp_ctx {
   int m = 0, splits = 1;
   int num_sms = 0, occ32 = 0, occ64 = 0;   // pair-kernel grid sizing
   double *V = nullptr, *H = nullptr;  // Krylov basis [(m+1)][3N], Hessenberg etc.
+  double* Z = nullptr;                 // preconditioned basis [m][3N] (flexible GMRES)
+  float* pinv = nullptr;               // isolated-sphere inverse (3 ns x 3 ns, FP32)
   double *phi = nullptr, *rhs = nullptr, *res = nullptr, *wv = nullptr, *dphi = nullptr;
   float* phi32 = nullptr;
   double* partial = nullptr;  // [splits][N][3]
@@ -171,6 +173,8 @@ int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision);
 int stokes_rhs(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs);
 int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef);
 int mobility_solve(lcp_ctx* ctx, const double* FT, int include_slip, double* UO);
+int precond_build(lcp_ctx* ctx);
+int precond_apply(lcp_ctx* ctx, const double* v, double* z);
 int scatter_D(lcp_ctx* ctx, const double* x, double* FT);
 int gather_Dt(lcp_ctx* ctx, const double* UO, double* out, const double* add);
 int rpy_apply(lcp_ctx* ctx, const double* FT, double* UO);

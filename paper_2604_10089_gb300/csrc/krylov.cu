@@ -244,7 +244,10 @@ static int read_status(lcp_ctx* ctx, double* vals, int count) {
   return LCP_OK;
 }
 
-// Restarted GMRES(m) on (K + P) phi = rhs with operator precision `prec`.
+// Restarted GMRES(m) on (K + P) phi = rhs with operator precision `prec`;
+// flexible GMRES (Saad 1993) with the block-diagonal preconditioner when it
+// is enabled: the solution is assembled from the stored preconditioned
+// vectors, so the preconditioner's precision does not limit the accuracy.
 // phi holds the initial guess (zero_init: assume phi = 0 and skip the first
 // residual apply).  Stops when the residual estimate <= tol_abs or after
 // maxit iterations.  Returns the iterations used in *its, the last residual
@@ -287,6 +290,11 @@ static int gmres(lcp_ctx* ctx, const double* rhs, double* phi, int zero_init, do
     for (; j < m; j++) {
       double* vj = ctx->V + (size_t)j * ldv;
       double* vn = ctx->V + (size_t)(j + 1) * ldv;
+      if (ctx->Z) {   // flexible right preconditioning: z_j = Minv v_j, w = A z_j
+        double* zj = ctx->Z + (size_t)j * ldv;
+        LCP_TRY(precond_apply(ctx, vj, zj));
+        vj = zj;
+      }
       LCP_TRY(stokes_apply(ctx, vj, vn, prec));
       total++;
       LCP_TRY(dots(ctx, L, j + 1, ctx->V, ldv, vn, h1));
@@ -302,7 +310,8 @@ static int gmres(lcp_ctx* ctx, const double* rhs, double* phi, int zero_init, do
       if (res <= tol_abs || total >= maxit || st[1] == 0.0) { j++; break; }
     }
     ++ctx->nlaunch, k_gmres_solve<<<1, 1, 0, ctx->stream>>>(base, m, j);
-    ++ctx->nlaunch, k_gmres_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j, ctx->V, ldv, y, phi);
+    ++ctx->nlaunch, k_gmres_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j, ctx->Z ? ctx->Z : ctx->V, ldv,
+                                                                             y, phi);
     LCP_CUDA(cudaGetLastError());
     if (res <= tol_abs || total >= maxit) break;
   }

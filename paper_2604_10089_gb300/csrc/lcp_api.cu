@@ -45,6 +45,7 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->memory = 32;
   c->ssn_maxit = 50;
   c->forcing = 1e-3;
+  c->precondition = 1;
   c->cuda_stream = nullptr;
 }
 
@@ -82,6 +83,10 @@ static int alloc_static(lcp_ctx* ctx) {
   ctx->splits = stokes_max_splits(ctx);
   ctx->dot_blocks = 2 * 152;
   ctx->V = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)L * (ctx->m + 1));
+  if (ctx->cfg.precondition) {
+    ctx->Z = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)L * ctx->m);
+    if (!ctx->Z) return LCP_ERR_OOM;
+  }
   ctx->H = (double*)ctx_alloc(ctx, sizeof(double) * ((size_t)(ctx->m + 1) * ctx->m + 6 * (size_t)ctx->m + 16));
   ctx->phi = (double*)ctx_alloc(ctx, sizeof(double) * L);
   ctx->rhs = (double*)ctx_alloc(ctx, sizeof(double) * L);
@@ -101,6 +106,7 @@ static int alloc_static(lcp_ctx* ctx) {
     return LCP_ERR_OOM;
   }
   LCP_TRY(pqn_configure(ctx, ctx->cfg.memory));
+  if (ctx->cfg.precondition) LCP_TRY(precond_build(ctx));
   return LCP_OK;
 }
 
