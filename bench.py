@@ -174,6 +174,7 @@ def run_ours(args, rank, world, local):
     launches = L.lcp_launch_count(ctx) - launches0
     c32, t32 = L.lcp_profile_read(ctx, 0)
     c64, t64 = L.lcp_profile_read(ctx, 1)
+    cdf, tdf = L.lcp_profile_read(ctx, 2)
     L.lcp_profile(ctx, False)
     if world > 1:
         torch.distributed.barrier()
@@ -243,10 +244,16 @@ def run_ours(args, rank, world, local):
         "e_mvps": [round(s["e_mvps"], 3) for s in stats], "iterations": [s["iterations"] for s in stats],
         "gmres_iterations": [s["gmres_iterations"] for s in stats],
         "fp32_applies": [s["fp32_applies"] for s in stats], "fp64_applies": [s["fp64_applies"] for s in stats],
+        "df64_applies": [s["df64_applies"] for s in stats],
         "kkt_abs": [s["kkt_abs"] for s in stats], "contacts": ncon,
         "converged": all(s["converged"] == 1 for s in stats),
     }
-    return dict(t_total=t_total, lat=lat, clocks=clk, launches=launches, roof=roof, k64=k64, e2e=e2e,
+    kdf = None
+    if cdf:
+        kdf = {"kernel": "k_pair_df", "launches": cdf, "avg_launch_ms": tdf / cdf,
+               "fp32_ops_per_pair_note": "double-FP32 arithmetic, ~250 FP32 operations per pair",
+               "pairs_per_s": pairs / (tdf / cdf / 1e3), "share_of_timed_region": tdf / 1e3 / t_total}
+    return dict(t_total=t_total, lat=lat, clocks=clk, launches=launches, roof=roof, k64=k64, kdf=kdf, e2e=e2e,
                 fp64=fp64, summary=summary, N=N, M=M)
 
 
@@ -335,7 +342,7 @@ def main():
                        "l2": "inputs larger than L2 (Krylov basis 76 MB + operator sweeps per apply)",
                        "parallelism": f"instances x{world}"},
             "latency_s": {"p50": pct(r["lat"], 50), "p99": pct(r["lat"], 99)},
-            "roofline": r["roof"], "fp64_kernel": r["k64"], "clocks": r["clocks"],
+            "roofline": r["roof"], "fp64_kernel": r["k64"], "df64_kernel": r["kdf"], "clocks": r["clocks"],
             "e2e": r["e2e"], "gpu_launches": r["launches"], "cpu_baseline": cpu,
             "fp64_mono_pqn": r["fp64"], "solver": s,
         }

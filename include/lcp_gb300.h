@@ -48,6 +48,7 @@ typedef enum {
 } lcp_status;
 
 enum { LCP_FP64 = 0, LCP_MIXED = 1 };          /* precision of the stresslet sums */
+enum { LCP_DF64 = 2 };                          /* double-FP32 sums (refinement residuals, ~1e-13) */
 enum { LCP_MONO_PQN = 0, LCP_BI_PQN = 1 };     /* Algorithm 1 / Algorithm 4 */
 enum { LCP_HIGH = 0, LCP_LOW_RPY = 1 };        /* mobility fidelity */
 
@@ -70,6 +71,7 @@ typedef struct {
   int ssn_maxit;            /* semi-smooth Newton iterations per prox */
   double forcing;           /* Bi-PQN subproblem tolerance = max(0.1 tol, forcing * kkt) */
   int precondition;         /* 1: flexible GMRES with the isolated-sphere block-diagonal inverse */
+  int residual_precision;   /* LCP_MIXED refinement residuals: LCP_FP64 or LCP_DF64 (default) */
   void* cuda_stream;        /* cudaStream_t to run on; NULL = the legacy default stream */
 } lcp_config;
 
@@ -93,6 +95,7 @@ typedef struct {
   double hi_mvp_seconds;    /* mean wall time of one high-fidelity MVP */
   double lo_mvp_seconds;    /* mean wall time of one low-fidelity MVP */
   double seconds;           /* wall time of the solve */
+  int df64_applies;         /* double-FP32 stresslet applications (refinement residuals) */
 } lcp_stats;
 
 typedef struct lcp_ctx lcp_ctx;   /* opaque, library-owned */
@@ -126,7 +129,7 @@ int lcp_update_dev(lcp_ctx* ctx, const double* centers, const double* axes);
 /* Kernel timing.  lcp_profile(ctx, 1) clears the record and starts timing
  * every stresslet-sum launch with CUDA events on the context's stream;
  * lcp_profile(ctx, 0) stops and clears.  lcp_profile_read returns the number
- * of launches of a kind (0 = FP32 pair sum, 1 = FP64 pair sum) and their
+ * of launches of a kind (0 = FP32, 1 = FP64, 2 = double-FP32 pair sum) and their
  * summed duration in milliseconds (synchronises the stream). */
 int lcp_profile(lcp_ctx* ctx, int enable);
 int lcp_profile_read(lcp_ctx* ctx, int kind, int* count, double* total_ms);
@@ -171,7 +174,8 @@ int lcp_solve_dev(lcp_ctx* ctx, int method, double tol, const double* x0, double
 /* Building blocks of the mobility solve, on device pointers and the context's
  * stream (used by the parity tests):
  *   lcp_stokes_apply_dev: out = (K + P) phi, phi/out [N*3], precision
- *     LCP_FP64 or LCP_MIXED (FP32 pair sums, compensated accumulation);
+ *     LCP_FP64, LCP_MIXED (FP32 pair sums, compensated accumulation) or
+ *     LCP_DF64 (double-FP32 pair sums);
  *   lcp_stokes_rhs_dev: rhs = s - S[F, T] at the nodes, FT [M*6], rhs [N*3];
  *   lcp_rigid_velocity_dev: UO = -(rigid coefficients of P phi), UO [M*6]. */
 int lcp_stokes_apply_dev(lcp_ctx* ctx, const double* phi, double* out, int precision);

@@ -15,7 +15,7 @@ LCP_ERR_NOT_CONVERGED = -4
 LCP_ERR_NUMERICAL = -5
 LCP_ERR_TIMEOUT = -6
 LCP_ERR_REJECTED = -8
-LCP_FP64, LCP_MIXED = 0, 1
+LCP_FP64, LCP_MIXED, LCP_DF64 = 0, 1, 2
 LCP_MONO_PQN, LCP_BI_PQN = 0, 1
 LCP_HIGH, LCP_LOW_RPY = 0, 1
 
@@ -32,7 +32,8 @@ class lcp_config(ctypes.Structure):
                 ("gmres_maxit", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("ir_maxit", ctypes.c_int), ("kmax", ctypes.c_int), ("kmax_inner", ctypes.c_int),
                 ("memory", ctypes.c_int), ("ssn_maxit", ctypes.c_int), ("forcing", ctypes.c_double),
-                ("precondition", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("precondition", ctypes.c_int), ("residual_precision", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class lcp_contact(ctypes.Structure):
@@ -47,7 +48,7 @@ class lcp_stats(ctypes.Structure):
                 ("fp32_applies", ctypes.c_int), ("kkt_abs", ctypes.c_double),
                 ("kkt_dot", ctypes.c_double), ("e_mvps", ctypes.c_double),
                 ("hi_mvp_seconds", ctypes.c_double), ("lo_mvp_seconds", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("df64_applies", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

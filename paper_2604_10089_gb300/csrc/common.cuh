@@ -12,6 +12,7 @@
 
 #define LCP_PI 3.14159265358979323846
 
+
 // ------------------------------------------------------------ reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -114,12 +115,13 @@ struct lcp_ctx {
   double* U_nc = nullptr;     // [M][6]
   // mobility solve workspace
   int m = 0, splits = 1;
-  int num_sms = 0, occ32 = 0, occ64 = 0;   // pair-kernel grid sizing
+  int num_sms = 0, occ32 = 0, occ64 = 0, occdf = 0;   // pair-kernel grid sizing
   double *V = nullptr, *H = nullptr;  // Krylov basis [(m+1)][3N], Hessenberg etc.
   double* Z = nullptr;                 // preconditioned basis [m][3N] (flexible GMRES)
   float* pinv = nullptr;               // isolated-sphere inverse (3 ns x 3 ns, FP32)
   double *phi = nullptr, *rhs = nullptr, *res = nullptr, *wv = nullptr, *dphi = nullptr;
   float* phi32 = nullptr;
+  float* phidf = nullptr;     // [N][6] double-FP32 density (hi xyz, lo xyz)
   double* partial = nullptr;  // [splits][N][3]
   double* coef = nullptr;     // [M][6]
   double* dotp = nullptr;     // dot-product partials
@@ -145,7 +147,7 @@ struct lcp_ctx {
   std::string err;
   unsigned long long nlaunch = 0;   // kernels launched by this context
   // counters of the current solve
-  int c_gmres = 0, c_fp64 = 0, c_fp32 = 0;
+  int c_gmres = 0, c_fp64 = 0, c_fp32 = 0, c_df64 = 0;
 };
 
 #define LCP_CUDA(call)                                                            \

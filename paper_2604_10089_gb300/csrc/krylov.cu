@@ -333,7 +333,7 @@ static int norm2(lcp_ctx* ctx, const double* v, int L, double* out) {
 // FP64: GMRES on the FP64 operator.  MIXED: iterative refinement.  Each sweep
 // solves for a correction d with GMRES on the FP32 operator (FP64 Arnoldi) to
 // inner_tol relative.  The residual after the first sweep is recomputed with
-// the FP64 operator; later residuals are updated, r <- r - (K + P)_32 d, which
+// the high-accuracy operator (FP64 or double-FP32 sums, residual_precision); later residuals are updated, r <- r - (K + P)_32 d, which
 // is accurate to ~eps32 ||K|| ||d|| because those corrections are small (the
 // FP32 operator's relative error eps32 is ~4e-7).  A correction larger than
 // IR_UPDATE_MAX ||phi|| falls back to an FP64 residual.
@@ -371,7 +371,7 @@ int density_solve(lcp_ctx* ctx, const double* rhs, double* phi) {
     LCP_TRY(norm2(ctx, ctx->dphi, L, &dn));
     LCP_TRY(norm2(ctx, phi, L, &pn));
     if (sweep == 0 || dn > IR_UPDATE_MAX * pn) {
-      LCP_TRY(stokes_apply(ctx, phi, ctx->wv, LCP_FP64));
+      LCP_TRY(stokes_apply(ctx, phi, ctx->wv, ctx->cfg.residual_precision));
       ++ctx->nlaunch, k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->wv, ctx->res);
     } else {
       LCP_TRY(stokes_apply(ctx, ctx->dphi, ctx->wv, LCP_MIXED));

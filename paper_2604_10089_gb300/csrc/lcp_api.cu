@@ -46,6 +46,7 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->ssn_maxit = 50;
   c->forcing = 1e-3;
   c->precondition = 1;
+  c->residual_precision = LCP_DF64;
   c->cuda_stream = nullptr;
 }
 
@@ -59,6 +60,7 @@ static int validate(const lcp_config* c, int M, const double* centers, std::stri
     return LCP_ERR_INVALID_ARG;
   }
   if (c->precision != LCP_FP64 && c->precision != LCP_MIXED) { *err = "precision must be LCP_FP64 or LCP_MIXED"; return LCP_ERR_INVALID_ARG; }
+  if (c->residual_precision != LCP_FP64 && c->residual_precision != LCP_DF64) { *err = "residual_precision must be LCP_FP64 or LCP_DF64"; return LCP_ERR_INVALID_ARG; }
   if (c->gmres_restart < 1 || c->gmres_restart > 200 || c->gmres_maxit < 1) { *err = "gmres_restart in [1, 200], gmres_maxit >= 1"; return LCP_ERR_INVALID_ARG; }
   if (c->memory < 1 || c->memory > 60) { *err = "memory in [1, 60]"; return LCP_ERR_INVALID_ARG; }
   if (c->kmax < 1 || c->kmax > 120 || c->kmax_inner < 1) { *err = "kmax in [1, 120], kmax_inner >= 1"; return LCP_ERR_INVALID_ARG; }
@@ -94,6 +96,7 @@ static int alloc_static(lcp_ctx* ctx) {
   ctx->wv = (double*)ctx_alloc(ctx, sizeof(double) * L);
   ctx->dphi = (double*)ctx_alloc(ctx, sizeof(double) * L);
   ctx->phi32 = (float*)ctx_alloc(ctx, sizeof(float) * L);
+  ctx->phidf = (float*)ctx_alloc(ctx, sizeof(float) * 2 * L);
   ctx->partial = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)L * ctx->splits);
   ctx->coef = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->dotp = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)(ctx->m + 2) * ctx->dot_blocks);
@@ -101,7 +104,7 @@ static int alloc_static(lcp_ctx* ctx) {
   ctx->UO = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->U_nc = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   if (!ctx->V || !ctx->H || !ctx->phi || !ctx->rhs || !ctx->res || !ctx->wv || !ctx->dphi || !ctx->phi32 ||
-      !ctx->partial || !ctx->coef || !ctx->dotp || !ctx->FT || !ctx->UO || !ctx->U_nc) {
+      !ctx->partial || !ctx->coef || !ctx->dotp || !ctx->FT || !ctx->UO || !ctx->U_nc || !ctx->phidf) {
     ctx->err = "device allocation failed";
     return LCP_ERR_OOM;
   }
@@ -400,7 +403,7 @@ extern "C" int lcp_solve(lcp_ctx* ctx, int method, double tol, const double* x0,
 
 extern "C" int lcp_stokes_apply_dev(lcp_ctx* ctx, const double* phi, double* out, int precision) {
   if (!ctx || !phi || !out) return LCP_ERR_INVALID_ARG;
-  if (precision != LCP_FP64 && precision != LCP_MIXED) return LCP_ERR_INVALID_ARG;
+  if (precision != LCP_FP64 && precision != LCP_MIXED && precision != LCP_DF64) return LCP_ERR_INVALID_ARG;
   LCP_TRY(stokes_apply(ctx, phi, out, precision));
   LCP_CUDA(cudaStreamSynchronize(ctx->stream));
   return LCP_OK;

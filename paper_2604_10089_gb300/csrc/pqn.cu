@@ -952,7 +952,7 @@ int pqn_configure(lcp_ctx* ctx, int rmax) {
 int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st) {
   const int n = ctx->n;
   const double t_start = now_s();
-  ctx->c_gmres = ctx->c_fp32 = ctx->c_fp64 = 0;
+  ctx->c_gmres = ctx->c_fp32 = ctx->c_fp64 = ctx->c_df64 = 0;
   lcp_stats s{};
   if (n == 0) {
     s.converged = 1;
@@ -1058,6 +1058,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
   s.gmres_iterations = ctx->c_gmres;
   s.fp32_applies = ctx->c_fp32;
   s.fp64_applies = ctx->c_fp64;
+  s.df64_applies = ctx->c_df64;
   s.seconds = now_s() - t_start;
   if (st) *st = s;
   if (!s.converged) {

@@ -179,6 +179,150 @@ k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-FP32 ("double-float") stresslet sum for the refinement residual.
+// Every quantity is an unevaluated sum hi + lo of two floats; sums and
+// products use the error-free transformations TwoSum (Knuth) and TwoProd (one
+// FMA), renormalised with Fast2Sum (Dekker).  Relative accuracy per operation
+// is about 2^-44, so (K phi)_p is accurate to ~1e-13 of its terms while
+// running on the FP32 pipe (64x the FP64 rate on GB300).  The reciprocal
+// square root is a MUFU seed refined by one Newton step in double-float.
+struct dfl {
+  float hi, lo;
+};
+__device__ __forceinline__ dfl df_fast2sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  const float e = __fadd_rn(b, -__fadd_rn(s, -a));
+  return {s, e};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fadd_rn(s, -a.hi);
+  const float e = __fadd_rn(__fadd_rn(a.hi, -__fadd_rn(s, -bb)), __fadd_rn(b.hi, -bb));
+  return df_fast2sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast2sum(p, e);
+}
+__device__ __forceinline__ dfl df_dot3(dfl ax, dfl ay, dfl az, dfl bx, dfl by, dfl bz) {
+  return df_add(df_add(df_mul(ax, bx), df_mul(ay, by)), df_mul(az, bz));
+}
+__device__ __forceinline__ dfl df_split(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(v - (double)h)};
+}
+
+__global__ void k_split_df(int L, const double* __restrict__ x, float* __restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L) return;
+  const int node = t / 3, d = t - 3 * node;
+  const dfl v = df_split(x[t]);
+  y[6 * node + d] = v.hi;
+  y[6 * node + 3 + d] = v.lo;
+}
+
+// Same work decomposition as k_pair32; one target per thread.
+__global__ void __launch_bounds__(PAIR_THREADS)
+k_pair_df(int N, int ns, int ns_pad, Units un, const double* __restrict__ tmpl64,
+          const double* __restrict__ centers, const float* __restrict__ phidf, double* __restrict__ partial) {
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  // 12 template arrays: -xi (hi, lo) x3, wn (hi, lo) x3; then the staged densities
+  float* s_t = sm;                       // [12][ns_pad]
+  float* s_f = s_t + 12 * ns_pad;        // [6][PAIR_CHUNK][ns_pad]: x hi, x lo, y hi, y lo, z hi, z lo
+  for (int q = threadIdx.x; q < ns_pad; q += blockDim.x) {
+    const bool real = q < ns;
+    for (int d = 0; d < 3; d++) {
+      const dfl x = real ? df_split(-tmpl64[8 * q + d]) : dfl{d == 0 ? -1.0e3f : 0.f, 0.f};
+      const dfl w = real ? df_split(tmpl64[8 * q + 3 + d]) : dfl{0.f, 0.f};
+      s_t[(2 * d) * ns_pad + q] = x.hi;
+      s_t[(2 * d + 1) * ns_pad + q] = x.lo;
+      s_t[(6 + 2 * d) * ns_pad + q] = w.hi;
+      s_t[(6 + 2 * d + 1) * ns_pad + q] = w.lo;
+    }
+  }
+  const int M = un.M;
+  const int c = blockIdx.x;
+  int u = un.start(c);
+  const int uend = un.start(c + 1);
+  while (u < uend) {
+    const int tb = u / M, jb0 = u - tb * M;
+    const int jb1 = min(M, jb0 + (uend - u));
+    const int slot = c - un.first_cta(tb);
+    u += jb1 - jb0;
+    const int p = tb * blockDim.x + threadIdx.x;
+    const int pc = p < N ? p : N - 1;
+    const int bi = pc / ns, qi = pc - bi * ns;
+    const double xpx = tmpl64[8 * qi], xpy = tmpl64[8 * qi + 1], xpz = tmpl64[8 * qi + 2];
+    const double cix = centers[3 * bi], ciy = centers[3 * bi + 1], ciz = centers[3 * bi + 2];
+    const float* fp = phidf + 6 * (size_t)pc;
+    const dfl nfx = {-fp[0], -fp[3]}, nfy = {-fp[1], -fp[4]}, nfz = {-fp[2], -fp[5]};
+    dfl ax = {0.f, 0.f}, ay = ax, az = ax;
+    for (int jc = jb0; jc < jb1; jc += PAIR_CHUNK) {
+      const int nb = min(PAIR_CHUNK, jb1 - jc);
+      __syncthreads();
+      const float* src = phidf + 6 * (size_t)jc * ns;
+      for (int t = threadIdx.x; t < 6 * nb * ns; t += blockDim.x) {
+        const int node = t / 6, k = t - 6 * node;         // k: 0..2 hi xyz, 3..5 lo xyz
+        const int b = node / ns, q = node - b * ns;
+        const int comp = k % 3, part = k / 3;
+        s_f[((2 * comp + part) * PAIR_CHUNK + b) * ns_pad + q] = src[t];
+      }
+      for (int t = threadIdx.x; t < nb * (ns_pad - ns); t += blockDim.x) {
+        const int b = t / (ns_pad - ns), q = ns + t % (ns_pad - ns);
+        for (int k = 0; k < 6; k++) s_f[(k * PAIR_CHUNK + b) * ns_pad + q] = 0.f;
+      }
+      __syncthreads();
+      for (int b = 0; b < nb; b++) {
+        const int j = jc + b;
+        const dfl ex = df_split((cix - centers[3 * j]) + xpx);
+        const dfl ey = df_split((ciy - centers[3 * j + 1]) + xpy);
+        const dfl ez = df_split((ciz - centers[3 * j + 2]) + xpz);
+        const float* f = s_f + b * ns_pad;
+        const int fs = PAIR_CHUNK * ns_pad;
+#pragma unroll 1
+        for (int q = 0; q < ns_pad; q++) {
+          const dfl rx = df_add(ex, {s_t[q], s_t[ns_pad + q]});
+          const dfl ry = df_add(ey, {s_t[2 * ns_pad + q], s_t[3 * ns_pad + q]});
+          const dfl rz = df_add(ez, {s_t[4 * ns_pad + q], s_t[5 * ns_pad + q]});
+          const dfl wx = {s_t[6 * ns_pad + q], s_t[7 * ns_pad + q]};
+          const dfl wy = {s_t[8 * ns_pad + q], s_t[9 * ns_pad + q]};
+          const dfl wz = {s_t[10 * ns_pad + q], s_t[11 * ns_pad + q]};
+          dfl r2 = df_dot3(rx, ry, rz, rx, ry, rz);
+          r2 = df_add(r2, {EPS32, 0.f});
+          // ir = 1 / sqrt(r2): y0 from MUFU, one Newton step y0 + y0 (1 - r2 y0^2) / 2
+          const float y0 = rsqrt_approx(r2.hi);
+          const dfl y02 = df_mul({y0, 0.f}, {y0, 0.f});
+          const dfl t = df_mul(r2, y02);
+          const float h = __fadd_rn(__fadd_rn(1.0f, -t.hi), -t.lo);
+          const dfl ir = df_fast2sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), h));
+          const dfl i2 = df_mul(ir, ir);
+          const dfl rn = df_dot3(rx, ry, rz, wx, wy, wz);
+          const dfl dx = df_add({f[q], f[fs + q]}, nfx);
+          const dfl dy = df_add({f[2 * fs + q], f[3 * fs + q]}, nfy);
+          const dfl dz = df_add({f[4 * fs + q], f[5 * fs + q]}, nfz);
+          const dfl rd = df_dot3(rx, ry, rz, dx, dy, dz);
+          const dfl sc = df_mul(df_mul(df_mul(rn, i2), df_mul(rd, i2)), ir);
+          ax = df_add(ax, df_mul(sc, rx));
+          ay = df_add(ay, df_mul(sc, ry));
+          az = df_add(az, df_mul(sc, rz));
+        }
+      }
+    }
+    if (p < N) {
+      double* o = partial + ((size_t)slot * N + p) * 3;
+      o[0] = (double)ax.hi + (double)ax.lo;
+      o[1] = (double)ay.hi + (double)ay.lo;
+      o[2] = (double)az.hi + (double)az.lo;
+    }
+  }
+}
+
 // FP64 stresslet sum, same decomposition, one target per thread.
 __global__ void __launch_bounds__(PAIR_THREADS)
 k_pair64(int N, int ns, Units un, const double* __restrict__ tmpl64, const double* __restrict__ centers,
@@ -358,11 +502,12 @@ __global__ void k_neg(int L, const double* __restrict__ x, double* __restrict__ 
 }
 
 // ------------------------------------------------------------------ host side
+size_t stokes_pair_smem(int ns, int precision);
 // One full wave of CTAs for a pair kernel: SMs x resident CTAs per SM, capped
 // by the number of (target block, source body) units.
 static int pair_grid(const lcp_ctx* ctx, int precision) {
   const int units = ((ctx->N + PAIR_THREADS - 1) / PAIR_THREADS) * ctx->M;
-  const int per_sm = precision == LCP_MIXED ? ctx->occ32 : ctx->occ64;
+  const int per_sm = precision == LCP_MIXED ? ctx->occ32 : (precision == LCP_DF64 ? ctx->occdf : ctx->occ64);
   int g = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
   return g < units ? g : units;
 }
@@ -409,6 +554,15 @@ int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
                                                                         ctx->centers32, ctx->phi32, ctx->partial);
     if (e1) LCP_CUDA(cudaEventRecord(e1, ctx->stream));
     ctx->c_fp32++;
+  } else if (precision == LCP_DF64) {
+    ++ctx->nlaunch, k_split_df<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(3 * N, phi, ctx->phidf);
+    const int ns_pad = (ns + 3) & ~3;
+    const size_t smem = stokes_pair_smem(ns, LCP_DF64);
+    if (e0) LCP_CUDA(cudaEventRecord(e0, ctx->stream));
+    ++ctx->nlaunch, k_pair_df<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, ns_pad, un, ctx->tmpl64,
+                                                                         ctx->centers, ctx->phidf, ctx->partial);
+    if (e1) LCP_CUDA(cudaEventRecord(e1, ctx->stream));
+    ctx->c_df64++;
   } else {
     const size_t smem = sizeof(double) * (6 * ns + 3 * PAIR_CHUNK * ns);
     if (e0) LCP_CUDA(cudaEventRecord(e0, ctx->stream));
@@ -423,7 +577,7 @@ int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
   if (e0) {
     ctx->ev_pool.push_back(e0);
     ctx->ev_pool.push_back(e1);
-    ctx->ev_kind.push_back(precision == LCP_MIXED ? 0 : 1);
+    ctx->ev_kind.push_back(precision == LCP_MIXED ? 0 : (precision == LCP_DF64 ? 2 : 1));
   }
   return LCP_OK;
 }
@@ -446,13 +600,18 @@ int stokes_velocity(lcp_ctx* ctx, const double* phi, double* UO) {
 
 // Partial slots to allocate: the larger of the two kernels' needs.
 int stokes_max_splits(const lcp_ctx* ctx) {
-  const int a = pair_slots(ctx, pair_grid(ctx, LCP_MIXED));
-  const int b = pair_slots(ctx, pair_grid(ctx, LCP_FP64));
-  return a > b ? a : b;
+  int m = 0;
+  const int precs[3] = {LCP_MIXED, LCP_FP64, LCP_DF64};
+  for (int prec : precs) {
+    const int s = pair_slots(ctx, pair_grid(ctx, prec));
+    if (s > m) m = s;
+  }
+  return m;
 }
 
 size_t stokes_pair_smem(int ns, int precision) {
   const int ns_pad = (ns + 3) & ~3;
+  if (precision == LCP_DF64) return sizeof(float) * (12 * ns_pad + 6 * PAIR_CHUNK * ns_pad);
   return precision == LCP_MIXED ? sizeof(float) * (6 * ns_pad + 3 * PAIR_CHUNK * ns_pad)
                                 : sizeof(double) * (6 * ns + 3 * PAIR_CHUNK * ns);
 }
@@ -467,5 +626,8 @@ int stokes_configure(lcp_ctx* ctx) {
   LCP_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev));
   LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occ32, k_pair32, PAIR_THREADS, s32));
   LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occ64, k_pair64, PAIR_THREADS, s64));
+  const size_t sdf = stokes_pair_smem(ctx->ns, LCP_DF64);
+  if (sdf > 48 * 1024) LCP_CUDA(cudaFuncSetAttribute(k_pair_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sdf));
+  LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occdf, k_pair_df, PAIR_THREADS, sdf));
   return LCP_OK;
 }

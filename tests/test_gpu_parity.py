@@ -2,6 +2,7 @@
 
 Tolerances (relative, max-norm over the compared vector):
   FP64 stresslet apply             1e-12   (rounding order only)
+  double-FP32 stresslet apply      1e-12   (~2^-44 per operation)
   FP32 stresslet apply (unrefined) 1e-4    (the mixed-mode bound of the spec; measured ~1e-6)
   mobility solve, FP64 and mixed   1e-9    (GMRES tol 1e-12 on a well-conditioned second-kind system)
   RPY, D, D^T, b                   1e-12 / 1e-9
@@ -49,7 +50,7 @@ def test_contacts_and_b_match_oracle(c1):
     assert rel(L.lcp_get_b(ctx), case["b"]) <= 1e-9
 
 
-@pytest.mark.parametrize("precision,tol", [(L.LCP_FP64, 1e-12), (L.LCP_MIXED, 1e-4)])
+@pytest.mark.parametrize("precision,tol", [(L.LCP_FP64, 1e-12), (L.LCP_MIXED, 1e-4), (L.LCP_DF64, 1e-12)])
 def test_stresslet_apply(c1, precision, tol):
     case, ctx = c1
     mob = case["mob"]
@@ -63,7 +64,7 @@ def test_stresslet_apply(c1, precision, tol):
 
 
 @pytest.mark.parametrize("name,index", [("spheres64_grid9x18", 0)])
-@pytest.mark.parametrize("precision,tol", [(L.LCP_FP64, 1e-12), (L.LCP_MIXED, 1e-4)])
+@pytest.mark.parametrize("precision,tol", [(L.LCP_FP64, 1e-12), (L.LCP_MIXED, 1e-4), (L.LCP_DF64, 1e-12)])
 def test_stresslet_apply_many_tiles(name, index, precision, tol):
     """10 368 nodes: 41 target blocks with a ragged tail and several source splits."""
     inst = make_instance(name, index)
@@ -95,11 +96,12 @@ def test_rhs_and_rigid_velocity(c1):
     assert rel(UO.cpu().numpy(), rigid_velocities(phi, mob.parts)) <= 1e-13
 
 
-@pytest.mark.parametrize("precision", [L.LCP_FP64, L.LCP_MIXED])
-def test_mobility_matches_dense_lu(c1, precision):
+@pytest.mark.parametrize("precision,residual", [(L.LCP_FP64, L.LCP_FP64), (L.LCP_MIXED, L.LCP_DF64),
+                                                (L.LCP_MIXED, L.LCP_FP64)])
+def test_mobility_matches_dense_lu(c1, precision, residual):
     case, _ = c1
     inst, mob = case["inst"], case["mob"]
-    ctx = L.lcp_setup(L.config_for(inst, precision), inst.centers, inst.axes)
+    ctx = L.lcp_setup(L.config_for(inst, precision, residual_precision=residual), inst.centers, inst.axes)
     try:
         FT = np.random.default_rng(7).standard_normal(6 * inst.n_bodies)
         U = L.mobility_apply(ctx, FT, include_slip=False)
