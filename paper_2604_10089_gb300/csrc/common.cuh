@@ -80,6 +80,7 @@ __global__ void k_template(int nt, int np, double a, double* tmpl64, float* tmpl
 __global__ void k_gram_inverse(int ns, const double* tmpl64, double* ginv);
 __global__ void k_centers32(int M, const double* c, float* c32);
 constexpr int PAIR_THREADS_PUBLIC = 256;     // block size of the pair kernels
+constexpr int PAIR32_TARGETS = 512;          // targets per CTA of the FP32 pair kernel (2 per thread)
 constexpr int PAIR_CHUNK_PUBLIC = 8;         // source bodies staged per tile
 void lcp_set_thread_error(const std::string& msg);
 

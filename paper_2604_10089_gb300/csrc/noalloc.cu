@@ -108,7 +108,8 @@ extern "C" int lcp_stokes_apply_noalloc(int n_bodies, int n_theta, int n_phi, do
 
   // grid: at most one wave, and few enough CTAs that no target block is
   // shared by more than NA_SLOTS of them
-  const int ntb = (Ni + PAIR_THREADS_PUBLIC - 1) / PAIR_THREADS_PUBLIC;
+  const int tpb = precision == LCP_MIXED ? PAIR32_TARGETS : PAIR_THREADS_PUBLIC;   // targets per CTA
+  const int ntb = (Ni + tpb - 1) / tpb;
   const int units = ntb * M;
   const int ns_pad = (nsi + 3) & ~3;
   const size_t smem = precision == LCP_MIXED

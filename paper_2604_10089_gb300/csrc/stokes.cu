@@ -26,11 +26,6 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   const float y = v - c;
@@ -39,14 +34,29 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   s = t;
 }
 
-// Two sources (packed in the halves of float2 operands) against one target.
+}  // namespace
+
+// FP32 stresslet sum: two targets per thread (PAIR32_TARGETS per CTA), sources
+// two at a time in packed FP32x2 arithmetic, |r|^-2 as the square of the MUFU
+// reciprocal square root.  Per-body (tile) sums in FP32, Kahan-compensated
+// FP32 across tiles, written as FP64 partials partial[slot][p][3].  ns_pad is
+// ns rounded up to 4; padded sources carry zero weight.
 __device__ __forceinline__ void pair2(const float2 ex, const float2 ey, const float2 ez,
                                       const float2 nfx, const float2 nfy, const float2 nfz,
-                                      const float2 nxq, const float2 nyq, const float2 nzq,
-                                      const float2 wx, const float2 wy, const float2 wz,
-                                      const float2 fx, const float2 fy, const float2 fz,
+                                      const float4& X, const float4& Y, const float4& Z,
+                                      const float4& WX, const float4& WY, const float4& WZ,
+                                      const float4& FX, const float4& FY, const float4& FZ, bool upper,
                                       float2& ax, float2& ay, float2& az) {
   const float2 eps = make_float2(EPS32, EPS32);
+  const float2 nxq = upper ? make_float2(X.z, X.w) : make_float2(X.x, X.y);
+  const float2 nyq = upper ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y);
+  const float2 nzq = upper ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y);
+  const float2 wx = upper ? make_float2(WX.z, WX.w) : make_float2(WX.x, WX.y);
+  const float2 wy = upper ? make_float2(WY.z, WY.w) : make_float2(WY.x, WY.y);
+  const float2 wz = upper ? make_float2(WZ.z, WZ.w) : make_float2(WZ.x, WZ.y);
+  const float2 fx = upper ? make_float2(FX.z, FX.w) : make_float2(FX.x, FX.y);
+  const float2 fy = upper ? make_float2(FY.z, FY.w) : make_float2(FY.x, FY.y);
+  const float2 fz = upper ? make_float2(FZ.z, FZ.w) : make_float2(FZ.x, FZ.y);
   const float2 rx = __fadd2_rn(ex, nxq);
   const float2 ry = __fadd2_rn(ey, nyq);
   const float2 rz = __fadd2_rn(ez, nzq);
@@ -54,7 +64,7 @@ __device__ __forceinline__ void pair2(const float2 ex, const float2 ey, const fl
   r2 = __ffma2_rn(ry, ry, r2);
   r2 = __ffma2_rn(rz, rz, r2);
   const float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-  const float2 i2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+  const float2 i2 = __fmul2_rn(ir, ir);
   float2 rn = __fmul2_rn(rx, wx);
   rn = __ffma2_rn(ry, wy, rn);
   rn = __ffma2_rn(rz, wz, rn);
@@ -64,24 +74,16 @@ __device__ __forceinline__ void pair2(const float2 ex, const float2 ey, const fl
   float2 rd = __fmul2_rn(rx, dx);
   rd = __ffma2_rn(ry, dy, rd);
   rd = __ffma2_rn(rz, dz, rd);
-  const float2 a = __fmul2_rn(rn, i2);
-  const float2 b = __fmul2_rn(rd, i2);
-  const float2 c = __fmul2_rn(a, b);
-  const float2 s = __fmul2_rn(c, ir);
+  const float2 s = __fmul2_rn(__fmul2_rn(__fmul2_rn(rn, i2), __fmul2_rn(rd, i2)), ir);
   ax = __ffma2_rn(s, rx, ax);
   ay = __ffma2_rn(s, ry, ay);
   az = __ffma2_rn(s, rz, az);
 }
 
-}  // namespace
-
-// FP32 stresslet sum: one target per thread; sources two at a time in packed
-// FP32x2 arithmetic.  Per-body (tile) sums in FP32, Kahan-compensated FP32
-// across tiles, written as FP64 partials partial[slot][p][3].  ns_pad is ns
-// rounded up to 4; padded sources carry zero weight.
-__global__ void __launch_bounds__(PAIR_THREADS)
+__global__ void __launch_bounds__(PAIR_THREADS, 2)
 k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
          const float* __restrict__ c32, const float* __restrict__ phi32, double* __restrict__ partial) {
+  constexpr int TPT = PAIR32_TARGETS / PAIR_THREADS;
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
   float* s_nx = sm;                    // -xi, per template node (padded)
@@ -110,15 +112,29 @@ k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
     const int jb1 = min(M, jb0 + (uend - u));
     const int slot = c - un.first_cta(tb);
     u += jb1 - jb0;
-    const int p = tb * blockDim.x + threadIdx.x;
-    const int pc = p < N ? p : N - 1;
-    const int bi = pc / ns, qi = pc - bi * ns;
-    const float xpx = tmpl32[qi], xpy = tmpl32[ns + qi], xpz = tmpl32[2 * ns + qi];
-    const float4 cih = *reinterpret_cast<const float4*>(c32 + 8 * bi);
-    const float4 cil = *reinterpret_cast<const float4*>(c32 + 8 * bi + 4);
-    const float fpx = phi32[3 * pc], fpy = phi32[3 * pc + 1], fpz = phi32[3 * pc + 2];
-    const float2 nfx = make_float2(-fpx, -fpx), nfy = make_float2(-fpy, -fpy), nfz = make_float2(-fpz, -fpz);
-    float sx = 0.f, sy = 0.f, sz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+    int pp[TPT];
+    float xp[TPT][3];
+    float4 cih[TPT], cil[TPT];
+    float2 nf[TPT][3];
+    float sacc[TPT][3], kacc[TPT][3];
+#pragma unroll
+    for (int t = 0; t < TPT; t++) {
+      const int p = tb * PAIR32_TARGETS + t * PAIR_THREADS + threadIdx.x;
+      pp[t] = p;
+      const int pc = p < N ? p : N - 1;
+      const int bi = pc / ns, qi = pc - bi * ns;
+      xp[t][0] = tmpl32[qi];
+      xp[t][1] = tmpl32[ns + qi];
+      xp[t][2] = tmpl32[2 * ns + qi];
+      cih[t] = *reinterpret_cast<const float4*>(c32 + 8 * bi);
+      cil[t] = *reinterpret_cast<const float4*>(c32 + 8 * bi + 4);
+      for (int d = 0; d < 3; d++) {
+        const float f = phi32[3 * pc + d];
+        nf[t][d] = make_float2(-f, -f);
+        sacc[t][d] = 0.f;
+        kacc[t][d] = 0.f;
+      }
+    }
     for (int jc = jb0; jc < jb1; jc += PAIR_CHUNK) {
       const int nb = min(PAIR_CHUNK, jb1 - jc);
       __syncthreads();
@@ -139,14 +155,23 @@ k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
         const int j = jc + b;
         const float4 cjh = *reinterpret_cast<const float4*>(c32 + 8 * j);
         const float4 cjl = *reinterpret_cast<const float4*>(c32 + 8 * j + 4);
-        const float ex1 = ((cih.x - cjh.x) + (cil.x - cjl.x)) + xpx;
-        const float ey1 = ((cih.y - cjh.y) + (cil.y - cjl.y)) + xpy;
-        const float ez1 = ((cih.z - cjh.z) + (cil.z - cjl.z)) + xpz;
-        const float2 ex = make_float2(ex1, ex1), ey = make_float2(ey1, ey1), ez = make_float2(ez1, ez1);
+        float2 e[TPT][3];
+#pragma unroll
+        for (int t = 0; t < TPT; t++) {
+          const float ex = ((cih[t].x - cjh.x) + (cil[t].x - cjl.x)) + xp[t][0];
+          const float ey = ((cih[t].y - cjh.y) + (cil[t].y - cjl.y)) + xp[t][1];
+          const float ez = ((cih[t].z - cjh.z) + (cil[t].z - cjl.z)) + xp[t][2];
+          e[t][0] = make_float2(ex, ex);
+          e[t][1] = make_float2(ey, ey);
+          e[t][2] = make_float2(ez, ez);
+        }
         const float* fxb = s_f + (0 * PAIR_CHUNK + b) * ns_pad;
         const float* fyb = s_f + (1 * PAIR_CHUNK + b) * ns_pad;
         const float* fzb = s_f + (2 * PAIR_CHUNK + b) * ns_pad;
-        float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+        float2 acc[TPT][3];
+#pragma unroll
+        for (int t = 0; t < TPT; t++)
+          for (int d = 0; d < 3; d++) acc[t][d] = make_float2(0.f, 0.f);
 #pragma unroll 1
         for (int q = 0; q < ns_pad; q += 4) {
           const float4 X = *reinterpret_cast<const float4*>(s_nx + q);
@@ -158,24 +183,25 @@ k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
           const float4 FX = *reinterpret_cast<const float4*>(fxb + q);
           const float4 FY = *reinterpret_cast<const float4*>(fyb + q);
           const float4 FZ = *reinterpret_cast<const float4*>(fzb + q);
-          pair2(ex, ey, ez, nfx, nfy, nfz, make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
-                make_float2(WX.x, WX.y), make_float2(WY.x, WY.y), make_float2(WZ.x, WZ.y),
-                make_float2(FX.x, FX.y), make_float2(FY.x, FY.y), make_float2(FZ.x, FZ.y), ax, ay, az);
-          pair2(ex, ey, ez, nfx, nfy, nfz, make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
-                make_float2(WX.z, WX.w), make_float2(WY.z, WY.w), make_float2(WZ.z, WZ.w),
-                make_float2(FX.z, FX.w), make_float2(FY.z, FY.w), make_float2(FZ.z, FZ.w), ax, ay, az);
+#pragma unroll
+          for (int t = 0; t < TPT; t++) {
+            pair2(e[t][0], e[t][1], e[t][2], nf[t][0], nf[t][1], nf[t][2], X, Y, Z, WX, WY, WZ, FX, FY, FZ, false,
+                  acc[t][0], acc[t][1], acc[t][2]);
+            pair2(e[t][0], e[t][1], e[t][2], nf[t][0], nf[t][1], nf[t][2], X, Y, Z, WX, WY, WZ, FX, FY, FZ, true,
+                  acc[t][0], acc[t][1], acc[t][2]);
+          }
         }
-        kahan_add(sx, kx, ax.x + ax.y);
-        kahan_add(sy, ky, ay.x + ay.y);
-        kahan_add(sz, kz, az.x + az.y);
+#pragma unroll
+        for (int t = 0; t < TPT; t++)
+          for (int d = 0; d < 3; d++) kahan_add(sacc[t][d], kacc[t][d], acc[t][d].x + acc[t][d].y);
       }
     }
-    if (p < N) {
-      double* o = partial + ((size_t)slot * N + p) * 3;
-      o[0] = (double)sx - (double)kx;
-      o[1] = (double)sy - (double)ky;
-      o[2] = (double)sz - (double)kz;
-    }
+#pragma unroll
+    for (int t = 0; t < TPT; t++)
+      if (pp[t] < N) {
+        double* o = partial + ((size_t)slot * N + pp[t]) * 3;
+        for (int d = 0; d < 3; d++) o[d] = (double)sacc[t][d] - (double)kacc[t][d];
+      }
   }
 }
 
@@ -505,16 +531,20 @@ __global__ void k_neg(int L, const double* __restrict__ x, double* __restrict__ 
 size_t stokes_pair_smem(int ns, int precision);
 // One full wave of CTAs for a pair kernel: SMs x resident CTAs per SM, capped
 // by the number of (target block, source body) units.
+static int pair_targets(int precision) { return precision == LCP_MIXED ? PAIR32_TARGETS : PAIR_THREADS; }
+
 static int pair_grid(const lcp_ctx* ctx, int precision) {
-  const int units = ((ctx->N + PAIR_THREADS - 1) / PAIR_THREADS) * ctx->M;
+  const int tpb = pair_targets(precision);
+  const int units = ((ctx->N + tpb - 1) / tpb) * ctx->M;
   const int per_sm = precision == LCP_MIXED ? ctx->occ32 : (precision == LCP_DF64 ? ctx->occdf : ctx->occ64);
   int g = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
   return g < units ? g : units;
 }
 
 // Largest number of CTAs that touch one target block (partial slots needed).
-static int pair_slots(const lcp_ctx* ctx, int grid) {
-  const long long units = (long long)((ctx->N + PAIR_THREADS - 1) / PAIR_THREADS) * ctx->M;
+static int pair_slots(const lcp_ctx* ctx, int grid, int precision) {
+  const int tpb = pair_targets(precision);
+  const long long units = (long long)((ctx->N + tpb - 1) / tpb) * ctx->M;
   const long long per = units / grid;   // every CTA holds per or per + 1 units
   const long long s = (ctx->M + per - 1) / (per > 0 ? per : 1) + 1;
   return (int)(s < grid ? s : grid);
@@ -530,9 +560,9 @@ int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef) {
 
 int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
   const int N = ctx->N, ns = ctx->ns, M = ctx->M;
-  const int ntb = (N + PAIR_THREADS - 1) / PAIR_THREADS;
+  const int ntb = (N + pair_targets(precision) - 1) / pair_targets(precision);
   const int grid = pair_grid(ctx, precision);
-  const int slots = pair_slots(ctx, grid);
+  const int slots = pair_slots(ctx, grid, precision);
   if (slots > ctx->splits) {
     ctx->err = "internal: pair-sum slots exceed the partial buffer";
     return LCP_ERR_INVALID_ARG;
@@ -603,7 +633,7 @@ int stokes_max_splits(const lcp_ctx* ctx) {
   int m = 0;
   const int precs[3] = {LCP_MIXED, LCP_FP64, LCP_DF64};
   for (int prec : precs) {
-    const int s = pair_slots(ctx, pair_grid(ctx, prec));
+    const int s = pair_slots(ctx, pair_grid(ctx, prec), prec);
     if (s > m) m = s;
   }
   return m;
