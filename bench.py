@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--fp64-compare", type=int, default=1)
     p.add_argument("--cpu-baseline", type=int, default=1)
     p.add_argument("--e2e", type=int, default=1)
+    p.add_argument("--trajectory", type=int, default=0,
+                   help="also time this many forward-Euler steps (solve + lcp_step) of one configuration")
     return p.parse_args()
 
 
@@ -220,6 +222,26 @@ def run_ours(args, rank, world, local):
                 "max_abs_diff_vs_ours": float(np.abs(xm - x64).max()),
                 "same_active_set": bool(np.array_equal(xm > thr, x64 > thr)),
                 "kkt_fp64": st64["kkt_abs"], "kkt_ours": stm["kkt_abs"]}
+    traj = None
+    if args.trajectory and rank == 0:
+        inst = insts[args.warmup]
+        L.lcp_update(ctx, inst.centers, inst.axes)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hi = lo = 0
+        kkts, ncs = [], []
+        for _ in range(args.trajectory):
+            _, st, _ = L.lcp_solve(ctx, method, tol)
+            hi += st["hi_mvps"]
+            lo += st["lo_mvps"]
+            kkts.append(st["kkt_abs"])
+            ncs.append(L.lcp_sizes(ctx)[2])
+            L.lcp_step(ctx, inst.dt)
+        torch.cuda.synchronize()
+        tt = time.perf_counter() - t0
+        traj = {"steps": args.trajectory, "dt": inst.dt, "seconds": tt, "steps_per_s": args.trajectory / tt,
+                "hi_mvps_per_step": hi / args.trajectory, "lo_mvps_per_step": lo / args.trajectory,
+                "max_kkt": max(kkts), "contacts_first_last": [ncs[0], ncs[-1]]}
     L.lcp_destroy(ctx)
 
     pairs = float(N) * (N - 1)
@@ -253,7 +275,7 @@ def run_ours(args, rank, world, local):
         kdf = {"kernel": "k_pair_df", "launches": cdf, "avg_launch_ms": tdf / cdf,
                "fp32_ops_per_pair_note": "double-FP32 arithmetic, ~250 FP32 operations per pair",
                "pairs_per_s": pairs / (tdf / cdf / 1e3), "share_of_timed_region": tdf / 1e3 / t_total}
-    return dict(t_total=t_total, lat=lat, clocks=clk, launches=launches, roof=roof, k64=k64, kdf=kdf, e2e=e2e,
+    return dict(t_total=t_total, lat=lat, clocks=clk, launches=launches, roof=roof, k64=k64, kdf=kdf, e2e=e2e, traj=traj,
                 fp64=fp64, summary=summary, N=N, M=M)
 
 
@@ -344,7 +366,7 @@ def main():
             "latency_s": {"p50": pct(r["lat"], 50), "p99": pct(r["lat"], 99)},
             "roofline": r["roof"], "fp64_kernel": r["k64"], "df64_kernel": r["kdf"], "clocks": r["clocks"],
             "e2e": r["e2e"], "gpu_launches": r["launches"], "cpu_baseline": cpu,
-            "fp64_mono_pqn": r["fp64"], "solver": s,
+            "fp64_mono_pqn": r["fp64"], "trajectory": r["traj"], "solver": s,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -126,6 +126,14 @@ int lcp_update(lcp_ctx* ctx, const double* centers, const double* axes, int n_co
  * always detected. */
 int lcp_update_dev(lcp_ctx* ctx, const double* centers, const double* axes);
 
+/* One forward Euler step of Eq. (dvi) after lcp_solve: body velocities
+ * U = U_nc + M D x (M D x accumulated during the solve with the same MVP reuse
+ * as the gradient, so no extra mobility solve), centres c += dt U, Janus axes
+ * rotated by the angle |Omega| dt about Omega; then the context is
+ * re-configured for the new positions (contacts, D, U_nc, b) as by lcp_update.
+ * centers_out [M*3] / axes_out [M*3]: optional host copies of the new state. */
+int lcp_step(lcp_ctx* ctx, double dt, double* centers_out, double* axes_out);
+
 /* Kernel timing.  lcp_profile(ctx, 1) clears the record and starts timing
  * every stresslet-sum launch with CUDA events on the context's stream;
  * lcp_profile(ctx, 0) stops and clears.  lcp_profile_read returns the number

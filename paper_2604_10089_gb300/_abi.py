@@ -65,6 +65,7 @@ PROTOTYPES = {
     "lcp_destroy": (None, [_P]),
     "lcp_update": (_I, [_P, _D, _D, _I, ctypes.POINTER(lcp_contact)]),
     "lcp_update_dev": (_I, [_P, _P, _P]),
+    "lcp_step": (_I, [_P, ctypes.c_double, _D, _D]),
     "lcp_profile": (_I, [_P, _I]),
     "lcp_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "lcp_profile_read": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),

@@ -114,6 +114,9 @@ struct lcp_ctx {
   int *bc_ptr = nullptr, *bc_idx = nullptr;
   int *flags = nullptr, *csr_cnt = nullptr;
   double* U_nc = nullptr;     // [M][6]
+  double* MDx = nullptr;      // [M][6] collisional velocities M D x of the last solve
+  double *cnext = nullptr, *anext = nullptr;   // [M][3] advanced centres / axes
+  bool have_solution = false;
   // mobility solve workspace
   int m = 0, splits = 1;
   int num_sms = 0, occ32 = 0, occ64 = 0, occdf = 0;   // pair-kernel grid sizing

@@ -15,6 +15,7 @@ int stokes_velocity(lcp_ctx* ctx, const double* phi, double* UO);
 int pqn_configure(lcp_ctx* ctx, int rmax);
 
 static thread_local std::string g_setup_error;
+static int copy_out(lcp_ctx* ctx, double* host, const double* dev, size_t count);
 
 void lcp_set_thread_error(const std::string& msg) { g_setup_error = msg; }
 
@@ -103,6 +104,10 @@ static int alloc_static(lcp_ctx* ctx) {
   ctx->FT = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->UO = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->U_nc = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
+  ctx->MDx = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
+  ctx->cnext = (double*)ctx_alloc(ctx, sizeof(double) * 3 * M);
+  ctx->anext = (double*)ctx_alloc(ctx, sizeof(double) * 3 * M);
+  if (!ctx->MDx || !ctx->cnext || !ctx->anext) return LCP_ERR_OOM;
   if (!ctx->V || !ctx->H || !ctx->phi || !ctx->rhs || !ctx->res || !ctx->wv || !ctx->dphi || !ctx->phi32 ||
       !ctx->partial || !ctx->coef || !ctx->dotp || !ctx->FT || !ctx->UO || !ctx->U_nc || !ctx->phidf) {
     ctx->err = "device allocation failed";
@@ -215,6 +220,51 @@ extern "C" int lcp_update(lcp_ctx* ctx, const double* centers, const double* axe
 extern "C" int lcp_update_dev(lcp_ctx* ctx, const double* centers, const double* axes) {
   if (!ctx || !centers) return LCP_ERR_INVALID_ARG;
   return configure(ctx, centers, axes, 0, nullptr, true);
+}
+
+// Forward Euler step of Eq. (dvi): U = U_nc + M D x; c += dt U; Janus axis
+// rotated by the angle |Omega| dt about Omega (Rodrigues' formula).
+__global__ void k_advance(int M, double dt, const double* __restrict__ c, const double* __restrict__ e,
+                          const double* __restrict__ unc, const double* __restrict__ mdx, int has_axes,
+                          double* __restrict__ cn, double* __restrict__ en) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double u[6];
+  for (int k = 0; k < 6; k++) u[k] = unc[6 * i + k] + mdx[6 * i + k];
+  for (int d = 0; d < 3; d++) cn[3 * i + d] = c[3 * i + d] + dt * u[d];
+  if (!has_axes) return;
+  const double wx = u[3], wy = u[4], wz = u[5];
+  const double wn = sqrt(wx * wx + wy * wy + wz * wz);
+  double ex = e[3 * i], ey = e[3 * i + 1], ez = e[3 * i + 2];
+  if (wn > 0.0) {
+    const double th = wn * dt, kx = wx / wn, ky = wy / wn, kz = wz / wn;
+    const double ct = cos(th), st = sin(th), kd = kx * ex + ky * ey + kz * ez;
+    const double cx = ky * ez - kz * ey, cy = kz * ex - kx * ez, cz = kx * ey - ky * ex;
+    const double nx = ex * ct + cx * st + kx * kd * (1.0 - ct);
+    const double ny = ey * ct + cy * st + ky * kd * (1.0 - ct);
+    const double nz = ez * ct + cz * st + kz * kd * (1.0 - ct);
+    const double nn = sqrt(nx * nx + ny * ny + nz * nz);
+    ex = nx / nn;
+    ey = ny / nn;
+    ez = nz / nn;
+  }
+  en[3 * i] = ex;
+  en[3 * i + 1] = ey;
+  en[3 * i + 2] = ez;
+}
+
+extern "C" int lcp_step(lcp_ctx* ctx, double dt, double* centers_out, double* axes_out) {
+  if (!ctx || !(dt > 0.0)) return LCP_ERR_INVALID_ARG;
+  if (!ctx->have_solution) { ctx->err = "lcp_step needs a solved LCP (call lcp_solve first)"; return LCP_ERR_INVALID_ARG; }
+  const int M = ctx->M;
+  ++ctx->nlaunch, k_advance<<<(M + 127) / 128, 128, 0, ctx->stream>>>(M, dt, ctx->centers, ctx->axes, ctx->U_nc,
+                                                                     ctx->MDx, ctx->has_axes, ctx->cnext, ctx->anext);
+  LCP_CUDA(cudaGetLastError());
+  LCP_TRY(configure(ctx, ctx->cnext, ctx->has_axes ? ctx->anext : nullptr, 0, nullptr, true));
+  ctx->have_solution = false;
+  if (centers_out) LCP_TRY(copy_out(ctx, centers_out, ctx->centers, 3 * (size_t)M));
+  if (axes_out && ctx->has_axes) LCP_TRY(copy_out(ctx, axes_out, ctx->axes, 3 * (size_t)M));
+  return LCP_OK;
 }
 
 // Kernel timing: CUDA events around every stresslet-sum launch while enabled.

@@ -792,6 +792,16 @@ __global__ void __launch_bounds__(PQN_T) k_bi_direction(PqnDev out, const double
   }
 }
 
+// M D x accumulated with the same over-relaxation as the gradient (the MVP
+// reuse of Sec. 4 applied to the 6M body velocities): init copies, else adds
+// eta * (M D p) with eta read from the PQN scalars.
+__global__ void k_mdx(int m6, const double* __restrict__ uo, const double* __restrict__ scal, int init,
+                      double* __restrict__ mdx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m6) return;
+  mdx[i] = init ? uo[i] : mdx[i] + scal[S_ETA] * uo[i];
+}
+
 __global__ void k_copy(int n, const double* a, double* b) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = a[i];
@@ -898,6 +908,8 @@ struct RunStats {
 // A x + b; mode 1: Bi-PQN subproblem (MVP = B^(k), g0 given, extra tracked).
 static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* b, const double* g0, double tol,
                     int kmax, RunStats* rs) {
+  const bool track = !sub && mvp == mvp_high;   // body velocities M D x for the time step
+  const int m6 = 6 * ctx->M;
   PqnWork wk = work_of(ctx, pq);
   double sc[S_NSCAL];
   const size_t smem = prox_smem_bytes(pq.rmax);
@@ -905,6 +917,7 @@ static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* 
   if (!sub) {
     t0 = now_s();
     LCP_TRY(mvp(ctx, pq.x, pq.Ap));
+    if (track) ++ctx->nlaunch, k_mdx<<<(m6 + 127) / 128, 128, 0, ctx->stream>>>(m6, ctx->UO, pq.scal, 1, ctx->MDx);
     LCP_CUDA(cudaStreamSynchronize(ctx->stream));
     rs->t_mvp += now_s() - t0;
     rs->mvps++;
@@ -932,6 +945,7 @@ static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* 
     rs->t_mvp += now_s() - t0;
     rs->mvps++;
     ++ctx->nlaunch, k_pqn_step<<<1, PQN_T, 0, ctx->stream>>>(pq, wk, sub, 1);
+    if (track) ++ctx->nlaunch, k_mdx<<<(m6 + 127) / 128, 128, 0, ctx->stream>>>(m6, ctx->UO, pq.scal, 0, ctx->MDx);
     LCP_CUDA(cudaGetLastError());
     LCP_TRY(read_scal(ctx, pq, sc));
   }
@@ -955,10 +969,13 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
   ctx->c_gmres = ctx->c_fp32 = ctx->c_fp64 = ctx->c_df64 = 0;
   lcp_stats s{};
   if (n == 0) {
+    LCP_CUDA(cudaMemsetAsync(ctx->MDx, 0, sizeof(double) * 6 * ctx->M, ctx->stream));
+    ctx->have_solution = true;
     s.converged = 1;
     if (st) *st = s;
     return LCP_OK;
   }
+  ctx->have_solution = false;
   PqnDev& po = ctx->pq_outer;
   PqnDev& pi = ctx->pq_inner;
   const int T = 256;
@@ -993,6 +1010,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
     ++ctx->nlaunch, k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, pi.x, po.x);
     double t0 = now_s();
     LCP_TRY(mvp_high(ctx, po.x, po.Ap));
+    ++ctx->nlaunch, k_mdx<<<(6 * ctx->M + 127) / 128, 128, 0, ctx->stream>>>(6 * ctx->M, ctx->UO, po.scal, 1, ctx->MDx);
     LCP_CUDA(cudaStreamSynchronize(ctx->stream));
     t_hi += now_s() - t0;
     hi++;
@@ -1032,6 +1050,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
       t_hi += now_s() - t0;
       hi++;
       ++ctx->nlaunch, k_bi_outer<<<1, PQN_T, 0, ctx->stream>>>(po, pi, wk_in, ctx->Uh, ctx->Vh, nh_dev, ctx->cfg.kmax, ahs);
+      ++ctx->nlaunch, k_mdx<<<(6 * ctx->M + 127) / 128, 128, 0, ctx->stream>>>(6 * ctx->M, ctx->UO, po.scal, 0, ctx->MDx);
       LCP_CUDA(cudaGetLastError());
       int nh_host = 0;
       LCP_CUDA(cudaMemcpyAsync(&nh_host, nh_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1061,6 +1080,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
   s.df64_applies = ctx->c_df64;
   s.seconds = now_s() - t_start;
   if (st) *st = s;
+  ctx->have_solution = true;
   if (!s.converged) {
     ctx->err = "PQN reached its iteration limit";
     status = LCP_ERR_NOT_CONVERGED;

@@ -102,6 +102,15 @@ def lcp_update_dev(ctx, centers, axes=None) -> None:
     _check(_lib().lcp_update_dev(ctx, _devptr(centers), _devptr(axes)), ctx)
 
 
+def lcp_step(ctx, dt: float):
+    """Advance the configuration by one time step; returns the new (centers, axes)."""
+    M, _, _ = lcp_sizes(ctx)
+    c = np.empty(3 * M)
+    a = np.empty(3 * M)
+    _check(_lib().lcp_step(ctx, float(dt), _dptr(c), _dptr(a)), ctx)
+    return c.reshape(M, 3), a.reshape(M, 3)
+
+
 def lcp_profile(ctx, enable: bool) -> None:
     _check(_lib().lcp_profile(ctx, int(enable)), ctx)
 

@@ -219,3 +219,56 @@ def test_invalid_arguments_are_rejected():
         L.lcp_setup(L.lcp_default_config(n_phi=13), [[0, 0, 0]])
     with pytest.raises(L.LcpError):
         L.lcp_setup(L.lcp_default_config(contact_radius=0.5), [[0, 0, 0]])
+
+
+def _rotate(e, w, dt):
+    th = np.linalg.norm(w) * dt
+    if th == 0.0:
+        return e
+    k = w / np.linalg.norm(w)
+    out = e * np.cos(th) + np.cross(k, e) * np.sin(th) + k * (k @ e) * (1 - np.cos(th))
+    return out / np.linalg.norm(out)
+
+
+@pytest.mark.parametrize("method", [L.LCP_MONO_PQN, L.LCP_BI_PQN])
+def test_time_step_matches_oracle(method):
+    """Eq. (dvi): c += dt (U_nc + M D x); the next configuration's b matches the oracle's."""
+    case = dense_case("spheres8_grid7x14", 4)
+    inst = case["inst"]
+    ctx = L.lcp_setup(L.config_for(inst), inst.centers, inst.axes)
+    try:
+        x, _, _ = L.lcp_solve(ctx, method, inst.tol)
+        c_new, a_new = L.lcp_step(ctx, inst.dt)
+        U = (case["U_nc"] + case["Mob"] @ (case["D"] @ x)).reshape(-1, 6)
+        c_ref = inst.centers + inst.dt * U[:, :3]
+        a_ref = np.array([_rotate(inst.axes[i], U[i, 3:], inst.dt) for i in range(inst.n_bodies)])
+        np.testing.assert_allclose(c_new, c_ref, atol=1e-12 + 1e-9 * inst.dt * np.abs(U[:, :3]).max())
+        np.testing.assert_allclose(a_new, a_ref, atol=1e-10)
+        # the context now holds the next LCP
+        from oracle.contacts import contact_matrix, detect_contacts
+        from oracle.lcp import lcp_data
+        mob = DenseMobility(c_ref, inst.n_theta, inst.n_phi, a=inst.radius)
+        pairs, normals, gaps = detect_contacts(c_ref, inst.contact_radius, inst.delta)
+        D = contact_matrix(inst.n_bodies, pairs, normals)
+        _, b_next = lcp_data(D, np.eye(6 * inst.n_bodies), mob.apply(np.zeros(6 * inst.n_bodies), axes=a_ref),
+                             gaps, inst.dt)
+        assert rel(L.lcp_get_b(ctx), b_next) <= 1e-8
+        with pytest.raises(L.LcpError):
+            L.lcp_step(ctx, inst.dt)          # no solve since the last step
+    finally:
+        L.lcp_destroy(ctx)
+
+
+def test_short_trajectory_mixed_bi_pqn():
+    inst = make_instance("spheres8_grid7x14", 2)
+    ctx = L.lcp_setup(L.config_for(inst, L.LCP_MIXED), inst.centers, inst.axes)
+    try:
+        for _ in range(5):
+            x, st, _ = L.lcp_solve(ctx, L.LCP_BI_PQN, inst.tol)
+            assert st["converged"] == 1
+            c, a = L.lcp_step(ctx, inst.dt)
+        d = np.linalg.norm(c[:, None] - c[None], axis=2) + np.eye(len(c)) * 10
+        assert d.min() - 2 * inst.contact_radius > -1e-3      # contacts resolved: no deep overlap
+        np.testing.assert_allclose(np.linalg.norm(a, axis=1), 1.0, rtol=1e-12)
+    finally:
+        L.lcp_destroy(ctx)
