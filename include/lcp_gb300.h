@@ -72,6 +72,8 @@ typedef struct {
   double forcing;           /* Bi-PQN subproblem tolerance = max(0.1 tol, forcing * kkt) */
   int precondition;         /* 1: flexible GMRES with the isolated-sphere block-diagonal inverse */
   int residual_precision;   /* LCP_MIXED refinement residuals: LCP_FP64 or LCP_DF64 (default) */
+  int autotune;             /* 1: time the FP32 pair-kernel variants at set-up, keep the fastest per size class */
+  int own_stream;           /* 1: the context creates (and destroys) its own non-blocking stream */
   void* cuda_stream;        /* cudaStream_t to run on; NULL = the legacy default stream */
 } lcp_config;
 
@@ -133,6 +135,39 @@ int lcp_update_dev(lcp_ctx* ctx, const double* centers, const double* axes);
  * re-configured for the new positions (contacts, D, U_nc, b) as by lcp_update.
  * centers_out [M*3] / axes_out [M*3]: optional host copies of the new state. */
 int lcp_step(lcp_ctx* ctx, double dt, double* centers_out, double* axes_out);
+
+/* Device bytes held by the context (its footprint for admission control). */
+int lcp_footprint(const lcp_ctx* ctx, size_t* bytes);
+
+/* Name of the FP32 pair-kernel variant in use ("t2c8" = 2 targets per thread,
+ * 8 source bodies per shared-memory tile; chosen by the autotuner when
+ * cfg.autotune is set). */
+const char* lcp_kernel_variant(const lcp_ctx* ctx);
+
+/* Batched solves: solves count independent contexts with `workers` host
+ * threads; contexts created with own_stream run concurrently on the GPU.
+ * x_dev: optional array of device pointers [n_i] (NULL entries or NULL array:
+ * results stay in the contexts).  stats: optional [count].  statuses [count]
+ * receives each solve's status; returns the first non-OK status or LCP_OK.
+ * Results are identical to solving the contexts one at a time. */
+int lcp_batch_solve(lcp_ctx** ctxs, int count, int method, double tol, double* const* x_dev, lcp_stats* stats,
+                    int* statuses, int workers);
+
+/* Continuous-batching solve server: `workers` host threads take requests as
+ * they arrive and run them concurrently (each context on its own stream).
+ * Contexts must be admitted first; admission counts lcp_footprint against
+ * hbm_budget_bytes and returns LCP_ERR_REJECTED when it would be exceeded.
+ * A context has at most one request in flight.  lcp_server_poll waits at most
+ * timeout_us for the ticket (LCP_ERR_TIMEOUT otherwise), copies x (host, at
+ * least n doubles) and the stats, and returns the solve's status. */
+typedef struct lcp_server lcp_server;
+int lcp_server_create(int workers, size_t hbm_budget_bytes, lcp_server** out);
+void lcp_server_destroy(lcp_server* srv);
+int lcp_server_admit(lcp_server* srv, lcp_ctx* ctx);
+int lcp_server_release(lcp_server* srv, lcp_ctx* ctx);
+int lcp_server_submit(lcp_server* srv, lcp_ctx* ctx, int method, double tol, uint64_t* ticket);
+int lcp_server_poll(lcp_server* srv, uint64_t ticket, double* x, int x_len, lcp_stats* st, int timeout_us);
+int lcp_server_stats(lcp_server* srv, size_t* resident_bytes, int* queued, int* in_flight);
 
 /* Kernel timing.  lcp_profile(ctx, 1) clears the record and starts timing
  * every stresslet-sum launch with CUDA events on the context's stream;

@@ -33,7 +33,7 @@ class lcp_config(ctypes.Structure):
                 ("ir_maxit", ctypes.c_int), ("kmax", ctypes.c_int), ("kmax_inner", ctypes.c_int),
                 ("memory", ctypes.c_int), ("ssn_maxit", ctypes.c_int), ("forcing", ctypes.c_double),
                 ("precondition", ctypes.c_int), ("residual_precision", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("autotune", ctypes.c_int), ("own_stream", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
 
 
 class lcp_contact(ctypes.Structure):
@@ -83,6 +83,17 @@ PROTOTYPES = {
     "lcp_stokes_rhs_dev": (_I, [_P, _P, _I, _P]),
     "lcp_rigid_velocity_dev": (_I, [_P, _P, _P]),
     "lcp_stokes_apply_noalloc": (_I, [_I, _I, _I, ctypes.c_double, _P, _P, _P, _I, _P]),
+    "lcp_footprint": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "lcp_kernel_variant": (ctypes.c_char_p, [_P]),
+    "lcp_batch_solve": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.c_double, ctypes.POINTER(_P),
+                             ctypes.POINTER(lcp_stats), ctypes.POINTER(_I), _I]),
+    "lcp_server_create": (_I, [_I, ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "lcp_server_destroy": (None, [_P]),
+    "lcp_server_admit": (_I, [_P, _P]),
+    "lcp_server_release": (_I, [_P, _P]),
+    "lcp_server_submit": (_I, [_P, _P, _I, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]),
+    "lcp_server_poll": (_I, [_P, ctypes.c_uint64, _D, _I, ctypes.POINTER(lcp_stats), _I]),
+    "lcp_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
 }
 
 _lib = None

@@ -120,6 +120,8 @@ struct lcp_ctx {
   // mobility solve workspace
   int m = 0, splits = 1;
   int num_sms = 0, occ32 = 0, occ64 = 0, occdf = 0;   // pair-kernel grid sizing
+  int occ32v[8] = {0};        // occupancy of each FP32 kernel variant
+  int v32 = 0;                // FP32 kernel variant in use (autotuned per size class)
   double *V = nullptr, *H = nullptr;  // Krylov basis [(m+1)][3N], Hessenberg etc.
   double* Z = nullptr;                 // preconditioned basis [m][3N] (flexible GMRES)
   float* pinv = nullptr;               // isolated-sphere inverse (3 ns x 3 ns, FP32)
@@ -140,8 +142,12 @@ struct lcp_ctx {
   int nh = 0;
   double *tmp_n = nullptr, *tmp_n2 = nullptr, *tmp_n3 = nullptr;
   std::vector<void*> allocs;
+  size_t bytes = 0;           // device bytes held (footprint for admission)
+  int device = 0;
+  bool owns_stream = false;
   // contact-sized buffers live in one arena, re-created when n outgrows it
   void* arena = nullptr;
+  size_t arena_bytes = 0;
   int ncap = 0;
   int pair_cap = 0;   // capacity of ci/cj/cnrm/gap
   // kernel timing (lcp_profile)

@@ -205,8 +205,13 @@ __global__ void k_scan_small(int M, const int* cnt, int* ptr) {
 void* ctx_alloc(lcp_ctx* ctx, size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed";
+    return nullptr;
+  }
   ctx->allocs.push_back(p);
+  ctx->bytes += bytes;
   return p;
 }
 

@@ -13,6 +13,8 @@ int stokes_configure(lcp_ctx* ctx);
 int stokes_max_splits(const lcp_ctx* ctx);
 int stokes_velocity(lcp_ctx* ctx, const double* phi, double* UO);
 int pqn_configure(lcp_ctx* ctx, int rmax);
+int stokes_autotune(lcp_ctx* ctx);
+const char* stokes_variant_name(const lcp_ctx* ctx);
 
 static thread_local std::string g_setup_error;
 static int copy_out(lcp_ctx* ctx, double* host, const double* dev, size_t count);
@@ -48,6 +50,8 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->forcing = 1e-3;
   c->precondition = 1;
   c->residual_precision = LCP_DF64;
+  c->autotune = 0;
+  c->own_stream = 0;
   c->cuda_stream = nullptr;
 }
 
@@ -115,6 +119,7 @@ static int alloc_static(lcp_ctx* ctx) {
   }
   LCP_TRY(pqn_configure(ctx, ctx->cfg.memory));
   if (ctx->cfg.precondition) LCP_TRY(precond_build(ctx));
+  if (ctx->cfg.autotune) LCP_TRY(stokes_autotune(ctx));
   return LCP_OK;
 }
 
@@ -137,6 +142,8 @@ static int arena_ensure(lcp_ctx* ctx, int n) {
     cudaFree(ctx->arena);
     ctx->arena = nullptr;
     ctx->ncap = 0;
+    ctx->bytes -= ctx->arena_bytes;
+    ctx->arena_bytes = 0;
   }
   if (cudaMalloc(&ctx->arena, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -144,6 +151,8 @@ static int arena_ensure(lcp_ctx* ctx, int n) {
     ctx->err = "device allocation of the contact buffers failed";
     return LCP_ERR_OOM;
   }
+  ctx->arena_bytes = bytes;
+  ctx->bytes += bytes;
   char* p = (char*)ctx->arena;
   ctx->b = (double*)p; p += al256(sizeof(double) * nn);
   ctx->tmp_n = (double*)p; p += al256(sizeof(double) * nn);
@@ -278,6 +287,14 @@ extern "C" int lcp_profile(lcp_ctx* ctx, int enable) {
   return LCP_OK;
 }
 
+extern "C" int lcp_footprint(const lcp_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return LCP_ERR_INVALID_ARG;
+  *bytes = ctx->bytes;
+  return LCP_OK;
+}
+
+extern "C" const char* lcp_kernel_variant(const lcp_ctx* ctx) { return ctx ? stokes_variant_name(ctx) : ""; }
+
 extern "C" int lcp_launch_count(const lcp_ctx* ctx, unsigned long long* count) {
   if (!ctx || !count) return LCP_ERR_INVALID_ARG;
   *count = ctx->nlaunch;
@@ -313,6 +330,16 @@ extern "C" int lcp_setup(const lcp_config* cfg, int n_bodies, const double* cent
   if (!ctx) { g_setup_error = "host allocation failed"; return LCP_ERR_OOM; }
   ctx->cfg = *cfg;
   ctx->stream = (cudaStream_t)cfg->cuda_stream;
+  cudaGetDevice(&ctx->device);
+  if (cfg->own_stream) {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      g_setup_error = "could not create the context's stream";
+      delete ctx;
+      return LCP_ERR_CUDA;
+    }
+    ctx->owns_stream = true;
+  }
   ctx->M = n_bodies;
   ctx->ns = cfg->n_theta * cfg->n_phi;
   ctx->N = ctx->M * ctx->ns;
@@ -334,6 +361,7 @@ extern "C" void lcp_destroy(lcp_ctx* ctx) {
   if (ctx->arena) cudaFree(ctx->arena);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->hscal) cudaFreeHost(ctx->hscal);
+  if (ctx->owns_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
 

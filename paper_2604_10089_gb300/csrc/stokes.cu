@@ -12,6 +12,9 @@
 // source body is staged per tile.  Positions are body-relative,
 // r = ((c_i - c_j) + xi_p) - xi_q with c_i - c_j formed from hi/lo parts,
 // which keeps FP32 differences accurate for nodes of touching spheres.
+#include <cmath>
+#include <vector>
+
 #include "common.cuh"
 
 namespace {
@@ -80,10 +83,10 @@ __device__ __forceinline__ void pair2(const float2 ex, const float2 ey, const fl
   az = __ffma2_rn(s, rz, az);
 }
 
-__global__ void __launch_bounds__(PAIR_THREADS, 2)
-k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
-         const float* __restrict__ c32, const float* __restrict__ phi32, double* __restrict__ partial) {
-  constexpr int TPT = PAIR32_TARGETS / PAIR_THREADS;
+template <int TPT, int CH>
+__device__ __forceinline__ void pair32_body(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
+                                            const float* __restrict__ c32, const float* __restrict__ phi32,
+                                            double* __restrict__ partial) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
   float* s_nx = sm;                    // -xi, per template node (padded)
@@ -92,7 +95,7 @@ k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
   float* s_wx = s_nz + ns_pad;         // -(3/4pi) w n
   float* s_wy = s_wx + ns_pad;
   float* s_wz = s_wy + ns_pad;
-  float* s_f = s_wz + ns_pad;          // [3][PAIR_CHUNK][ns_pad] source densities
+  float* s_f = s_wz + ns_pad;          // [3][CH][ns_pad] source densities
 
   for (int q = threadIdx.x; q < ns_pad; q += blockDim.x) {
     const bool real = q < ns;
@@ -119,7 +122,7 @@ k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
     float sacc[TPT][3], kacc[TPT][3];
 #pragma unroll
     for (int t = 0; t < TPT; t++) {
-      const int p = tb * PAIR32_TARGETS + t * PAIR_THREADS + threadIdx.x;
+      const int p = tb * (TPT * PAIR_THREADS) + t * PAIR_THREADS + threadIdx.x;
       pp[t] = p;
       const int pc = p < N ? p : N - 1;
       const int bi = pc / ns, qi = pc - bi * ns;
@@ -135,8 +138,8 @@ k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
         kacc[t][d] = 0.f;
       }
     }
-    for (int jc = jb0; jc < jb1; jc += PAIR_CHUNK) {
-      const int nb = min(PAIR_CHUNK, jb1 - jc);
+    for (int jc = jb0; jc < jb1; jc += CH) {
+      const int nb = min(CH, jb1 - jc);
       __syncthreads();
       // stage densities of bodies jc .. jc+nb-1 (contiguous in phi32), SoA in smem
       const int cnt = nb * ns;
@@ -144,11 +147,11 @@ k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
       for (int t = threadIdx.x; t < 3 * cnt; t += blockDim.x) {
         const int node = t / 3, d = t - 3 * node;
         const int b = node / ns, q = node - b * ns;
-        s_f[(d * PAIR_CHUNK + b) * ns_pad + q] = src[t];
+        s_f[(d * CH + b) * ns_pad + q] = src[t];
       }
       for (int t = threadIdx.x; t < nb * (ns_pad - ns); t += blockDim.x) {
         const int b = t / (ns_pad - ns), q = ns + t % (ns_pad - ns);
-        for (int d = 0; d < 3; d++) s_f[(d * PAIR_CHUNK + b) * ns_pad + q] = 0.f;
+        for (int d = 0; d < 3; d++) s_f[(d * CH + b) * ns_pad + q] = 0.f;
       }
       __syncthreads();
       for (int b = 0; b < nb; b++) {
@@ -165,9 +168,9 @@ k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
           e[t][1] = make_float2(ey, ey);
           e[t][2] = make_float2(ez, ez);
         }
-        const float* fxb = s_f + (0 * PAIR_CHUNK + b) * ns_pad;
-        const float* fyb = s_f + (1 * PAIR_CHUNK + b) * ns_pad;
-        const float* fzb = s_f + (2 * PAIR_CHUNK + b) * ns_pad;
+        const float* fxb = s_f + (0 * CH + b) * ns_pad;
+        const float* fyb = s_f + (1 * CH + b) * ns_pad;
+        const float* fzb = s_f + (2 * CH + b) * ns_pad;
         float2 acc[TPT][3];
 #pragma unroll
         for (int t = 0; t < TPT; t++)
@@ -204,6 +207,35 @@ k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32,
       }
   }
 }
+
+// The default FP32 kernel (two targets per thread, 8 source bodies per tile)
+// and the variants the autotuner chooses from per size class.
+__global__ void __launch_bounds__(PAIR_THREADS, 2)
+k_pair32(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32, const float* __restrict__ c32,
+         const float* __restrict__ phi32, double* __restrict__ partial) {
+  pair32_body<PAIR32_TARGETS / PAIR_THREADS, PAIR_CHUNK>(N, ns, ns_pad, un, tmpl32, c32, phi32, partial);
+}
+#define PAIR32_VARIANT(NAME, TPT, CH, MINB)                                                                  \
+  __global__ void __launch_bounds__(PAIR_THREADS, MINB)                                                       \
+      NAME(int N, int ns, int ns_pad, Units un, const float* __restrict__ tmpl32, const float* __restrict__ c32, \
+           const float* __restrict__ phi32, double* __restrict__ partial) {                                     \
+    pair32_body<TPT, CH>(N, ns, ns_pad, un, tmpl32, c32, phi32, partial);                                       \
+  }
+PAIR32_VARIANT(k_pair32_t1c8, 1, 8, 4)
+PAIR32_VARIANT(k_pair32_t2c16, 2, 16, 2)
+PAIR32_VARIANT(k_pair32_t2c4, 2, 4, 2)
+PAIR32_VARIANT(k_pair32_t1c16, 1, 16, 4)
+
+typedef void (*Pair32Kernel)(int, int, int, Units, const float*, const float*, const float*, double*);
+struct Pair32Variant {
+  Pair32Kernel kernel;
+  int tpt, chunk;
+  const char* name;
+};
+static const Pair32Variant kPair32Variants[] = {
+    {k_pair32, 2, 8, "t2c8"}, {k_pair32_t1c8, 1, 8, "t1c8"}, {k_pair32_t2c16, 2, 16, "t2c16"},
+    {k_pair32_t2c4, 2, 4, "t2c4"}, {k_pair32_t1c16, 1, 16, "t1c16"}};
+constexpr int kNumPair32Variants = sizeof(kPair32Variants) / sizeof(kPair32Variants[0]);
 
 // ---------------------------------------------------------------------------
 // Double-FP32 ("double-float") stresslet sum for the refinement residual.
@@ -531,19 +563,28 @@ __global__ void k_neg(int L, const double* __restrict__ x, double* __restrict__ 
 size_t stokes_pair_smem(int ns, int precision);
 // One full wave of CTAs for a pair kernel: SMs x resident CTAs per SM, capped
 // by the number of (target block, source body) units.
-static int pair_targets(int precision) { return precision == LCP_MIXED ? PAIR32_TARGETS : PAIR_THREADS; }
+static int pair_targets(int precision, int v32) {
+  return precision == LCP_MIXED ? kPair32Variants[v32].tpt * PAIR_THREADS : PAIR_THREADS;
+}
 
-static int pair_grid(const lcp_ctx* ctx, int precision) {
-  const int tpb = pair_targets(precision);
+static size_t pair32_smem(int ns, int v32) {
+  const int ns_pad = (ns + 3) & ~3;
+  return sizeof(float) * (6 * ns_pad + 3 * kPair32Variants[v32].chunk * ns_pad);
+}
+
+static int pair_grid_v(const lcp_ctx* ctx, int precision, int v32) {
+  const int tpb = pair_targets(precision, v32);
   const int units = ((ctx->N + tpb - 1) / tpb) * ctx->M;
-  const int per_sm = precision == LCP_MIXED ? ctx->occ32 : (precision == LCP_DF64 ? ctx->occdf : ctx->occ64);
+  const int per_sm = precision == LCP_MIXED ? ctx->occ32v[v32] : (precision == LCP_DF64 ? ctx->occdf : ctx->occ64);
   int g = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
   return g < units ? g : units;
 }
 
+static int pair_grid(const lcp_ctx* ctx, int precision) { return pair_grid_v(ctx, precision, ctx->v32); }
+
 // Largest number of CTAs that touch one target block (partial slots needed).
-static int pair_slots(const lcp_ctx* ctx, int grid, int precision) {
-  const int tpb = pair_targets(precision);
+static int pair_slots_v(const lcp_ctx* ctx, int grid, int precision, int v32) {
+  const int tpb = pair_targets(precision, v32);
   const long long units = (long long)((ctx->N + tpb - 1) / tpb) * ctx->M;
   const long long per = units / grid;   // every CTA holds per or per + 1 units
   const long long s = (ctx->M + per - 1) / (per > 0 ? per : 1) + 1;
@@ -560,9 +601,10 @@ int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef) {
 
 int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
   const int N = ctx->N, ns = ctx->ns, M = ctx->M;
-  const int ntb = (N + pair_targets(precision) - 1) / pair_targets(precision);
+  const int tpb = pair_targets(precision, ctx->v32);
+  const int ntb = (N + tpb - 1) / tpb;
   const int grid = pair_grid(ctx, precision);
-  const int slots = pair_slots(ctx, grid, precision);
+  const int slots = pair_slots_v(ctx, grid, precision, ctx->v32);
   if (slots > ctx->splits) {
     ctx->err = "internal: pair-sum slots exceed the partial buffer";
     return LCP_ERR_INVALID_ARG;
@@ -578,10 +620,10 @@ int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
   if (precision == LCP_MIXED) {
     ++ctx->nlaunch, k_to_f32<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(3 * N, phi, ctx->phi32);
     const int ns_pad = (ns + 3) & ~3;
-    const size_t smem = sizeof(float) * (6 * ns_pad + 3 * PAIR_CHUNK * ns_pad);
+    const size_t smem = pair32_smem(ns, ctx->v32);
     if (e0) LCP_CUDA(cudaEventRecord(e0, ctx->stream));
-    ++ctx->nlaunch, k_pair32<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, ns_pad, un, ctx->tmpl32,
-                                                                        ctx->centers32, ctx->phi32, ctx->partial);
+    ++ctx->nlaunch, kPair32Variants[ctx->v32].kernel<<<grid, PAIR_THREADS, smem, ctx->stream>>>(
+                        N, ns, ns_pad, un, ctx->tmpl32, ctx->centers32, ctx->phi32, ctx->partial);
     if (e1) LCP_CUDA(cudaEventRecord(e1, ctx->stream));
     ctx->c_fp32++;
   } else if (precision == LCP_DF64) {
@@ -631,9 +673,13 @@ int stokes_velocity(lcp_ctx* ctx, const double* phi, double* UO) {
 // Partial slots to allocate: the larger of the two kernels' needs.
 int stokes_max_splits(const lcp_ctx* ctx) {
   int m = 0;
-  const int precs[3] = {LCP_MIXED, LCP_FP64, LCP_DF64};
+  for (int v = 0; v < kNumPair32Variants; v++) {
+    const int s = pair_slots_v(ctx, pair_grid_v(ctx, LCP_MIXED, v), LCP_MIXED, v);
+    if (s > m) m = s;
+  }
+  const int precs[2] = {LCP_FP64, LCP_DF64};
   for (int prec : precs) {
-    const int s = pair_slots(ctx, pair_grid(ctx, prec), prec);
+    const int s = pair_slots_v(ctx, pair_grid_v(ctx, prec, 0), prec, 0);
     if (s > m) m = s;
   }
   return m;
@@ -642,22 +688,91 @@ int stokes_max_splits(const lcp_ctx* ctx) {
 size_t stokes_pair_smem(int ns, int precision) {
   const int ns_pad = (ns + 3) & ~3;
   if (precision == LCP_DF64) return sizeof(float) * (12 * ns_pad + 6 * PAIR_CHUNK * ns_pad);
-  return precision == LCP_MIXED ? sizeof(float) * (6 * ns_pad + 3 * PAIR_CHUNK * ns_pad)
-                                : sizeof(double) * (6 * ns + 3 * PAIR_CHUNK * ns);
+  return precision == LCP_MIXED ? pair32_smem(ns, 0) : sizeof(double) * (6 * ns + 3 * PAIR_CHUNK * ns);
 }
 
 // Shared-memory limits and one-wave grid sizes (occupancy) of the pair kernels.
 int stokes_configure(lcp_ctx* ctx) {
-  const size_t s32 = stokes_pair_smem(ctx->ns, LCP_MIXED), s64 = stokes_pair_smem(ctx->ns, LCP_FP64);
+  const size_t s64 = stokes_pair_smem(ctx->ns, LCP_FP64);
   if (s64 > 48 * 1024) LCP_CUDA(cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
-  if (s32 > 48 * 1024) LCP_CUDA(cudaFuncSetAttribute(k_pair32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32));
+  for (int v = 0; v < kNumPair32Variants; v++) {
+    const size_t sv = pair32_smem(ctx->ns, v);
+    if (sv > 48 * 1024)
+      LCP_CUDA(cudaFuncSetAttribute(kPair32Variants[v].kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv));
+    LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occ32v[v], kPair32Variants[v].kernel, PAIR_THREADS, sv));
+  }
   int dev = 0;
   LCP_CUDA(cudaGetDevice(&dev));
   LCP_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev));
-  LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occ32, k_pair32, PAIR_THREADS, s32));
   LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occ64, k_pair64, PAIR_THREADS, s64));
   const size_t sdf = stokes_pair_smem(ctx->ns, LCP_DF64);
   if (sdf > 48 * 1024) LCP_CUDA(cudaFuncSetAttribute(k_pair_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sdf));
   LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occdf, k_pair_df, PAIR_THREADS, sdf));
   return LCP_OK;
 }
+
+// ---------------------------------------------------------------- autotuner
+// Chooses the FP32 pair-kernel variant (targets per CTA = target-block size,
+// source bodies per shared-memory tile) for a size class by timing every
+// variant on this context's geometry; the choice is cached per (nodes per
+// sphere, bodies) class for the process.
+#include <map>
+#include <mutex>
+
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, int> g_tune_cache;
+
+static int size_class(int M) {   // bodies rounded up to a power of two
+  int c = 1;
+  while (c < M) c <<= 1;
+  return c;
+}
+
+int stokes_autotune(lcp_ctx* ctx) {
+  const std::pair<int, int> key(ctx->ns, size_class(ctx->M));
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      ctx->v32 = it->second;
+      return LCP_OK;
+    }
+  }
+  const int L = 3 * ctx->N;
+  // a deterministic density: phi = sin(k) pattern, built on the device
+  double* phi = ctx->dphi;
+  double* out = ctx->wv;
+  std::vector<double> h(L);
+  for (int i = 0; i < L; i++) h[i] = std::sin(0.37 * i);
+  LCP_CUDA(cudaMemcpyAsync(phi, h.data(), sizeof(double) * L, cudaMemcpyHostToDevice, ctx->stream));
+  cudaEvent_t a, b;
+  LCP_CUDA(cudaEventCreate(&a));
+  LCP_CUDA(cudaEventCreate(&b));
+  float best = 1e30f;
+  int best_v = 0;
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  for (int v = 0; v < kNumPair32Variants; v++) {
+    if (ctx->occ32v[v] <= 0) continue;
+    ctx->v32 = v;
+    if (pair_slots_v(ctx, pair_grid_v(ctx, LCP_MIXED, v), LCP_MIXED, v) > ctx->splits) continue;
+    LCP_TRY(stokes_apply(ctx, phi, out, LCP_MIXED));   // warm-up
+    LCP_CUDA(cudaEventRecord(a, ctx->stream));
+    for (int r = 0; r < 3; r++) LCP_TRY(stokes_apply(ctx, phi, out, LCP_MIXED));
+    LCP_CUDA(cudaEventRecord(b, ctx->stream));
+    LCP_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    LCP_CUDA(cudaEventElapsedTime(&ms, a, b));
+    if (ms < best) { best = ms; best_v = v; }
+  }
+  ctx->prof = prof;
+  ctx->c_fp32 = 0;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  ctx->v32 = best_v;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = best_v;
+  return LCP_OK;
+}
+
+const char* stokes_variant_name(const lcp_ctx* ctx) { return kPair32Variants[ctx->v32].name; }

@@ -231,6 +231,70 @@ def lcp_stokes_apply_noalloc(n_bodies, n_theta, n_phi, radius, centers, phi, out
                                            stream), None)
 
 
+def lcp_footprint(ctx) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib().lcp_footprint(ctx, ctypes.byref(b)), ctx)
+    return b.value
+
+
+def lcp_kernel_variant(ctx) -> str:
+    return _lib().lcp_kernel_variant(ctx).decode()
+
+
+def lcp_batch_solve(ctxs, method: int, tol: float, xs=None, workers: int = 8):
+    """Solve contexts concurrently; xs: optional CUDA tensors.  Returns (statuses, stats dicts)."""
+    n = len(ctxs)
+    carr = (ctypes.c_void_p * max(n, 1))(*ctxs)
+    xarr = None
+    if xs is not None:
+        xarr = (ctypes.c_void_p * max(n, 1))(*[_devptr(x) for x in xs])
+    st = (_abi.lcp_stats * max(n, 1))()
+    sts = (ctypes.c_int * max(n, 1))()
+    _lib().lcp_batch_solve(carr, n, int(method), float(tol), xarr, st, sts, int(workers))
+    return [sts[i] for i in range(n)], [st[i].as_dict() for i in range(n)]
+
+
+def lcp_server_create(workers: int, hbm_budget_bytes: int):
+    out = ctypes.c_void_p()
+    _check(_lib().lcp_server_create(int(workers), int(hbm_budget_bytes), ctypes.byref(out)), None)
+    return out.value
+
+
+def lcp_server_destroy(srv) -> None:
+    if srv:
+        _lib().lcp_server_destroy(srv)
+
+
+def lcp_server_admit(srv, ctx) -> int:
+    """Returns LCP_OK or LCP_ERR_REJECTED (memory budget)."""
+    return _lib().lcp_server_admit(srv, ctx)
+
+
+def lcp_server_release(srv, ctx) -> None:
+    _check(_lib().lcp_server_release(srv, ctx), None)
+
+
+def lcp_server_submit(srv, ctx, method: int, tol: float) -> int:
+    t = ctypes.c_uint64()
+    _check(_lib().lcp_server_submit(srv, ctx, int(method), float(tol), ctypes.byref(t)), None)
+    return t.value
+
+
+def lcp_server_poll(srv, ticket: int, n: int, timeout_us: int):
+    """Returns (status, x, stats dict); status LCP_ERR_TIMEOUT if not ready."""
+    x = np.empty(max(n, 1))
+    st = _abi.lcp_stats()
+    status = _lib().lcp_server_poll(srv, ctypes.c_uint64(ticket), _dptr(x), max(n, 1), ctypes.byref(st),
+                                    int(timeout_us))
+    return status, x[:n], st.as_dict()
+
+
+def lcp_server_stats(srv):
+    b, q, f = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib().lcp_server_stats(srv, ctypes.byref(b), ctypes.byref(q), ctypes.byref(f)), None)
+    return b.value, q.value, f.value
+
+
 def config_for(instance, precision: int = LCP_FP64, **overrides) -> _abi.lcp_config:
     """Config of a workload instance (grid, radii, dt, delta) with overrides."""
     cfg = lcp_default_config(n_theta=instance.n_theta, n_phi=instance.n_phi, radius=instance.radius,
