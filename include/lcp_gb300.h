@@ -139,6 +139,10 @@ int lcp_step(lcp_ctx* ctx, double dt, double* centers_out, double* axes_out);
 /* Device bytes held by the context (its footprint for admission control). */
 int lcp_footprint(const lcp_ctx* ctx, size_t* bytes);
 
+/* Upper estimate of lcp_footprint for a context of n_bodies bodies and about
+ * n_contacts contacts with this config, computable before creating it. */
+int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n_contacts, size_t* bytes);
+
 /* Name of the FP32 pair-kernel variant in use ("t2c8" = 2 targets per thread,
  * 8 source bodies per shared-memory tile; chosen by the autotuner when
  * cfg.autotune is set). */

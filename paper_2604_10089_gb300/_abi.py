@@ -84,6 +84,7 @@ PROTOTYPES = {
     "lcp_rigid_velocity_dev": (_I, [_P, _P, _P]),
     "lcp_stokes_apply_noalloc": (_I, [_I, _I, _I, ctypes.c_double, _P, _P, _P, _I, _P]),
     "lcp_footprint": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "lcp_footprint_estimate": (_I, [ctypes.POINTER(lcp_config), _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "lcp_kernel_variant": (ctypes.c_char_p, [_P]),
     "lcp_batch_solve": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.c_double, ctypes.POINTER(_P),
                              ctypes.POINTER(lcp_stats), ctypes.POINTER(_I), _I]),

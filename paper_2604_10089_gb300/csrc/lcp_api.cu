@@ -287,6 +287,28 @@ extern "C" int lcp_profile(lcp_ctx* ctx, int enable) {
   return LCP_OK;
 }
 
+// Device bytes a context of this size will hold (same buffers as lcp_setup,
+// with n_contacts contacts), for admission decisions before creating it.
+extern "C" int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n_contacts, size_t* bytes) {
+  if (!cfg || !bytes || n_bodies < 1 || n_contacts < 0) return LCP_ERR_INVALID_ARG;
+  const size_t M = n_bodies, ns = (size_t)cfg->n_theta * cfg->n_phi, N = M * ns, L = 3 * N;
+  const size_t m = cfg->gmres_restart, R = cfg->memory, K = cfg->kmax;
+  const size_t n = n_contacts > 64 ? n_contacts : 64;
+  const size_t pairs = M * (M - 1) / 2 > 0 ? M * (M - 1) / 2 : 1;
+  size_t b = 0;
+  b += sizeof(double) * L * (m + 1) + (cfg->precondition ? sizeof(double) * L * m : 0);   // Krylov bases
+  b += sizeof(double) * L * 5 + sizeof(float) * L * 3;                                      // node vectors
+  b += sizeof(double) * L * 6;                                                               // partial slots
+  b += sizeof(double) * ((m + 1) * m + 6 * m + 16 + (m + 2) * 304);                          // Hessenberg, dots
+  b += sizeof(double) * (8 * ns + 36) + sizeof(float) * 6 * ns + sizeof(double) * 30 * M + sizeof(float) * 8 * M;
+  b += (sizeof(int) * 2 + sizeof(double) * 4) * pairs + sizeof(int) * M * (M + 2);           // contact buffers
+  if (cfg->precondition) b += sizeof(double) * 9 * ns * ns * 3 + sizeof(float) * 9 * ns * ns;  // preconditioner
+  b += sizeof(double) * n * (6 + 2 * K) + sizeof(int) * (2 * n + 1);                         // arena
+  b += 2 * sizeof(double) * (n * (8 + 6 * R) + 3 * R * R + 64);                              // PQN states
+  *bytes = b + (b >> 4);                                                                     // 1/16 slack
+  return LCP_OK;
+}
+
 extern "C" int lcp_footprint(const lcp_ctx* ctx, size_t* bytes) {
   if (!ctx || !bytes) return LCP_ERR_INVALID_ARG;
   *bytes = ctx->bytes;

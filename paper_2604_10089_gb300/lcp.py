@@ -237,6 +237,12 @@ def lcp_footprint(ctx) -> int:
     return b.value
 
 
+def lcp_footprint_estimate(cfg, n_bodies: int, n_contacts: int) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib().lcp_footprint_estimate(ctypes.byref(cfg), int(n_bodies), int(n_contacts), ctypes.byref(b)), None)
+    return b.value
+
+
 def lcp_kernel_variant(ctx) -> str:
     return _lib().lcp_kernel_variant(ctx).decode()
 
