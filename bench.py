@@ -130,6 +130,22 @@ def source_sha1():
     return h.hexdigest()
 
 
+def rank_seeds(rank: int, count: int) -> list:
+    """Instance indices of one rank: disjoint across ranks (weak scaling, no shared data)."""
+    return [rank * 1000 + i for i in range(count)]
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Maximum of a per-rank time over all ranks (the slowest rank sets the job time)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def pct(v, q):
     return float(np.percentile(np.asarray(v), q)) if len(v) else None
 
@@ -144,7 +160,7 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     n_inst = args.warmup + args.steps
-    insts = [make_instance(args.workload, rank * 1000 + i) for i in range(n_inst)]
+    insts = [make_instance(args.workload, k) for k in rank_seeds(rank, n_inst)]
     prec = L.LCP_MIXED if args.precision == "mixed" else L.LCP_FP64
     method = L.LCP_BI_PQN if args.method == "bi" else L.LCP_MONO_PQN
     cfg = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream)
@@ -192,10 +208,7 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     lat = [ev[k].elapsed_time(ev[k + 1]) / 1e3 for k in range(args.steps)]
     t_total = ev[0].elapsed_time(ev[-1]) / 1e3
-    if world > 1:
-        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = max_over_ranks(t_total, dev)
 
     # end to end through the host API: host centres/axes in, host x out
     e2e = None
