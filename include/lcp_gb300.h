@@ -32,6 +32,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define LCP_API __attribute__((visibility("default")))
+#else
+#define LCP_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -104,7 +110,7 @@ typedef struct lcp_ctx lcp_ctx;   /* opaque, library-owned */
 
 /* Fills cfg with defaults (grid 9 x 18, a = 1, contact radius 1.25, mu = 1,
  * dt = 0.01, delta = 0.05, FP64, GMRES tol 1e-12, restart 60, ...). */
-void lcp_default_config(lcp_config* cfg);
+LCP_API void lcp_default_config(lcp_config* cfg);
 
 /* Builds a context for one configuration (Sec. 3, Eqs. collisional-set, LCP,
  * defAandb).  centers: host [M*3].  axes: host [M*3] unit Janus axes, or NULL
@@ -114,7 +120,7 @@ void lcp_default_config(lcp_config* cfg);
  * non-collisional velocity U_nc (one slip-driven mobility solve) and
  * b = gap / dt + D^T U_nc.  Allocates all device state; *out receives the
  * context (NULL on failure, message via lcp_last_error(NULL)). */
-int lcp_setup(const lcp_config* cfg, int n_bodies, const double* centers, const double* axes,
+LCP_API int lcp_setup(const lcp_config* cfg, int n_bodies, const double* centers, const double* axes,
               int n_contacts, const lcp_contact* contacts, lcp_ctx** out);
 
 /* Re-configures the context for new centres (same M and grid): uploads
@@ -122,11 +128,11 @@ int lcp_setup(const lcp_config* cfg, int n_bodies, const double* centers, const 
  * n_contacts caller contacts), rebuilds D, U_nc and b.  Reuses the device
  * buffers; the contact-sized ones grow when n exceeds their capacity.  This
  * is the per-time-step entry of a trajectory (Eq. dvi). */
-int lcp_update(lcp_ctx* ctx, const double* centers, const double* axes, int n_contacts,
+LCP_API int lcp_update(lcp_ctx* ctx, const double* centers, const double* axes, int n_contacts,
                const lcp_contact* contacts);
 /* Same with device pointers centers [M*3], axes [M*3] or NULL; contacts are
  * always detected. */
-int lcp_update_dev(lcp_ctx* ctx, const double* centers, const double* axes);
+LCP_API int lcp_update_dev(lcp_ctx* ctx, const double* centers, const double* axes);
 
 /* One forward Euler step of Eq. (dvi) after lcp_solve: body velocities
  * U = U_nc + M D x (M D x accumulated during the solve with the same MVP reuse
@@ -134,19 +140,19 @@ int lcp_update_dev(lcp_ctx* ctx, const double* centers, const double* axes);
  * rotated by the angle |Omega| dt about Omega; then the context is
  * re-configured for the new positions (contacts, D, U_nc, b) as by lcp_update.
  * centers_out [M*3] / axes_out [M*3]: optional host copies of the new state. */
-int lcp_step(lcp_ctx* ctx, double dt, double* centers_out, double* axes_out);
+LCP_API int lcp_step(lcp_ctx* ctx, double dt, double* centers_out, double* axes_out);
 
 /* Device bytes held by the context (its footprint for admission control). */
-int lcp_footprint(const lcp_ctx* ctx, size_t* bytes);
+LCP_API int lcp_footprint(const lcp_ctx* ctx, size_t* bytes);
 
 /* Upper estimate of lcp_footprint for a context of n_bodies bodies and about
  * n_contacts contacts with this config, computable before creating it. */
-int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n_contacts, size_t* bytes);
+LCP_API int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n_contacts, size_t* bytes);
 
 /* Name of the FP32 pair-kernel variant in use ("t2c8" = 2 targets per thread,
  * 8 source bodies per shared-memory tile; chosen by the autotuner when
  * cfg.autotune is set). */
-const char* lcp_kernel_variant(const lcp_ctx* ctx);
+LCP_API const char* lcp_kernel_variant(const lcp_ctx* ctx);
 
 /* Batched solves: solves count independent contexts with `workers` host
  * threads; contexts created with own_stream run concurrently on the GPU.
@@ -154,7 +160,7 @@ const char* lcp_kernel_variant(const lcp_ctx* ctx);
  * results stay in the contexts).  stats: optional [count].  statuses [count]
  * receives each solve's status; returns the first non-OK status or LCP_OK.
  * Results are identical to solving the contexts one at a time. */
-int lcp_batch_solve(lcp_ctx** ctxs, int count, int method, double tol, double* const* x_dev, lcp_stats* stats,
+LCP_API int lcp_batch_solve(lcp_ctx** ctxs, int count, int method, double tol, double* const* x_dev, lcp_stats* stats,
                     int* statuses, int workers);
 
 /* Continuous-batching solve server: `workers` host threads take requests as
@@ -165,58 +171,58 @@ int lcp_batch_solve(lcp_ctx** ctxs, int count, int method, double tol, double* c
  * timeout_us for the ticket (LCP_ERR_TIMEOUT otherwise), copies x (host, at
  * least n doubles) and the stats, and returns the solve's status. */
 typedef struct lcp_server lcp_server;
-int lcp_server_create(int workers, size_t hbm_budget_bytes, lcp_server** out);
-void lcp_server_destroy(lcp_server* srv);
-int lcp_server_admit(lcp_server* srv, lcp_ctx* ctx);
-int lcp_server_release(lcp_server* srv, lcp_ctx* ctx);
-int lcp_server_submit(lcp_server* srv, lcp_ctx* ctx, int method, double tol, uint64_t* ticket);
-int lcp_server_poll(lcp_server* srv, uint64_t ticket, double* x, int x_len, lcp_stats* st, int timeout_us);
-int lcp_server_stats(lcp_server* srv, size_t* resident_bytes, int* queued, int* in_flight);
+LCP_API int lcp_server_create(int workers, size_t hbm_budget_bytes, lcp_server** out);
+LCP_API void lcp_server_destroy(lcp_server* srv);
+LCP_API int lcp_server_admit(lcp_server* srv, lcp_ctx* ctx);
+LCP_API int lcp_server_release(lcp_server* srv, lcp_ctx* ctx);
+LCP_API int lcp_server_submit(lcp_server* srv, lcp_ctx* ctx, int method, double tol, uint64_t* ticket);
+LCP_API int lcp_server_poll(lcp_server* srv, uint64_t ticket, double* x, int x_len, lcp_stats* st, int timeout_us);
+LCP_API int lcp_server_stats(lcp_server* srv, size_t* resident_bytes, int* queued, int* in_flight);
 
 /* Kernel timing.  lcp_profile(ctx, 1) clears the record and starts timing
  * every stresslet-sum launch with CUDA events on the context's stream;
  * lcp_profile(ctx, 0) stops and clears.  lcp_profile_read returns the number
  * of launches of a kind (0 = FP32, 1 = FP64, 2 = double-FP32 pair sum) and their
  * summed duration in milliseconds (synchronises the stream). */
-int lcp_profile(lcp_ctx* ctx, int enable);
-int lcp_profile_read(lcp_ctx* ctx, int kind, int* count, double* total_ms);
+LCP_API int lcp_profile(lcp_ctx* ctx, int enable);
+LCP_API int lcp_profile_read(lcp_ctx* ctx, int kind, int* count, double* total_ms);
 
 /* Number of kernels this context has launched since lcp_setup. */
-int lcp_launch_count(const lcp_ctx* ctx, unsigned long long* count);
+LCP_API int lcp_launch_count(const lcp_ctx* ctx, unsigned long long* count);
 
 /* Frees every device buffer of the context.  NULL is ignored. */
-void lcp_destroy(lcp_ctx* ctx);
+LCP_API void lcp_destroy(lcp_ctx* ctx);
 
 /* Message of the last failure on ctx (or of the calling thread's last failed
  * lcp_setup when ctx is NULL).  Valid until the next call on ctx. */
-const char* lcp_last_error(const lcp_ctx* ctx);
+LCP_API const char* lcp_last_error(const lcp_ctx* ctx);
 
 /* Sizes: bodies M, nodes N, contacts n. */
-int lcp_sizes(const lcp_ctx* ctx, int* n_bodies, int* n_nodes, int* n_contacts);
+LCP_API int lcp_sizes(const lcp_ctx* ctx, int* n_bodies, int* n_nodes, int* n_contacts);
 
 /* Copies the contacts (host [n]), b (host [n]) or U_nc (host [M*6]). */
-int lcp_get_contacts(lcp_ctx* ctx, lcp_contact* out);
-int lcp_get_b(lcp_ctx* ctx, double* b);
-int lcp_get_unc(lcp_ctx* ctx, double* U_nc);
+LCP_API int lcp_get_contacts(lcp_ctx* ctx, lcp_contact* out);
+LCP_API int lcp_get_b(lcp_ctx* ctx, double* b);
+LCP_API int lcp_get_unc(lcp_ctx* ctx, double* U_nc);
 
 /* U = M F (Sec. 2, Eq. mobility).  FT, UO: host [M*6].  include_slip adds the
  * Janus slip-driven part (U_nc for FT = 0).  fidelity: LCP_HIGH (boundary
  * integral, GMRES, precision of the context) or LCP_LOW_RPY (pairwise RPY). */
-int mobility_apply(lcp_ctx* ctx, const double* FT, double* UO, int include_slip, int fidelity);
+LCP_API int mobility_apply(lcp_ctx* ctx, const double* FT, double* UO, int include_slip, int fidelity);
 /* Same on device pointers FT [M*6], UO [M*6], on the context's stream. */
-int mobility_apply_dev(lcp_ctx* ctx, const double* FT, double* UO, int include_slip, int fidelity);
+LCP_API int mobility_apply_dev(lcp_ctx* ctx, const double* FT, double* UO, int include_slip, int fidelity);
 
 /* One matrix-vector product A[x] = D^T M D x (Sec. 3, Eq. defAandb) of the
  * given fidelity.  Host x [n], Ax [n]. */
-int lcp_apply_A(lcp_ctx* ctx, const double* x, double* Ax, int fidelity);
+LCP_API int lcp_apply_A(lcp_ctx* ctx, const double* x, double* Ax, int fidelity);
 
 /* Solves 0 <= x perp A x + b >= 0 by Mono-PQN (Algorithm 1) or Bi-PQN
  * (Algorithm 4) to ||min(x, A x + b)||_2 <= tol.  x0: host [n] initial guess
  * (projected onto x >= 0) or NULL for 0.  x: host [n] result.  st: optional.
  * Returns LCP_ERR_NOT_CONVERGED (x = last iterate) if kmax is reached. */
-int lcp_solve(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st);
+LCP_API int lcp_solve(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st);
 /* Same with device pointers x0 (or NULL) and x, both [n] FP64. */
-int lcp_solve_dev(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st);
+LCP_API int lcp_solve_dev(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st);
 
 /* Building blocks of the mobility solve, on device pointers and the context's
  * stream (used by the parity tests):
@@ -225,9 +231,9 @@ int lcp_solve_dev(lcp_ctx* ctx, int method, double tol, const double* x0, double
  *     LCP_DF64 (double-FP32 pair sums);
  *   lcp_stokes_rhs_dev: rhs = s - S[F, T] at the nodes, FT [M*6], rhs [N*3];
  *   lcp_rigid_velocity_dev: UO = -(rigid coefficients of P phi), UO [M*6]. */
-int lcp_stokes_apply_dev(lcp_ctx* ctx, const double* phi, double* out, int precision);
-int lcp_stokes_rhs_dev(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs);
-int lcp_rigid_velocity_dev(lcp_ctx* ctx, const double* phi, double* UO);
+LCP_API int lcp_stokes_apply_dev(lcp_ctx* ctx, const double* phi, double* out, int precision);
+LCP_API int lcp_stokes_rhs_dev(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs);
+LCP_API int lcp_rigid_velocity_dev(lcp_ctx* ctx, const double* phi, double* UO);
 
 /* Allocation-free stresslet apply: out = (K + P) phi for n_bodies spheres of
  * radius `radius` on an n_theta x n_phi grid, with no context and no memory
@@ -250,7 +256,7 @@ int lcp_rigid_velocity_dev(lcp_ctx* ctx, const double* phi, double* UO);
  * make that first call before any stream capture.  All calls share the
  * scratch area: calls whose GPU work may overlap (other streams or threads
  * without ordering) race and must be serialised by the caller. */
-int lcp_stokes_apply_noalloc(int n_bodies, int n_theta, int n_phi, double radius, const double* centers,
+LCP_API int lcp_stokes_apply_noalloc(int n_bodies, int n_theta, int n_phi, double radius, const double* centers,
                              const double* phi, double* out, int precision, void* cuda_stream);
 
 #ifdef __cplusplus

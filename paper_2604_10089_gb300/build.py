@@ -20,7 +20,8 @@ LIB = os.path.join(HERE, "liblcp_gb300.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["geometry.cu", "stokes.cu", "krylov.cu", "pqn.cu", "lcp_api.cu", "noalloc.cu", "precond.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+         "-I" + INCLUDE]
 
 
 def nvcc() -> str:

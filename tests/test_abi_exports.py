@@ -1,0 +1,53 @@
+"""The C ABI: every function declared in include/*.h is exported by the library
+(and nothing else of the library's internals leaks); the library loads and its
+defaults are readable without a GPU."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_2604_10089_gb300", "liblcp_gb300.so")
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:LCP_API\s+)?(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*"
+                             r"([A-Za-z_][A-Za-z0-9_]*)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2604_10089_gb300.build import build
+    build()
+    return LIB
+
+
+def test_every_declared_function_is_exported(built):
+    declared = declared_functions()
+    assert len(declared) >= 30, sorted(declared)
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = declared - exported
+    assert not missing, sorted(missing)
+    internal = {s for s in exported if s.startswith("_Z")}
+    assert not internal, sorted(internal)[:10]
+
+
+def test_library_loads_and_binding_matches(built):
+    from paper_2604_10089_gb300 import _abi
+    import paper_2604_10089_gb300 as L
+    lib = _abi.load()
+    for name in declared_functions():
+        assert hasattr(lib, name)
+        assert name in _abi.PROTOTYPES, name
+    cfg = L.lcp_default_config()
+    assert cfg.n_theta == 9 and cfg.n_phi == 18 and cfg.gmres_tol == 1e-12
+    assert cfg.residual_precision == L.LCP_DF64 and cfg.precondition == 1
