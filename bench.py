@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--fp64-compare", type=int, default=1)
     p.add_argument("--cpu-baseline", type=int, default=1)
+    p.add_argument("--compare-methods", type=int, default=1,
+                   help="also solve the first timed configuration with BB-PGD, Mono-PQN and Bi-PQN (mixed)")
     p.add_argument("--e2e", type=int, default=1)
     p.add_argument("--mode", default="solve", choices=["solve", "batched", "serving"],
                    help="solve: the headline metric; batched: 256 uneven instances solved together; "
@@ -244,6 +246,18 @@ def run_ours(args, rank, world, local):
                 "max_abs_diff_vs_ours": float(np.abs(xm - x64).max()),
                 "same_active_set": bool(np.array_equal(xm > thr, x64 > thr)),
                 "kkt_fp64": st64["kkt_abs"], "kkt_ours": stm["kkt_abs"]}
+    # the paper's comparison on this workload: high-fidelity MVPs and time per solve
+    comparison = None
+    if args.compare_methods and rank == 0:
+        comparison = {}
+        inst = insts[args.warmup]
+        for name, meth in (("bb_pgd", L.LCP_BB_PGD), ("mono_pqn", L.LCP_MONO_PQN), ("bi_pqn", L.LCP_BI_PQN)):
+            L.lcp_update(ctx, inst.centers, inst.axes)
+            ts = time.perf_counter()
+            _, st, status = L.lcp_solve(ctx, meth, tol, allow_not_converged=True)
+            comparison[name] = {"hi_mvps": st["hi_mvps"], "lo_mvps": st["lo_mvps"], "e_mvps": round(st["e_mvps"], 3),
+                                "iterations": st["iterations"], "seconds": time.perf_counter() - ts,
+                                "converged": st["converged"] == 1}
     traj = None
     if args.trajectory and rank == 0:
         inst = insts[args.warmup]
@@ -298,6 +312,7 @@ def run_ours(args, rank, world, local):
                "fp32_ops_per_pair_note": "double-FP32 arithmetic, ~250 FP32 operations per pair",
                "pairs_per_s": pairs / (tdf / cdf / 1e3), "share_of_timed_region": tdf / 1e3 / t_total}
     return dict(t_total=t_total, lat=lat, clocks=clk, launches=launches, roof=roof, k64=k64, kdf=kdf, e2e=e2e, traj=traj,
+                comparison=comparison,
                 fp64=fp64, summary=summary, N=N, M=M)
 
 
@@ -556,7 +571,8 @@ def main():
             "latency_s": {"p50": pct(r["lat"], 50), "p99": pct(r["lat"], 99)},
             "roofline": r["roof"], "fp64_kernel": r["k64"], "df64_kernel": r["kdf"], "clocks": r["clocks"],
             "e2e": r["e2e"], "gpu_launches": r["launches"], "cpu_baseline": cpu,
-            "fp64_mono_pqn": r["fp64"], "trajectory": r["traj"], "solver": s,
+            "fp64_mono_pqn": r["fp64"], "method_comparison_mixed": r["comparison"], "trajectory": r["traj"],
+            "solver": s,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -56,6 +56,7 @@ typedef enum {
 enum { LCP_FP64 = 0, LCP_MIXED = 1 };          /* precision of the stresslet sums */
 enum { LCP_DF64 = 2 };                          /* double-FP32 sums (refinement residuals, ~1e-13) */
 enum { LCP_MONO_PQN = 0, LCP_BI_PQN = 1 };     /* Algorithm 1 / Algorithm 4 */
+enum { LCP_BB_PGD = 2 };                        /* baseline of Sec. 6: PGD with the Barzilai-Borwein step */
 enum { LCP_HIGH = 0, LCP_LOW_RPY = 1 };        /* mobility fidelity */
 
 typedef struct {
@@ -80,6 +81,8 @@ typedef struct {
   int residual_precision;   /* LCP_MIXED refinement residuals: LCP_FP64 or LCP_DF64 (default) */
   int autotune;             /* 1: time the FP32 pair-kernel variants at set-up, keep the fastest per size class */
   int own_stream;           /* 1: the context creates (and destroys) its own non-blocking stream */
+  int h0_scaling;           /* 0: B_0 = H_0 = I as printed in Algorithm 1; 1: B_0 = delta I with
+                               delta = y^T s / s^T s of the first step (H_0 = I / delta) */
   void* cuda_stream;        /* cudaStream_t to run on; NULL = the legacy default stream */
 } lcp_config;
 
@@ -104,6 +107,10 @@ typedef struct {
   double lo_mvp_seconds;    /* mean wall time of one low-fidelity MVP */
   double seconds;           /* wall time of the solve */
   int df64_applies;         /* double-FP32 stresslet applications (refinement residuals) */
+  int resets;               /* quasi-Newton memory resets (non-descent direction) */
+  int ssn_iterations;       /* semi-smooth Newton iterations of all prox evaluations */
+  int ssn_fallbacks;        /* prox evaluations that needed the projected Gauss-Seidel fallback */
+  double h0_delta;          /* scale delta of B_0 = delta I (1 when unscaled) */
 } lcp_stats;
 
 typedef struct lcp_ctx lcp_ctx;   /* opaque, library-owned */
@@ -216,8 +223,9 @@ LCP_API int mobility_apply_dev(lcp_ctx* ctx, const double* FT, double* UO, int i
  * given fidelity.  Host x [n], Ax [n]. */
 LCP_API int lcp_apply_A(lcp_ctx* ctx, const double* x, double* Ax, int fidelity);
 
-/* Solves 0 <= x perp A x + b >= 0 by Mono-PQN (Algorithm 1) or Bi-PQN
- * (Algorithm 4) to ||min(x, A x + b)||_2 <= tol.  x0: host [n] initial guess
+/* Solves 0 <= x perp A x + b >= 0 by Mono-PQN (Algorithm 1), Bi-PQN
+ * (Algorithm 4) or the BB-PGD baseline (Sec. 6, Eq. spectralStepSize, first
+ * step tau_0 = 3 pi mu a) to ||min(x, A x + b)||_2 <= tol.  x0: host [n] initial guess
  * (projected onto x >= 0) or NULL for 0.  x: host [n] result.  st: optional.
  * Returns LCP_ERR_NOT_CONVERGED (x = last iterate) if kmax is reached. */
 LCP_API int lcp_solve(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st);

@@ -204,7 +204,7 @@ class PQNResult:
 
 
 def mono_pqn(mvp, b, x0, tol=1e-8, kmax=100, d=None, pairs=(), r_max=32,
-             g0=None, extra_mvp=None):
+             g0=None, extra_mvp=None, scale0=False):
     """Algorithm 1 (Mono-PQN).
 
     mvp(v) returns A[v].  With g0 given the initial gradient is taken as is
@@ -250,6 +250,10 @@ def mono_pqn(mvp, b, x0, tol=1e-8, kmax=100, d=None, pairs=(), r_max=32,
         g = g + eta * Ap
         if extra_mvp:
             extra = extra + eta * out[1]
+        if scale0 and model.r == 0 and not getattr(model, "scaled", False):
+            sv, yv = eta * p, eta * Ap
+            model.d = np.full(n, float(yv @ sv) / float(sv @ sv))
+            model.scaled = True
         model.update(eta * p, eta * Ap)
     kkt = float(np.linalg.norm(np.minimum(x, g)))
     hist.append(kkt)
@@ -270,7 +274,7 @@ class BiPQNResult:
 
 
 def bi_pqn(mvp_hi, mvp_lo, b, x_init, tol=1e-8, kmax=50, kmax_inner=100,
-           forcing=1e-3, r_max=32):
+           forcing=1e-3, r_max=32, scale0=False):
     """Algorithm 4 (Bi-PQN) with B^(0) = A_hat.
 
     The subproblem min_{z>=0} 1/2 z^T B z + (g - B x)^T z (Eq. pqnSubproblem)
@@ -281,7 +285,8 @@ def bi_pqn(mvp_hi, mvp_lo, b, x_init, tol=1e-8, kmax=50, kmax_inner=100,
     b = np.asarray(b, float)
     n = b.shape[0]
     # low-fidelity initialisation (Sec. 5.2)
-    init = mono_pqn(mvp_lo, b, x_init, tol=tol, kmax=kmax_inner, r_max=r_max)
+    init = mono_pqn(mvp_lo, b, x_init, tol=tol, kmax=kmax_inner, r_max=r_max, scale0=scale0)
+    d_inner = init.model.d
     lo = init.mvps
     S_low = list(init.model.S)
     Y_low = list(init.model.Y)
@@ -306,7 +311,7 @@ def bi_pqn(mvp_hi, mvp_lo, b, x_init, tol=1e-8, kmax=50, kmax_inner=100,
         hist.append(kkt)
         if kkt <= tol:
             return BiPQNResult(x, g, k, hi, lo, kkt, True, hist)
-        sub = mono_pqn(sub_mvp, b, x, tol=max(0.1 * tol, forcing * kkt), kmax=kmax_inner,
+        sub = mono_pqn(sub_mvp, b, x, tol=max(0.1 * tol, forcing * kkt), kmax=kmax_inner, d=d_inner,
                        pairs=list(zip(S_low, Y_low)), r_max=r_max, g0=g, extra_mvp=True)
         lo += sub.mvps
         p = sub.x - x

@@ -16,7 +16,7 @@ LCP_ERR_NUMERICAL = -5
 LCP_ERR_TIMEOUT = -6
 LCP_ERR_REJECTED = -8
 LCP_FP64, LCP_MIXED, LCP_DF64 = 0, 1, 2
-LCP_MONO_PQN, LCP_BI_PQN = 0, 1
+LCP_MONO_PQN, LCP_BI_PQN, LCP_BB_PGD = 0, 1, 2
 LCP_HIGH, LCP_LOW_RPY = 0, 1
 
 STATUS_NAMES = {0: "LCP_OK", -1: "LCP_ERR_INVALID_ARG", -2: "LCP_ERR_OOM", -3: "LCP_ERR_CUDA",
@@ -33,7 +33,8 @@ class lcp_config(ctypes.Structure):
                 ("ir_maxit", ctypes.c_int), ("kmax", ctypes.c_int), ("kmax_inner", ctypes.c_int),
                 ("memory", ctypes.c_int), ("ssn_maxit", ctypes.c_int), ("forcing", ctypes.c_double),
                 ("precondition", ctypes.c_int), ("residual_precision", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("own_stream", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("autotune", ctypes.c_int), ("own_stream", ctypes.c_int), ("h0_scaling", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class lcp_contact(ctypes.Structure):
@@ -48,7 +49,8 @@ class lcp_stats(ctypes.Structure):
                 ("fp32_applies", ctypes.c_int), ("kkt_abs", ctypes.c_double),
                 ("kkt_dot", ctypes.c_double), ("e_mvps", ctypes.c_double),
                 ("hi_mvp_seconds", ctypes.c_double), ("lo_mvp_seconds", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("df64_applies", ctypes.c_int)]
+                ("seconds", ctypes.c_double), ("df64_applies", ctypes.c_int), ("resets", ctypes.c_int),
+                ("ssn_iterations", ctypes.c_int), ("ssn_fallbacks", ctypes.c_int), ("h0_delta", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -52,6 +52,7 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->residual_precision = LCP_DF64;
   c->autotune = 0;
   c->own_stream = 0;
+  c->h0_scaling = 1;
   c->cuda_stream = nullptr;
 }
 
@@ -482,13 +483,13 @@ extern "C" int lcp_apply_A(lcp_ctx* ctx, const double* x, double* Ax, int fideli
 
 extern "C" int lcp_solve_dev(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st) {
   if (!ctx || (ctx->n && !x) || !(tol >= 0.0)) return LCP_ERR_INVALID_ARG;
-  if (method != LCP_MONO_PQN && method != LCP_BI_PQN) { ctx->err = "unknown method"; return LCP_ERR_INVALID_ARG; }
+  if (method != LCP_MONO_PQN && method != LCP_BI_PQN && method != LCP_BB_PGD) { ctx->err = "unknown method"; return LCP_ERR_INVALID_ARG; }
   return lcp_solve_device(ctx, method, tol, x0, x, st);
 }
 
 extern "C" int lcp_solve(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st) {
   if (!ctx || (ctx->n && !x) || !(tol >= 0.0)) return LCP_ERR_INVALID_ARG;
-  if (method != LCP_MONO_PQN && method != LCP_BI_PQN) { ctx->err = "unknown method"; return LCP_ERR_INVALID_ARG; }
+  if (method != LCP_MONO_PQN && method != LCP_BI_PQN && method != LCP_BB_PGD) { ctx->err = "unknown method"; return LCP_ERR_INVALID_ARG; }
   const int n = ctx->n;
   const double* x0d = nullptr;
   if (x0 && n) {

@@ -30,7 +30,7 @@ constexpr int PQN_W = PQN_T / 32;
 // scal slots of a PqnDev
 enum {
   S_KKT = 0, S_KKTDOT = 1, S_FLAG = 2, S_ETA = 3, S_SSN_IT = 4, S_SSN_FAIL = 5, S_PG = 6, S_PAP = 7,
-  S_ACCEPT = 8, S_BLK = 9, S_NSCAL = 16
+  S_ACCEPT = 8, S_BLK = 9, S_TAU = 10, S_DELTA = 11, S_DSET = 12, S_NSCAL = 16
 };
 
 // Per-run workspace laid out after the PqnDev vectors (device pointers).
@@ -42,6 +42,11 @@ struct PqnWork {
 };
 
 __device__ __forceinline__ double bsum(double v, double* red) { return block_sum(v, red); }
+
+// Scale of the initial model B_0 = delta I (H_0 = I / delta); 1 until set.
+__device__ __forceinline__ double delta_of(const PqnDev& pq) {
+  return pq.scal[S_DSET] != 0.0 ? pq.scal[S_DELTA] : 1.0;
+}
 
 // out[k] = M[k] . v for k < rows (warp per row, fixed lane order).  out in smem or global.
 __device__ void bmultidot(const double* __restrict__ Mt, int n, int rows, const double* __restrict__ v,
@@ -123,6 +128,9 @@ __device__ void two_loop(const PqnDev& pq, const PqnWork& wk, int r, const doubl
     for (int i = threadIdx.x; i < n; i += blockDim.x) q[i] -= a * y[i];
     __syncthreads();
   }
+  const double hd = 1.0 / delta_of(pq);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) q[i] *= hd;
+  __syncthreads();
   for (int k = 0; k < r; k++) {
     const double* s = pq.S + (size_t)k * n;
     const double* y = pq.Y + (size_t)k * n;
@@ -185,9 +193,11 @@ __device__ double ssn_residual(const PqnDev& pq, const PqnWork& wk, int r, const
     sm.c[k] = s;
   }
   __syncthreads();
+  const double idl = 1.0 / delta_of(pq);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double y = xt[i];
+    double y = 0.0;
     for (int k = 0; k < r; k++) y += pq.V[(size_t)k * n + i] * at[k] - pq.U[(size_t)k * n + i] * sm.c[k];
+    y = xt[i] + idl * y;
     const double z = y > 0.0 ? y : 0.0;
     wk.z[i] = z;
     wk.lam[i] = y > 0.0 ? 1.f : 0.f;
@@ -197,8 +207,9 @@ __device__ double ssn_residual(const PqnDev& pq, const PqnWork& wk, int r, const
   bmultidot(pq.U, n, r, wk.d, sm.udv);
   bmultidot(pq.V, n, r, wk.d, sm.udv + r);
   for (int k = threadIdx.x; k < r; k += blockDim.x) {
-    double s = a[k] + sm.udv[k];
+    double s = 0.0;
     for (int l = 0; l < r; l++) s += sm.UCV[k * r + l] * at[l];
+    s = a[k] + sm.udv[k] + idl * s;
     G[k] = s;
     G[r + k] = at[k] + sm.udv[r + k];
   }
@@ -223,7 +234,7 @@ __device__ int prox_ssn(const PqnDev& pq, const PqnWork& wk, int r, const double
   // small = I + U^T U (in tmp), X = small^{-1} U^T V
   for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
     const int k = t / r, l = t % r;
-    sm.tmp[t] = pq.UU[k * R + l] + (k == l ? 1.0 : 0.0);
+    sm.tmp[t] = pq.UU[k * R + l] + (k == l ? delta_of(pq) : 0.0);
     sm.X[t] = pq.UV[k * R + l];
   }
   __syncthreads();
@@ -278,6 +289,7 @@ __device__ int prox_ssn(const PqnDev& pq, const PqnWork& wk, int r, const double
     }
     __syncthreads();
     const int m2 = 2 * r;
+    const float jscale = (float)(1.0 / delta_of(pq));
     for (int t = threadIdx.x; t < m2 * m2; t += blockDim.x) {
       const int row = t / m2, col = t % m2;
       float v;
@@ -290,7 +302,7 @@ __device__ int prox_ssn(const PqnDev& pq, const PqnWork& wk, int r, const double
         const int k = row - r, l = col - r;
         v = -(sm.GVV[k * r + l] - sm.T2[k * r + l]);
       }
-      sm.J[t] = v + (row == col ? 1.f : 0.f);
+      sm.J[t] = v * jscale + (row == col ? 1.f : 0.f);
     }
     for (int k = threadIdx.x; k < m2; k += blockDim.x) sm.gf[k] = (float)sm.G[k];
     __syncthreads();
@@ -338,8 +350,8 @@ __device__ int prox_ssn(const PqnDev& pq, const PqnWork& wk, int r, const double
         }
         gr = warp_sum(gr);
         bll = warp_sum(bll);
-        gr += zout[l] - xt[l];
-        bll += 1.0;
+        gr += delta_of(pq) * (zout[l] - xt[l]);
+        bll += delta_of(pq);
         const double zn = fmax(0.0, zout[l] - gr / bll);
         const double dz = zn - zout[l];
         const double kk = fabs(fmin(zout[l], gr));
@@ -394,7 +406,9 @@ __global__ void __launch_bounds__(PQN_T) k_pqn_direction(PqnDev pq, PqnWork wk, 
   __shared__ double alpha[128];
   const int n = pq.n;
   const int r = *pq.r;
-  two_loop(pq, wk, r, pq.g, pq.xt, alpha, red);
+  two_loop(pq, wk, r, pq.g, pq.xt, alpha, red);     // xt = H g
+  for (int i = threadIdx.x; i < n; i += blockDim.x) pq.xt[i] = pq.x[i] - pq.xt[i];   // x_tilde = x - H g
+  __syncthreads();
   const int it = prox_ssn(pq, wk, r, pq.xt, pq.xh, smem, red, jmax);
   double part = 0.0, amax = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -467,8 +481,9 @@ __device__ double apply_B(const PqnDev& pq, int r, const double* s, double* Bs, 
   bmultidot(pq.U, n, r, s, tmp);
   bmultidot(pq.V, n, r, s, tmp + 64);
   double part = 0.0;
+  const double dl = delta_of(pq);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double v = s[i];
+    double v = dl * s[i];
     for (int k = 0; k < r; k++) v += pq.U[(size_t)k * n + i] * tmp[k] - pq.V[(size_t)k * n + i] * tmp[64 + k];
     Bs[i] = v;
     part += s[i] * v;
@@ -517,7 +532,8 @@ __global__ void __launch_bounds__(PQN_T) k_pqn_rebuild(PqnDev pq, PqnWork wk) {
 // Step of Algorithm 1 after the MVP Ap = A[p] (and lop = A_hat[p] when the
 // extra accumulation of Appendix D.2 is tracked): Algorithm 2, the updates of
 // x and g, and the BFGS update.  quasi_newton = 0 skips the BFGS update.
-__global__ void __launch_bounds__(PQN_T) k_pqn_step(PqnDev pq, PqnWork wk, int track_extra, int quasi_newton) {
+__global__ void __launch_bounds__(PQN_T) k_pqn_step(PqnDev pq, PqnWork wk, int track_extra, int quasi_newton,
+                                                    int scale0) {
   __shared__ double red[32];
   __shared__ double tmp[256];
   __shared__ double bestv[PQN_W];
@@ -584,6 +600,15 @@ __global__ void __launch_bounds__(PQN_T) k_pqn_step(PqnDev pq, PqnWork wk, int t
       a3 += wk.z[i] * wk.z[i];
     }
     const double ys = block_sum(a1, red), ss = block_sum(a2, red), yy = block_sum(a3, red);
+    if (scale0 && r == 0 && pq.scal[S_DSET] == 0.0 && ys > 0.0 && ss > 0.0) {
+      // B_0 = delta I with delta = y^T s / s^T s of the first step
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        pq.scal[S_DELTA] = ys / ss;
+        pq.scal[S_DSET] = 1.0;
+      }
+      __syncthreads();
+    }
     const double sBs = apply_B(pq, r, wk.d, wk.q, tmp, red);
     if (ys > 1e-12 * sqrt(ss) * sqrt(yy) && sBs > 0.0) {
       accepted = 1.0;
@@ -802,6 +827,51 @@ __global__ void k_mdx(int m6, const double* __restrict__ uo, const double* __res
   mdx[i] = init ? uo[i] : mdx[i] + scal[S_ETA] * uo[i];
 }
 
+// BB-PGD (Sec. 6, Eq. spectralStepSize; Table 1: over-relaxation 1):
+// p = (x - tau g)_+ - x.
+__global__ void __launch_bounds__(PQN_T) k_pgd_direction(PqnDev pq) {
+  __shared__ double red[32];
+  const double tau = pq.scal[S_TAU];
+  double nz = 0.0;
+  for (int i = threadIdx.x; i < pq.n; i += blockDim.x) {
+    const double p = fmax(pq.x[i] - tau * pq.g[i], 0.0) - pq.x[i];
+    pq.p[i] = p;
+    nz += p != 0.0 ? 1.0 : 0.0;
+  }
+  nz = block_sum(nz, red);
+  if (threadIdx.x == 0) pq.scal[S_FLAG] = nz == 0.0 ? 1.0 : 0.0;
+}
+
+// x += p, g += A p, tau = p^T p / p^T A p (tau0 if not positive), KKT.
+__global__ void __launch_bounds__(PQN_T) k_pgd_step(PqnDev pq, double tau0) {
+  __shared__ double red[32];
+  double a = 0.0, c = 0.0, k1 = 0.0, k2 = 0.0;
+  for (int i = threadIdx.x; i < pq.n; i += blockDim.x) {
+    const double p = pq.p[i], ap = pq.Ap[i];
+    a += p * p;
+    c += p * ap;
+    const double x = fmax(pq.x[i] + p, 0.0);
+    const double g = pq.g[i] + ap;
+    pq.x[i] = x;
+    pq.g[i] = g;
+    const double m = fmin(x, g);
+    k1 += m * m;
+    k2 += x * g;
+  }
+  a = block_sum(a, red);
+  c = block_sum(c, red);
+  k1 = block_sum(k1, red);
+  k2 = block_sum(k2, red);
+  if (threadIdx.x == 0) {
+    pq.scal[S_TAU] = c > 0.0 ? a / c : tau0;
+    pq.scal[S_ETA] = 1.0;
+    pq.scal[S_KKT] = sqrt(k1);
+    pq.scal[S_KKTDOT] = k2;
+  }
+}
+
+__global__ void k_set_scalar(double* slot, double v) { *slot = v; }
+
 __global__ void k_copy(int n, const double* a, double* b) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = a[i];
@@ -899,7 +969,7 @@ static int mvp_sub(lcp_ctx* ctx, PqnDev& pq, const double* v) {
 }
 
 struct RunStats {
-  int iterations = 0, mvps = 0;
+  int iterations = 0, mvps = 0, resets = 0;
   double kkt = 0.0, kktdot = 0.0, t_mvp = 0.0;
   bool converged = false;
 };
@@ -935,6 +1005,7 @@ static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* 
     LCP_CUDA(cudaGetLastError());
     LCP_TRY(read_scal(ctx, pq, sc));
     if (sc[S_FLAG] == 1.0) break;  // p = 0: stationary
+    if (sc[S_FLAG] == 2.0) rs->resets++;
     t0 = now_s();
     if (sub) {
       LCP_TRY(mvp_sub(ctx, pq, pq.p));
@@ -944,7 +1015,7 @@ static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* 
     LCP_CUDA(cudaStreamSynchronize(ctx->stream));
     rs->t_mvp += now_s() - t0;
     rs->mvps++;
-    ++ctx->nlaunch, k_pqn_step<<<1, PQN_T, 0, ctx->stream>>>(pq, wk, sub, 1);
+    ++ctx->nlaunch, k_pqn_step<<<1, PQN_T, 0, ctx->stream>>>(pq, wk, sub, 1, ctx->cfg.h0_scaling);
     if (track) ++ctx->nlaunch, k_mdx<<<(m6 + 127) / 128, 128, 0, ctx->stream>>>(m6, ctx->UO, pq.scal, 0, ctx->MDx);
     LCP_CUDA(cudaGetLastError());
     LCP_TRY(read_scal(ctx, pq, sc));
@@ -990,6 +1061,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
     ++ctx->nlaunch, k_pqn_init<<<1, PQN_T, 0, ctx->stream>>>(po, x0);
     LCP_TRY(run_mono(ctx, po, mvp_high, 0, ctx->b, nullptr, tol, ctx->cfg.kmax, &rs));
     s.iterations = rs.iterations;
+    s.resets = rs.resets;
     s.hi_mvps = rs.mvps;
     s.kkt_abs = rs.kkt;
     s.kkt_dot = rs.kktdot;
@@ -1031,6 +1103,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
       LCP_TRY(run_mono(ctx, pi, nullptr, 1, nullptr, po.g, tin, ctx->cfg.kmax_inner, &rs));
       lo += rs.mvps;
       t_lo += rs.t_mvp;
+      s.resets += rs.resets;
       inner_total += rs.iterations;
       ++ctx->nlaunch, k_bi_direction<<<1, PQN_T, 0, ctx->stream>>>(po, pi.x);
       LCP_TRY(read_scal(ctx, po, sc));
@@ -1068,12 +1141,59 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
     s.lo_mvp_seconds = lo ? t_lo / lo : 0.0;
     s.e_mvps = hi + (s.hi_mvp_seconds > 0 ? lo * s.lo_mvp_seconds / s.hi_mvp_seconds : 0.0);
     ++ctx->nlaunch, k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, po.x, x);
+  } else if (method == LCP_BB_PGD) {
+    // BB-PGD baseline of Sec. 6: one MVP per iteration; tau_0 = 3 pi mu a
+    const double tau0 = 3.0 * LCP_PI * ctx->cfg.viscosity * ctx->cfg.radius;
+    const int m6 = 6 * ctx->M;
+    ++ctx->nlaunch, k_pqn_init<<<1, PQN_T, 0, ctx->stream>>>(po, x0);
+    double t0 = now_s(), t_hi = 0.0;
+    LCP_TRY(mvp_high(ctx, po.x, po.Ap));
+    ++ctx->nlaunch, k_mdx<<<(m6 + 127) / 128, 128, 0, ctx->stream>>>(m6, ctx->UO, po.scal, 1, ctx->MDx);
+    LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+    t_hi += now_s() - t0;
+    int hi = 1;
+    ++ctx->nlaunch, k_pqn_grad<<<1, PQN_T, 0, ctx->stream>>>(po, po.Ap, ctx->b, nullptr);
+    ++ctx->nlaunch, k_set_scalar<<<1, 1, 0, ctx->stream>>>(po.scal + S_TAU, tau0);
+    LCP_TRY(read_scal(ctx, po, sc));
+    int k = 0;
+    for (; k < ctx->cfg.kmax; k++) {
+      if (!(sc[S_KKT] == sc[S_KKT])) { ctx->err = "BB-PGD: NaN in the KKT error"; return LCP_ERR_NUMERICAL; }
+      if (sc[S_KKT] <= tol) break;
+      ++ctx->nlaunch, k_pgd_direction<<<1, PQN_T, 0, ctx->stream>>>(po);
+      LCP_TRY(read_scal(ctx, po, sc));
+      if (sc[S_FLAG] == 1.0) break;
+      t0 = now_s();
+      LCP_TRY(mvp_high(ctx, po.p, po.Ap));
+      LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+      t_hi += now_s() - t0;
+      hi++;
+      ++ctx->nlaunch, k_pgd_step<<<1, PQN_T, 0, ctx->stream>>>(po, tau0);
+      ++ctx->nlaunch, k_mdx<<<(m6 + 127) / 128, 128, 0, ctx->stream>>>(m6, ctx->UO, po.scal, 0, ctx->MDx);
+      LCP_TRY(read_scal(ctx, po, sc));
+    }
+    s.iterations = k;
+    s.hi_mvps = hi;
+    s.kkt_abs = sc[S_KKT];
+    s.kkt_dot = sc[S_KKTDOT];
+    s.converged = sc[S_KKT] <= tol;
+    s.hi_mvp_seconds = t_hi / hi;
+    s.e_mvps = hi;
+    ++ctx->nlaunch, k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, po.x, x);
   } else {
     ctx->err = "unknown method";
     return LCP_ERR_INVALID_ARG;
   }
   LCP_CUDA(cudaGetLastError());
   LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+  {
+    double a[S_NSCAL], b2[S_NSCAL];
+    LCP_TRY(read_scal(ctx, po, a));
+    LCP_TRY(read_scal(ctx, pi, b2));
+    s.ssn_iterations = (int)(a[S_SSN_IT] + b2[S_SSN_IT]);
+    s.ssn_fallbacks = (int)(a[S_SSN_FAIL] + b2[S_SSN_FAIL]);
+    s.h0_delta = method == LCP_BI_PQN ? (b2[S_DSET] != 0.0 ? b2[S_DELTA] : 1.0)
+                                      : (a[S_DSET] != 0.0 ? a[S_DELTA] : 1.0);
+  }
   s.gmres_iterations = ctx->c_gmres;
   s.fp32_applies = ctx->c_fp32;
   s.fp64_applies = ctx->c_fp64;

@@ -24,7 +24,7 @@
 extern "C" int lcp_batch_solve(lcp_ctx** ctxs, int count, int method, double tol, double* const* x_dev,
                                lcp_stats* stats, int* statuses, int workers) {
   if (count < 0 || (count > 0 && (!ctxs || !statuses)) || workers < 1 || !(tol >= 0.0)) return LCP_ERR_INVALID_ARG;
-  if (method != LCP_MONO_PQN && method != LCP_BI_PQN) return LCP_ERR_INVALID_ARG;
+  if (method != LCP_MONO_PQN && method != LCP_BI_PQN && method != LCP_BB_PGD) return LCP_ERR_INVALID_ARG;
   for (int i = 0; i < count; i++)
     if (!ctxs[i]) return LCP_ERR_INVALID_ARG;
   std::atomic<int> next(0);
@@ -157,7 +157,7 @@ extern "C" int lcp_server_release(lcp_server* s, lcp_ctx* ctx) {
 
 extern "C" int lcp_server_submit(lcp_server* s, lcp_ctx* ctx, int method, double tol, uint64_t* ticket) {
   if (!s || !ctx || !ticket || !(tol >= 0.0)) return LCP_ERR_INVALID_ARG;
-  if (method != LCP_MONO_PQN && method != LCP_BI_PQN) return LCP_ERR_INVALID_ARG;
+  if (method != LCP_MONO_PQN && method != LCP_BI_PQN && method != LCP_BB_PGD) return LCP_ERR_INVALID_ARG;
   {
     std::lock_guard<std::mutex> lock(s->mu);
     if (!s->admitted.count(ctx)) return LCP_ERR_REJECTED;

@@ -272,3 +272,20 @@ def test_short_trajectory_mixed_bi_pqn():
         np.testing.assert_allclose(np.linalg.norm(a, axis=1), 1.0, rtol=1e-12)
     finally:
         L.lcp_destroy(ctx)
+
+
+@pytest.mark.parametrize("index", [0, 1, 3])
+def test_bb_pgd_baseline_matches_oracle(index):
+    """The BB-PGD comparison method of Sec. 6 on the GPU: same solution, same MVP count as the oracle's."""
+    from oracle.pgd import bb_pgd
+    case = dense_case("spheres8_grid7x14", index)
+    inst = case["inst"]
+    ctx = L.lcp_setup(L.config_for(inst), inst.centers, inst.axes)
+    try:
+        x, st, _ = L.lcp_solve(ctx, L.LCP_BB_PGD, inst.tol)
+        check_solution(case, x, inst.tol)
+        _, _, it, mvps, ok = bb_pgd(lambda v: case["A"] @ v, case["b"], np.zeros(case["b"].size),
+                                    tau0=3 * np.pi * inst.viscosity * inst.radius, tol=inst.tol)
+        assert ok and abs(st["hi_mvps"] - mvps) <= 1
+    finally:
+        L.lcp_destroy(ctx)

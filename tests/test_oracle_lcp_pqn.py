@@ -131,9 +131,10 @@ def test_mono_pqn_reduces_to_cg_without_active_constraints():
         cg.append(x.copy())
     assert res.converged and res.iterations <= n
     np.testing.assert_allclose(res.x, xstar, rtol=1e-10)
-    # replay: the first few iterates coincide with CG's
-    replay = P.mono_pqn(lambda v: A @ v, b, x0, tol=0.0, kmax=3)
-    np.testing.assert_allclose(replay.x, cg[3], rtol=1e-9)
+    # replay: the first few iterates coincide with CG's, with B_0 = I and with B_0 = delta I
+    for scale0 in (False, True):
+        replay = P.mono_pqn(lambda v: A @ v, b, x0, tol=0.0, kmax=3, scale0=scale0)
+        np.testing.assert_allclose(replay.x, cg[3], rtol=1e-9)
 
 
 def dense_instance(name, index):
@@ -229,3 +230,29 @@ def _secant_trace(sign):
 def test_bi_pqn_secant_carry_over_identity():
     assert _secant_trace(+1) <= 1e-10
     assert _secant_trace(-1) > 1e-6      # the printed sign breaks the identity
+
+
+@pytest.mark.parametrize("index", range(3))
+def test_bb_pgd_converges_to_the_lcp_solution(index):
+    from oracle.pgd import bb_pgd
+    inst, A, b, _ = dense_instance("spheres8_grid7x14", index)
+    xs = pgs(A, b)
+    x, g, it, mvps, ok = bb_pgd(lambda v: A @ v, b, np.zeros(b.size), tau0=3 * np.pi, tol=inst.tol)
+    assert ok and mvps == it + 1
+    np.testing.assert_allclose(x, xs, atol=1e-6)
+    np.testing.assert_allclose(g, A @ x + b, atol=1e-12)
+
+
+def test_bb_step_is_the_inverse_rayleigh_quotient_on_a_quadratic():
+    """With no active constraint the second step uses tau = s^T s / s^T A s."""
+    from oracle.pgd import bb_pgd
+    rng = np.random.default_rng(5)
+    A = random_spd(6, rng)
+    xstar = rng.uniform(20, 30, 6)
+    b = -A @ xstar
+    x0 = xstar + rng.uniform(-1, 1, 6)
+    x1, g1, *_ = bb_pgd(lambda v: A @ v, b, x0, tau0=0.1, tol=0.0, kmax=1)
+    s = x1 - x0
+    tau = (s @ s) / (s @ A @ s)
+    x2, *_ = bb_pgd(lambda v: A @ v, b, x0, tau0=0.1, tol=0.0, kmax=2)
+    np.testing.assert_allclose(x2, x1 - tau * (A @ x1 + b), rtol=1e-12)
