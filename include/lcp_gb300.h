@@ -189,7 +189,8 @@ LCP_API int lcp_server_stats(lcp_server* srv, size_t* resident_bytes, int* queue
 /* Kernel timing.  lcp_profile(ctx, 1) clears the record and starts timing
  * every stresslet-sum launch with CUDA events on the context's stream;
  * lcp_profile(ctx, 0) stops and clears.  lcp_profile_read returns the number
- * of launches of a kind (0 = FP32, 1 = FP64, 2 = double-FP32 pair sum) and their
+ * of launches of a kind (0 = FP32, 1 = FP64, 2 = double-FP32 pair sum; 3 = PQN direction,
+ * 4 = PQN step, 5 = quasi-Newton rebuild, 6 = low-fidelity MVP) and their
  * summed duration in milliseconds (synchronises the stream). */
 LCP_API int lcp_profile(lcp_ctx* ctx, int enable);
 LCP_API int lcp_profile_read(lcp_ctx* ctx, int kind, int* count, double* total_ms);

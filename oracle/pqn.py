@@ -109,7 +109,9 @@ class QNModel:
         self.Y.append(y)
         self.B0S.append(b0s)
         if len(self.S) > self.r_max:
-            self.S.pop(0), self.Y.pop(0), self.B0S.pop(0)
+            # memory full: the oldest quarter of the pairs is dropped at once
+            drop = max(1, self.r_max // 4)
+            del self.S[:drop], self.Y[:drop], self.B0S[:drop]
             self.U, self.V = [], []
             for s_, y_, b_ in zip(self.S, self.Y, self.B0S):
                 self._append_uv(s_, y_, b_)

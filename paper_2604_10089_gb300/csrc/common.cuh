@@ -175,6 +175,24 @@ struct lcp_ctx {
     if (s_ != LCP_OK) return s_;       \
   } while (0)
 
+// Event timing of a launch (lcp_profile): returns the start event or null.
+inline cudaEvent_t prof_begin(lcp_ctx* ctx) {
+  if (!ctx->prof) return nullptr;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  cudaEventRecord(e, ctx->stream);
+  return e;
+}
+inline void prof_end(lcp_ctx* ctx, cudaEvent_t start, int kind) {
+  if (!start) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, ctx->stream);
+  ctx->ev_pool.push_back(start);
+  ctx->ev_pool.push_back(e);
+  ctx->ev_kind.push_back(kind);
+}
+
 // Internal launch helpers implemented in the .cu files.
 int geometry_build(lcp_ctx* ctx);
 int geometry_update(lcp_ctx* ctx);

@@ -112,6 +112,53 @@ __device__ void block_solve(T* A, int lda, T* B, int ldb, int m, int nr, int* pi
   }
 }
 
+// Same system solved by warp 0 alone (no block barriers): partial pivoting by a
+// warp-wide argmax, lanes own rows during elimination and back substitution.
+// The other warps wait at the barrier that ends the call.
+template <typename T>
+__device__ void warp_solve(T* A, int lda, T* B, int ldb, int m, int nr) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int k = 0; k < m; k++) {
+      T best = -1;
+      int arg = k;
+      for (int i = k + lane; i < m; i += 32) {
+        const T v = fabs(A[i * lda + k]);
+        if (v > best) { best = v; arg = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (ov > best || (ov == best && oa < arg)) { best = ov; arg = oa; }
+      }
+      if (arg != k) {
+        for (int j = lane; j < m; j += 32) { const T t = A[k * lda + j]; A[k * lda + j] = A[arg * lda + j]; A[arg * lda + j] = t; }
+        for (int j = lane; j < nr; j += 32) { const T t = B[k * ldb + j]; B[k * ldb + j] = B[arg * ldb + j]; B[arg * ldb + j] = t; }
+      }
+      __syncwarp();
+      const T inv = T(1) / A[k * lda + k];
+      for (int i = k + 1 + lane; i < m; i += 32) {
+        const T f = A[i * lda + k] * inv;
+        for (int j = k + 1; j < m; j++) A[i * lda + j] -= f * A[k * lda + j];
+        for (int j = 0; j < nr; j++) B[i * ldb + j] -= f * B[k * ldb + j];
+        A[i * lda + k] = 0;
+      }
+      __syncwarp();
+    }
+    for (int k = m - 1; k >= 0; k--) {
+      const T d = A[k * lda + k];
+      for (int j = lane; j < nr; j += 32) B[k * ldb + j] /= d;
+      __syncwarp();
+      for (int i = lane; i < k; i += 32) {
+        const T f = A[i * lda + k];
+        for (int j = 0; j < nr; j++) B[i * ldb + j] -= f * B[k * ldb + j];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
 // q = H g with H_0 = I (Nocedal-Wright two-loop recursion over the r pairs).
 __device__ void two_loop(const PqnDev& pq, const PqnWork& wk, int r, const double* g, double* q, double* alpha,
                          double* red) {
@@ -238,7 +285,7 @@ __device__ int prox_ssn(const PqnDev& pq, const PqnWork& wk, int r, const double
     sm.X[t] = pq.UV[k * R + l];
   }
   __syncthreads();
-  block_solve<double>(sm.tmp, r, sm.X, r, r, r, sm.piv);
+  warp_solve<double>(sm.tmp, r, sm.X, r, r, r);
   // UCV = UV - UU X ; VCV = VV - UV^T X
   for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
     const int k = t / r, l = t % r;
@@ -264,16 +311,24 @@ __device__ int prox_ssn(const PqnDev& pq, const PqnWork& wk, int r, const double
   bool ok = false;
   for (; j < jmax; j++) {
     if (gn <= 1e-13 * scale) { ok = true; break; }
-    // masked Grams in FP32
-    for (int t = threadIdx.x; t < 3 * r * r; t += blockDim.x) {
-      const int which = t / (r * r), e = t % (r * r), k = e / r, l = e % r;
-      const float* A = which == 2 ? wk.V32 : (which == 1 ? wk.V32 : wk.U32);
-      const float* Bm = which == 2 ? wk.V32 : wk.U32;
-      const float* ak = A + (size_t)k * n;
-      const float* bl = Bm + (size_t)l * n;
-      float s = 0.f;
-      for (int i = 0; i < n; i++) s = fmaf(ak[i] * wk.lam[i], bl[i], s);
-      (which == 0 ? sm.GUU : which == 1 ? sm.GVU : sm.GVV)[e] = s;
+    // masked Grams in FP32: one warp per entry, lanes stride the contacts
+    // (coalesced); the symmetric U^T L U and V^T L V only for l >= k
+    {
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      for (int t = wid; t < 3 * r * r; t += PQN_W) {
+        const int which = t / (r * r), e = t % (r * r), k = e / r, l = e % r;
+        if (which != 1 && l < k) continue;
+        const float* ak = (which == 0 ? wk.U32 : wk.V32) + (size_t)k * n;
+        const float* bl = (which == 2 ? wk.V32 : wk.U32) + (size_t)l * n;
+        float acc = 0.f;
+        for (int i = lane; i < n; i += 32) acc = fmaf(ak[i] * wk.lam[i], bl[i], acc);
+        acc = warp_sumf(acc);
+        if (lane == 0) {
+          float* G = which == 0 ? sm.GUU : (which == 1 ? sm.GVU : sm.GVV);
+          G[k * r + l] = acc;
+          if (which != 1) G[l * r + k] = acc;
+        }
+      }
     }
     __syncthreads();
     // T1 = GUU X, T2 = GVU X
@@ -306,7 +361,7 @@ __device__ int prox_ssn(const PqnDev& pq, const PqnWork& wk, int r, const double
     }
     for (int k = threadIdx.x; k < m2; k += blockDim.x) sm.gf[k] = (float)sm.G[k];
     __syncthreads();
-    block_solve<float>(sm.J, m2, sm.gf, 1, m2, 1, sm.piv);
+    warp_solve<float>(sm.J, m2, sm.gf, 1, m2, 1);
     // backtracking on ||G||
     double t = 1.0;
     for (int bt = 0; bt < 30; bt++) {
@@ -616,20 +671,22 @@ __global__ void __launch_bounds__(PQN_T) k_pqn_step(PqnDev pq, PqnWork wk, int t
         append_pair(pq, wk, r, wk.d, wk.z, ys, sBs, wk.q, red, tmp);
         r++;
       } else {
-        // FIFO: drop the oldest pair, append, rebuild the unrolled factors
-        for (int k = 0; k + 1 < r; k++) {
+        // memory full: drop the oldest quarter of the pairs at once (so the
+        // unrolled factors are rebuilt once per rmax/4 steps), append, rebuild
+        const int drop = max(1, pq.rmax / 4);
+        for (int k = 0; k + drop < r; k++) {
           for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            pq.S[(size_t)k * n + i] = pq.S[(size_t)(k + 1) * n + i];
-            pq.Y[(size_t)k * n + i] = pq.Y[(size_t)(k + 1) * n + i];
+            pq.S[(size_t)k * n + i] = pq.S[(size_t)(k + drop) * n + i];
+            pq.Y[(size_t)k * n + i] = pq.Y[(size_t)(k + drop) * n + i];
           }
-          __syncthreads();
-        }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          pq.S[(size_t)(r - 1) * n + i] = wk.d[i];
-          pq.Y[(size_t)(r - 1) * n + i] = wk.z[i];
         }
         __syncthreads();
-        r = rebuild(pq, wk, r, red, tmp);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          pq.S[(size_t)(r - drop) * n + i] = wk.d[i];
+          pq.Y[(size_t)(r - drop) * n + i] = wk.z[i];
+        }
+        __syncthreads();
+        r = rebuild(pq, wk, r - drop + 1, red, tmp);
       }
       __syncthreads();
       if (threadIdx.x == 0) *pq.r = r;
@@ -962,7 +1019,9 @@ static double now_s() {
 
 // Inner MVP of Bi-PQN subproblems: lop = A_hat[v]; Ap = lop + U_h U_h^T v - V_h V_h^T v.
 static int mvp_sub(lcp_ctx* ctx, PqnDev& pq, const double* v) {
+  cudaEvent_t ev = prof_begin(ctx);
   LCP_TRY(mvp_low(ctx, v, pq.lop));
+  prof_end(ctx, ev, 6);
   ++ctx->nlaunch, k_bi_lowrank<<<1, PQN_T, 0, ctx->stream>>>(pq.n, ctx->nh, ctx->Uh, ctx->Vh, v, pq.lop, pq.Ap);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
@@ -1001,7 +1060,9 @@ static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* 
   for (; k < kmax; k++) {
     if (!(sc[S_KKT] == sc[S_KKT])) { ctx->err = "PQN: NaN in the KKT error"; return LCP_ERR_NUMERICAL; }
     if (sc[S_KKT] <= tol) break;
+    cudaEvent_t ev = prof_begin(ctx);
     ++ctx->nlaunch, k_pqn_direction<<<1, PQN_T, smem, ctx->stream>>>(pq, wk, ctx->cfg.ssn_maxit);
+    prof_end(ctx, ev, 3);
     LCP_CUDA(cudaGetLastError());
     LCP_TRY(read_scal(ctx, pq, sc));
     if (sc[S_FLAG] == 1.0) break;  // p = 0: stationary
@@ -1015,7 +1076,9 @@ static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* 
     LCP_CUDA(cudaStreamSynchronize(ctx->stream));
     rs->t_mvp += now_s() - t0;
     rs->mvps++;
+    ev = prof_begin(ctx);
     ++ctx->nlaunch, k_pqn_step<<<1, PQN_T, 0, ctx->stream>>>(pq, wk, sub, 1, ctx->cfg.h0_scaling);
+    prof_end(ctx, ev, 4);
     if (track) ++ctx->nlaunch, k_mdx<<<(m6 + 127) / 128, 128, 0, ctx->stream>>>(m6, ctx->UO, pq.scal, 0, ctx->MDx);
     LCP_CUDA(cudaGetLastError());
     LCP_TRY(read_scal(ctx, pq, sc));
@@ -1096,7 +1159,9 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
       // subproblem (Eq. pqnSubproblem) from x with gradient g, inherited pairs
       ++ctx->nlaunch, k_copy<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, po.x, pi.x);
       ++ctx->nlaunch, k_zero<<<(n + T - 1) / T, T, 0, ctx->stream>>>(n, pi.extra);
+      cudaEvent_t evr = prof_begin(ctx);
       ++ctx->nlaunch, k_pqn_rebuild<<<1, PQN_T, 0, ctx->stream>>>(pi, wk_in);
+      prof_end(ctx, evr, 5);
       LCP_CUDA(cudaGetLastError());
       RunStats rs;
       const double tin = std::max(0.1 * tol, ctx->cfg.forcing * sc[S_KKT]);
