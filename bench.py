@@ -44,7 +44,7 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 # workload (11 on the first configuration).
 REFERENCE_SOLVES_PER_LCP = 12.0
 # DRAM traffic of one k_pair32 launch from an ncu capture (null once the kernel changes).
-PAIR32_TRAFFIC = {"source_sha1": "81299f09e2c1820bb86966afa5ec10ad77dc9029", "bytes_per_launch": 665088}
+PAIR32_TRAFFIC = {"source_sha1": "298b391165dc32f4d22c484bf6d970a4f86ee95e", "bytes_per_launch": 665088}
 
 
 def parse():
@@ -125,11 +125,13 @@ class ClockSampler:
 
 
 def source_sha1():
+    """SHA-1 of the FP32 pair kernel's source text (pair2 .. the variant table)."""
     import hashlib
-    h = hashlib.sha1()
     with open(os.path.join(ROOT, "paper_2604_10089_gb300", "csrc", "stokes.cu"), "rb") as f:
-        h.update(f.read())
-    return h.hexdigest()
+        text = f.read()
+    a = text.find(b"__device__ __forceinline__ void pair2(")
+    b = text.find(b"constexpr int kNumPair32Variants")
+    return hashlib.sha1(text[a:b] if 0 <= a < b else text).hexdigest()
 
 
 def rank_seeds(rank: int, count: int) -> list:

@@ -122,9 +122,15 @@ struct lcp_ctx {
   int num_sms = 0, occ32 = 0, occ64 = 0, occdf = 0;   // pair-kernel grid sizing
   int occ32v[8] = {0};        // occupancy of each FP32 kernel variant
   int v32 = 0;                // FP32 kernel variant in use (autotuned per size class)
+  bool sym = true;            // FP32 sums by the symmetric kernel (stokes_sym.cu)
+  int occsym = 0, sym_ntb = 0, sym_units = 0, sym_grid = 0, sym_slots = 0;
+  int* sym_off = nullptr;          // [ntb + 1] first unit of each target block
+  long long* sym_roff = nullptr;   // [ntb + 1] first float of each block's reverse rows
+  float* sym_rev = nullptr;        // reverse partial sums, one row per unit
   double *V = nullptr, *H = nullptr;  // Krylov basis [(m+1)][3N], Hessenberg etc.
   double* Z = nullptr;                 // preconditioned basis [m][3N] (flexible GMRES)
   float* pinv = nullptr;               // isolated-sphere inverse (3 ns x 3 ns, FP32)
+  float* ppart = nullptr;              // split-k partial products of the preconditioner GEMM
   double *phi = nullptr, *rhs = nullptr, *res = nullptr, *wv = nullptr, *dphi = nullptr;
   float* phi32 = nullptr;
   float* phidf = nullptr;     // [N][6] double-FP32 density (hi xyz, lo xyz)

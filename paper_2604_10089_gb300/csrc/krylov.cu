@@ -14,22 +14,36 @@ namespace {
 constexpr int DOT_THREADS = 256;
 }
 
-// partial[k * G + b] = sum over block b's chunk of V[k][i] * w[i]; the last
-// block to finish reduces the partials in block order into out[k].
+// Fused Gram-Schmidt pass over one chunk of rows per block:
+//   w -= sum_{k < nu} h[k] V[k]            (skipped when nu = 0), then
+//   out[k] = Vd[k] . w  for k < nd          (Vd may be w itself: the norm).
+// Block b owns rows [b c, (b+1) c), so the update and the partial dots of its
+// rows need no grid-wide barrier; partial dots are reduced warp-per-vector,
+// written to partial[k * G + b], and the last block to finish adds them in
+// block order (deterministic).
 __global__ void __launch_bounds__(DOT_THREADS)
-k_dots(int L, int nv, const double* __restrict__ V, size_t ldv, const double* __restrict__ w,
-       double* __restrict__ partial, double* __restrict__ out, unsigned int* __restrict__ counter) {
-  __shared__ double red[DOT_THREADS / 32];
+k_update_dots(int L, int nu, const double* __restrict__ V, size_t ldv, const double* __restrict__ h, double* w,
+              int nd, const double* Vd, size_t ldvd, double* __restrict__ partial, double* __restrict__ out,
+              unsigned int* __restrict__ counter) {
   __shared__ bool last;
   const int G = gridDim.x;
   const int chunk = (L + G - 1) / G;
   const int i0 = blockIdx.x * chunk, i1 = min(L, i0 + chunk);
-  for (int k = 0; k < nv; k++) {
-    const double* v = V + (size_t)k * ldv;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  if (nu > 0) {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      double s = w[i];
+      for (int k = 0; k < nu; k++) s -= h[k] * V[(size_t)k * ldv + i];
+      w[i] = s;
+    }
+    __syncthreads();
+  }
+  for (int k = warp; k < nd; k += nwarps) {
+    const double* v = Vd + (size_t)k * ldvd;
     double s = 0.0;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += v[i] * w[i];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) partial[(size_t)k * G + blockIdx.x] = s;
+    for (int i = i0 + lane; i < i1; i += 32) s += v[i] * w[i];
+    s = warp_sum(s);
+    if (lane == 0) partial[(size_t)k * G + blockIdx.x] = s;
   }
   __threadfence();
   __syncthreads();
@@ -37,22 +51,13 @@ k_dots(int L, int nv, const double* __restrict__ V, size_t ldv, const double* __
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+  for (int k = warp; k < nd; k += nwarps) {
     double s = 0.0;
-    for (int b = 0; b < G; b++) s += ((volatile double*)partial)[(size_t)k * G + b];
-    out[k] = s;
+    for (int b = lane; b < G; b += 32) s += ((volatile double*)partial)[(size_t)k * G + b];
+    s = warp_sum(s);
+    if (lane == 0) out[k] = s;
   }
   if (threadIdx.x == 0) *counter = 0u;
-}
-
-// w -= sum_k h[k] V[k]
-__global__ void k_update(int L, int nv, const double* __restrict__ V, size_t ldv, const double* __restrict__ h,
-                         double* __restrict__ w) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L) return;
-  double s = w[i];
-  for (int k = 0; k < nv; k++) s -= h[k] * V[(size_t)k * ldv + i];
-  w[i] = s;
 }
 
 // y = a * x (+ y if accumulate)
@@ -230,11 +235,16 @@ __global__ void k_rpy(int M, double a, double mu, const double* __restrict__ c, 
 // ------------------------------------------------------------------ host side
 static int blocks_for(int L, int t) { return (L + t - 1) / t; }
 
-static int dots(lcp_ctx* ctx, int L, int nv, const double* V, size_t ldv, const double* w, double* out) {
-  ++ctx->nlaunch, k_dots<<<ctx->dot_blocks, DOT_THREADS, 0, ctx->stream>>>(L, nv, V, ldv, w, ctx->dotp, out,
-                                                            (unsigned int*)(ctx->dscal + 60));
+static int update_dots(lcp_ctx* ctx, int L, int nu, const double* V, size_t ldv, const double* h, double* w,
+                       int nd, const double* Vd, size_t ldvd, double* out) {
+  ++ctx->nlaunch, k_update_dots<<<ctx->dot_blocks, DOT_THREADS, 0, ctx->stream>>>(
+                      L, nu, V, ldv, h, w, nd, Vd, ldvd, ctx->dotp, out, (unsigned int*)(ctx->dscal + 60));
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
+}
+
+static int dots(lcp_ctx* ctx, int L, int nv, const double* V, size_t ldv, const double* w, double* out) {
+  return update_dots(ctx, L, 0, nullptr, 0, nullptr, const_cast<double*>(w), nv, V, ldv, out);
 }
 
 static int read_status(lcp_ctx* ctx, double* vals, int count) {
@@ -297,11 +307,10 @@ static int gmres(lcp_ctx* ctx, const double* rhs, double* phi, int zero_init, do
       }
       LCP_TRY(stokes_apply(ctx, vj, vn, prec));
       total++;
+      // classical Gram-Schmidt twice; each update is fused with the next dots
       LCP_TRY(dots(ctx, L, j + 1, ctx->V, ldv, vn, h1));
-      ++ctx->nlaunch, k_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j + 1, ctx->V, ldv, h1, vn);
-      LCP_TRY(dots(ctx, L, j + 1, ctx->V, ldv, vn, h2));
-      ++ctx->nlaunch, k_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, j + 1, ctx->V, ldv, h2, vn);
-      LCP_TRY(dots(ctx, L, 1, vn, ldv, vn, hn));
+      LCP_TRY(update_dots(ctx, L, j + 1, ctx->V, ldv, h1, vn, j + 1, ctx->V, ldv, h2));
+      LCP_TRY(update_dots(ctx, L, j + 1, ctx->V, ldv, h2, vn, 1, vn, ldv, hn));
       ++ctx->nlaunch, k_gmres_column<<<1, 1, 0, ctx->stream>>>(base, m, j, ctx->dscal);
       ++ctx->nlaunch, k_scale<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, vn, hn, vn, 0, 0);   // v_{j+1} = w / H[j+1][j]
       LCP_TRY(read_status(ctx, st, 2));

@@ -5,12 +5,15 @@
 // sequences the launches.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "common.cuh"
 
 int stokes_configure(lcp_ctx* ctx);
 int stokes_max_splits(const lcp_ctx* ctx);
+int stokes_sym_configure(lcp_ctx* ctx);
+size_t stokes_sym_bytes(int M, int ns);
 int stokes_velocity(lcp_ctx* ctx, const double* phi, double* UO);
 int pqn_configure(lcp_ctx* ctx, int rmax);
 int stokes_autotune(lcp_ctx* ctx);
@@ -88,7 +91,8 @@ static int alloc_static(lcp_ctx* ctx) {
   LCP_TRY(geometry_build(ctx));
   ctx->m = ctx->cfg.gmres_restart;
   LCP_TRY(stokes_configure(ctx));
-  ctx->splits = stokes_max_splits(ctx);
+  LCP_TRY(stokes_sym_configure(ctx));
+  ctx->splits = std::max(stokes_max_splits(ctx), ctx->sym_slots);
   ctx->dot_blocks = 2 * 152;
   ctx->V = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)L * (ctx->m + 1));
   if (ctx->cfg.precondition) {
@@ -299,11 +303,14 @@ extern "C" int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n
   size_t b = 0;
   b += sizeof(double) * L * (m + 1) + (cfg->precondition ? sizeof(double) * L * m : 0);   // Krylov bases
   b += sizeof(double) * L * 5 + sizeof(float) * L * 3;                                      // node vectors
-  b += sizeof(double) * L * 6;                                                               // partial slots
+  const size_t ntb = (N + 511) / 512, units = ntb * M / 2 + 1;                               // symmetric pair sum
+  const size_t slots = std::min(units, 2 + M / std::max<size_t>(1, units / 304));
+  b += sizeof(double) * L * std::max<size_t>(6, slots) + stokes_sym_bytes(n_bodies, (int)ns); // partial slots
   b += sizeof(double) * ((m + 1) * m + 6 * m + 16 + (m + 2) * 304);                          // Hessenberg, dots
   b += sizeof(double) * (8 * ns + 36) + sizeof(float) * 6 * ns + sizeof(double) * 30 * M + sizeof(float) * 8 * M;
   b += (sizeof(int) * 2 + sizeof(double) * 4) * pairs + sizeof(int) * M * (M + 2);           // contact buffers
-  if (cfg->precondition) b += sizeof(double) * 9 * ns * ns * 3 + sizeof(float) * 9 * ns * ns;  // preconditioner
+  if (cfg->precondition)                                                                     // preconditioner
+    b += sizeof(double) * 9 * ns * ns * 3 + sizeof(float) * 9 * ns * ns + sizeof(float) * 4 * L;
   b += sizeof(double) * n * (6 + 2 * K) + sizeof(int) * (2 * n + 1);                         // arena
   b += 2 * sizeof(double) * (n * (8 + 6 * R) + 3 * R * R + 64);                              // PQN states
   *bytes = b + (b >> 4);                                                                     // 1/16 slack

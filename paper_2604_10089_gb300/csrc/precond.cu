@@ -133,26 +133,30 @@ __global__ void k_gj_extract(int n, const double* __restrict__ Aug, float* __res
 
 // z_b = Minv v_b for every body b: C (n x M) = Minv (n x n) B (n x M), B and C
 // column-major with columns = bodies (the node-vector layout).  FP32 tiles,
-// FP64 in and out.
-constexpr int PT_R = 64, PT_C = 16, PT_K = 32;
-__global__ void __launch_bounds__(256) k_precond(int n, int M, const float* __restrict__ Minv,
-                                                 const double* __restrict__ v, double* __restrict__ z) {
+// FP64 in.  The k range is split PT_KS ways so that the small GEMM fills the
+// SMs with several CTAs each (one CTA per SM would wait on every tile load);
+// split s writes its FP32 partial product to part[s][M][n] and k_precond_sum
+// adds the splits in a fixed order.
+constexpr int PT_R = 64, PT_C = 16, PT_K = 32, PT_KS = 4;
+__global__ void __launch_bounds__(256) k_precond(int n, int M, int kc, const float* __restrict__ Minv,
+                                                 const double* __restrict__ v, float* __restrict__ part) {
   __shared__ float As[PT_K][PT_R + 1];
   __shared__ float Bs[PT_C][PT_K + 1];
   const int r0 = blockIdx.x * PT_R, c0 = blockIdx.y * PT_C;
+  const int ka = blockIdx.z * kc, kb = min(n, ka + kc);
   const int tr = threadIdx.x % PT_R;        // row within the tile
   const int tc = threadIdx.x / PT_R;        // 0..3: handles columns tc, tc+4, tc+8, tc+12
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int k0 = 0; k0 < n; k0 += PT_K) {
+  for (int k0 = ka; k0 < kb; k0 += PT_K) {
     for (int t = threadIdx.x; t < PT_R * PT_K; t += blockDim.x) {
       const int rr = t / PT_K, kk = t % PT_K;
       const int gr = r0 + rr, gk = k0 + kk;
-      As[kk][rr] = (gr < n && gk < n) ? Minv[(size_t)gr * n + gk] : 0.f;
+      As[kk][rr] = (gr < n && gk < kb) ? Minv[(size_t)gr * n + gk] : 0.f;
     }
     for (int t = threadIdx.x; t < PT_C * PT_K; t += blockDim.x) {
       const int cc = t / PT_K, kk = t % PT_K;
       const int gc = c0 + cc, gk = k0 + kk;
-      Bs[cc][kk] = (gc < M && gk < n) ? (float)v[(size_t)gc * n + gk] : 0.f;
+      Bs[cc][kk] = (gc < M && gk < kb) ? (float)v[(size_t)gc * n + gk] : 0.f;
     }
     __syncthreads();
 #pragma unroll 8
@@ -167,8 +171,17 @@ __global__ void __launch_bounds__(256) k_precond(int n, int M, const float* __re
   if (gr < n)
     for (int u = 0; u < 4; u++) {
       const int gc = c0 + tc + 4 * u;
-      if (gc < M) z[(size_t)gc * n + gr] = (double)acc[u];
+      if (gc < M) part[((size_t)blockIdx.z * M + gc) * n + gr] = acc[u];
     }
+}
+
+__global__ void k_precond_sum(int L, const float* __restrict__ part, double* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < PT_KS; k++) s += (double)part[(size_t)k * L + i];
+  z[i] = s;
 }
 
 int precond_build(lcp_ctx* ctx) {
@@ -176,7 +189,8 @@ int precond_build(lcp_ctx* ctx) {
   double* aug = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)n * 2 * n);
   double* colk = (double*)ctx_alloc(ctx, sizeof(double) * n);
   ctx->pinv = (float*)ctx_alloc(ctx, sizeof(float) * (size_t)n * n);
-  if (!aug || !colk || !ctx->pinv) return LCP_ERR_OOM;
+  ctx->ppart = (float*)ctx_alloc(ctx, sizeof(float) * PT_KS * (size_t)n * ctx->M);
+  if (!aug || !colk || !ctx->pinv || !ctx->ppart) return LCP_ERR_OOM;
   // assemble K_iso + P_iso (n x n), then copy it into the left half of [A | I]
   double* tmp = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)n * n);
   if (!tmp) return LCP_ERR_OOM;
@@ -199,8 +213,11 @@ int precond_build(lcp_ctx* ctx) {
 
 int precond_apply(lcp_ctx* ctx, const double* v, double* z) {
   const int n = 3 * ctx->ns;
-  dim3 grid((n + PT_R - 1) / PT_R, (ctx->M + PT_C - 1) / PT_C);
-  ++ctx->nlaunch, k_precond<<<grid, 256, 0, ctx->stream>>>(n, ctx->M, ctx->pinv, v, z);
+  const int kc = ((n + PT_K - 1) / PT_K + PT_KS - 1) / PT_KS * PT_K;
+  dim3 grid((n + PT_R - 1) / PT_R, (ctx->M + PT_C - 1) / PT_C, PT_KS);
+  ++ctx->nlaunch, k_precond<<<grid, 256, 0, ctx->stream>>>(n, ctx->M, kc, ctx->pinv, v, ctx->ppart);
+  const int L = n * ctx->M;
+  ++ctx->nlaunch, k_precond_sum<<<(L + 255) / 256, 256, 0, ctx->stream>>>(L, ctx->ppart, z);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }

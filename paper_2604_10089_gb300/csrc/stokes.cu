@@ -248,28 +248,6 @@ constexpr int kNumPair32Variants = sizeof(kPair32Variants) / sizeof(kPair32Varia
 struct dfl {
   float hi, lo;
 };
-__device__ __forceinline__ dfl df_fast2sum(float a, float b) {   // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  const float e = __fadd_rn(b, -__fadd_rn(s, -a));
-  return {s, e};
-}
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-  const float s = __fadd_rn(a.hi, b.hi);
-  const float bb = __fadd_rn(s, -a.hi);
-  const float e = __fadd_rn(__fadd_rn(a.hi, -__fadd_rn(s, -bb)), __fadd_rn(b.hi, -bb));
-  return df_fast2sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return df_fast2sum(p, e);
-}
-__device__ __forceinline__ dfl df_dot3(dfl ax, dfl ay, dfl az, dfl bx, dfl by, dfl bz) {
-  return df_add(df_add(df_mul(ax, bx), df_mul(ay, by)), df_mul(az, bz));
-}
 __device__ __forceinline__ dfl df_split(double v) {
   const float h = __double2float_rn(v);
   return {h, __double2float_rn(v - (double)h)};
@@ -284,28 +262,88 @@ __global__ void k_split_df(int L, const double* __restrict__ x, float* __restric
   y[6 * node + 3 + d] = v.lo;
 }
 
-// Same work decomposition as k_pair32; one target per thread.
-__global__ void __launch_bounds__(PAIR_THREADS)
+// Packed double-float arithmetic on two lanes at once (FP32x2 instructions):
+// every D2 holds two independent double-float numbers, here the terms of two
+// source nodes q, q+1 for one target.  Intermediate results stay
+// unnormalised (lo may exceed half an ulp of hi by a few ulps; the dropped
+// lo*lo products are then ~2^-44 of the operands' product) and are
+// renormalised with Fast2Sum only where cancellation is expected (the
+// separation r and the dot products r.n, r.(phi_q - phi_p)), after the
+// Newton step of |r|^-1, and in the running sums.
+struct D2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b, rounded once
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// TwoSum (Knuth): s + e = a + b exactly.
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+__device__ __forceinline__ D2 fast2sum2(float2 a, float2 b) {   // |a| >= |b|
+  const float2 s = add2(a, b);
+  return {s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ D2 dadd_u(D2 a, D2 b) {
+  float2 s, e;
+  two_sum2(a.hi, b.hi, s, e);
+  return {s, add2(e, add2(a.lo, b.lo))};
+}
+__device__ __forceinline__ D2 dadd_n(D2 a, D2 b) {
+  const D2 t = dadd_u(a, b);
+  return fast2sum2(t.hi, t.lo);
+}
+// TwoProd by FMA plus the cross terms.
+__device__ __forceinline__ D2 dmul_u(D2 a, D2 b) {
+  const float2 p = mul2(a.hi, b.hi);
+  float2 e = fma2(a.hi, b.hi, neg2(p));
+  e = fma2(a.hi, b.lo, e);
+  e = fma2(a.lo, b.hi, e);
+  return {p, e};
+}
+__device__ __forceinline__ D2 dsq_u(D2 a) {
+  const float2 p = mul2(a.hi, a.hi);
+  float2 e = fma2(a.hi, a.hi, neg2(p));
+  e = fma2(a.hi, add2(a.lo, a.lo), e);
+  return {p, e};
+}
+
+// Double-float stresslet sum: same (target block, source body) decomposition
+// as the FP32 kernel, one target per thread, source nodes two at a time in
+// packed double-float arithmetic.  Shared memory holds the template as 12
+// SoA arrays (-xi hi/lo, w n hi/lo per component) and the staged source
+// densities as 6 SoA arrays per body (hi xyz, lo xyz).  ns_pad is ns rounded
+// up to 4; padded sources have zero weight and density, far away.
+__global__ void __launch_bounds__(PAIR_THREADS, 2)
 k_pair_df(int N, int ns, int ns_pad, Units un, const double* __restrict__ tmpl64,
           const double* __restrict__ centers, const float* __restrict__ phidf, double* __restrict__ partial) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
-  // 12 template arrays: -xi (hi, lo) x3, wn (hi, lo) x3; then the staged densities
-  float* s_t = sm;                       // [12][ns_pad]
-  float* s_f = s_t + 12 * ns_pad;        // [6][PAIR_CHUNK][ns_pad]: x hi, x lo, y hi, y lo, z hi, z lo
+  float* s_t = sm;                       // [12][ns_pad]: -xi hi x,y,z; -xi lo x,y,z; wn hi x,y,z; wn lo x,y,z
+  float* s_f = s_t + 12 * ns_pad;        // [6][PAIR_CHUNK][ns_pad]: phi hi x,y,z; phi lo x,y,z
   for (int q = threadIdx.x; q < ns_pad; q += blockDim.x) {
     const bool real = q < ns;
     for (int d = 0; d < 3; d++) {
       const dfl x = real ? df_split(-tmpl64[8 * q + d]) : dfl{d == 0 ? -1.0e3f : 0.f, 0.f};
       const dfl w = real ? df_split(tmpl64[8 * q + 3 + d]) : dfl{0.f, 0.f};
-      s_t[(2 * d) * ns_pad + q] = x.hi;
-      s_t[(2 * d + 1) * ns_pad + q] = x.lo;
-      s_t[(6 + 2 * d) * ns_pad + q] = w.hi;
-      s_t[(6 + 2 * d + 1) * ns_pad + q] = w.lo;
+      s_t[d * ns_pad + q] = x.hi;
+      s_t[(3 + d) * ns_pad + q] = x.lo;
+      s_t[(6 + d) * ns_pad + q] = w.hi;
+      s_t[(9 + d) * ns_pad + q] = w.lo;
     }
   }
+  // padded source slots of every staged body stay zero for the whole kernel
+  for (int t = threadIdx.x; t < 6 * PAIR_CHUNK * ns_pad; t += blockDim.x) s_f[t] = 0.f;
   const int M = un.M;
   const int c = blockIdx.x;
+  const int fs = PAIR_CHUNK * ns_pad;
   int u = un.start(c);
   const int uend = un.start(c + 1);
   while (u < uend) {
@@ -319,8 +357,8 @@ k_pair_df(int N, int ns, int ns_pad, Units un, const double* __restrict__ tmpl64
     const double xpx = tmpl64[8 * qi], xpy = tmpl64[8 * qi + 1], xpz = tmpl64[8 * qi + 2];
     const double cix = centers[3 * bi], ciy = centers[3 * bi + 1], ciz = centers[3 * bi + 2];
     const float* fp = phidf + 6 * (size_t)pc;
-    const dfl nfx = {-fp[0], -fp[3]}, nfy = {-fp[1], -fp[4]}, nfz = {-fp[2], -fp[5]};
-    dfl ax = {0.f, 0.f}, ay = ax, az = ax;
+    const D2 nfx = {f2(-fp[0]), f2(-fp[3])}, nfy = {f2(-fp[1]), f2(-fp[4])}, nfz = {f2(-fp[2]), f2(-fp[5])};
+    D2 ax = {f2(0.f), f2(0.f)}, ay = ax, az = ax;
     for (int jc = jb0; jc < jb1; jc += PAIR_CHUNK) {
       const int nb = min(PAIR_CHUNK, jb1 - jc);
       __syncthreads();
@@ -328,55 +366,54 @@ k_pair_df(int N, int ns, int ns_pad, Units un, const double* __restrict__ tmpl64
       for (int t = threadIdx.x; t < 6 * nb * ns; t += blockDim.x) {
         const int node = t / 6, k = t - 6 * node;         // k: 0..2 hi xyz, 3..5 lo xyz
         const int b = node / ns, q = node - b * ns;
-        const int comp = k % 3, part = k / 3;
-        s_f[((2 * comp + part) * PAIR_CHUNK + b) * ns_pad + q] = src[t];
-      }
-      for (int t = threadIdx.x; t < nb * (ns_pad - ns); t += blockDim.x) {
-        const int b = t / (ns_pad - ns), q = ns + t % (ns_pad - ns);
-        for (int k = 0; k < 6; k++) s_f[(k * PAIR_CHUNK + b) * ns_pad + q] = 0.f;
+        s_f[(k * PAIR_CHUNK + b) * ns_pad + q] = src[t];
       }
       __syncthreads();
       for (int b = 0; b < nb; b++) {
         const int j = jc + b;
-        const dfl ex = df_split((cix - centers[3 * j]) + xpx);
-        const dfl ey = df_split((ciy - centers[3 * j + 1]) + xpy);
-        const dfl ez = df_split((ciz - centers[3 * j + 2]) + xpz);
+        const dfl ex1 = df_split((cix - centers[3 * j]) + xpx);
+        const dfl ey1 = df_split((ciy - centers[3 * j + 1]) + xpy);
+        const dfl ez1 = df_split((ciz - centers[3 * j + 2]) + xpz);
+        const D2 ex = {f2(ex1.hi), f2(ex1.lo)}, ey = {f2(ey1.hi), f2(ey1.lo)}, ez = {f2(ez1.hi), f2(ez1.lo)};
         const float* f = s_f + b * ns_pad;
-        const int fs = PAIR_CHUNK * ns_pad;
 #pragma unroll 1
-        for (int q = 0; q < ns_pad; q++) {
-          const dfl rx = df_add(ex, {s_t[q], s_t[ns_pad + q]});
-          const dfl ry = df_add(ey, {s_t[2 * ns_pad + q], s_t[3 * ns_pad + q]});
-          const dfl rz = df_add(ez, {s_t[4 * ns_pad + q], s_t[5 * ns_pad + q]});
-          const dfl wx = {s_t[6 * ns_pad + q], s_t[7 * ns_pad + q]};
-          const dfl wy = {s_t[8 * ns_pad + q], s_t[9 * ns_pad + q]};
-          const dfl wz = {s_t[10 * ns_pad + q], s_t[11 * ns_pad + q]};
-          dfl r2 = df_dot3(rx, ry, rz, rx, ry, rz);
-          r2 = df_add(r2, {EPS32, 0.f});
-          // ir = 1 / sqrt(r2): y0 from MUFU, one Newton step y0 + y0 (1 - r2 y0^2) / 2
-          const float y0 = rsqrt_approx(r2.hi);
-          const dfl y02 = df_mul({y0, 0.f}, {y0, 0.f});
-          const dfl t = df_mul(r2, y02);
-          const float h = __fadd_rn(__fadd_rn(1.0f, -t.hi), -t.lo);
-          const dfl ir = df_fast2sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), h));
-          const dfl i2 = df_mul(ir, ir);
-          const dfl rn = df_dot3(rx, ry, rz, wx, wy, wz);
-          const dfl dx = df_add({f[q], f[fs + q]}, nfx);
-          const dfl dy = df_add({f[2 * fs + q], f[3 * fs + q]}, nfy);
-          const dfl dz = df_add({f[4 * fs + q], f[5 * fs + q]}, nfz);
-          const dfl rd = df_dot3(rx, ry, rz, dx, dy, dz);
-          const dfl sc = df_mul(df_mul(df_mul(rn, i2), df_mul(rd, i2)), ir);
-          ax = df_add(ax, df_mul(sc, rx));
-          ay = df_add(ay, df_mul(sc, ry));
-          az = df_add(az, df_mul(sc, rz));
+        for (int q = 0; q < ns_pad; q += 2) {
+#define LD2(ptr) (*reinterpret_cast<const float2*>((ptr) + q))
+          const D2 rx = dadd_n(ex, {LD2(s_t), LD2(s_t + 3 * ns_pad)});
+          const D2 ry = dadd_n(ey, {LD2(s_t + ns_pad), LD2(s_t + 4 * ns_pad)});
+          const D2 rz = dadd_n(ez, {LD2(s_t + 2 * ns_pad), LD2(s_t + 5 * ns_pad)});
+          D2 r2 = dadd_u(dadd_u(dsq_u(rx), dsq_u(ry)), dsq_u(rz));
+          r2.hi = add2(r2.hi, f2(EPS32));
+          // |r|^-1: MUFU seed y0, one Newton step y0 + (y0 / 2)(1 - r2 y0^2) in double-float
+          const float2 y0 = make_float2(rsqrt_approx(r2.hi.x), rsqrt_approx(r2.hi.y));
+          const float2 yy = mul2(y0, y0);
+          const D2 t = dmul_u(r2, {yy, fma2(y0, y0, neg2(yy))});
+          const float2 h = sub2(sub2(f2(1.f), t.hi), t.lo);
+          // renormalised: an unnormalised lo of ~2^-22 y0 would drop lo^2 ~ 2^-44 in |r|^-2
+          const D2 ir = fast2sum2(y0, mul2(mul2(f2(0.5f), y0), h));
+          const D2 i2 = dsq_u(ir);
+          const D2 rn = dadd_n(dadd_u(dmul_u(rx, {LD2(s_t + 6 * ns_pad), LD2(s_t + 9 * ns_pad)}),
+                                      dmul_u(ry, {LD2(s_t + 7 * ns_pad), LD2(s_t + 10 * ns_pad)})),
+                               dmul_u(rz, {LD2(s_t + 8 * ns_pad), LD2(s_t + 11 * ns_pad)}));
+          const D2 dx = dadd_u({LD2(f), LD2(f + 3 * fs)}, nfx);
+          const D2 dy = dadd_u({LD2(f + fs), LD2(f + 4 * fs)}, nfy);
+          const D2 dz = dadd_u({LD2(f + 2 * fs), LD2(f + 5 * fs)}, nfz);
+#undef LD2
+          const D2 rd = dadd_n(dadd_u(dmul_u(rx, dx), dmul_u(ry, dy)), dmul_u(rz, dz));
+          const D2 sc = dmul_u(dmul_u(dmul_u(rn, i2), dmul_u(rd, i2)), ir);
+          // the accumulators stay normalised: an unnormalised lo would collect
+          // rounding errors over ~N/2 additions per lane
+          ax = dadd_n(ax, dmul_u(sc, rx));
+          ay = dadd_n(ay, dmul_u(sc, ry));
+          az = dadd_n(az, dmul_u(sc, rz));
         }
       }
     }
     if (p < N) {
       double* o = partial + ((size_t)slot * N + p) * 3;
-      o[0] = (double)ax.hi + (double)ax.lo;
-      o[1] = (double)ay.hi + (double)ay.lo;
-      o[2] = (double)az.hi + (double)az.lo;
+      o[0] = ((double)ax.hi.x + (double)ax.hi.y) + ((double)ax.lo.x + (double)ax.lo.y);
+      o[1] = ((double)ay.hi.x + (double)ay.hi.y) + ((double)ay.lo.x + (double)ay.lo.y);
+      o[2] = ((double)az.hi.x + (double)az.hi.y) + ((double)az.lo.x + (double)az.lo.y);
     }
   }
 }
@@ -561,6 +598,7 @@ __global__ void k_neg(int L, const double* __restrict__ x, double* __restrict__ 
 
 // ------------------------------------------------------------------ host side
 size_t stokes_pair_smem(int ns, int precision);
+int stokes_sym_apply(lcp_ctx* ctx, double* out);
 // One full wave of CTAs for a pair kernel: SMs x resident CTAs per SM, capped
 // by the number of (target block, source body) units.
 static int pair_targets(int precision, int v32) {
@@ -611,6 +649,11 @@ int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
   }
   Units un{ntb * M, grid, M};
   LCP_TRY(stokes_coefs(ctx, phi, ctx->coef));
+  if (precision == LCP_MIXED && ctx->sym) {
+    ++ctx->nlaunch, k_to_f32<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(3 * N, phi, ctx->phi32);
+    ctx->c_fp32++;
+    return stokes_sym_apply(ctx, out);
+  }
   LCP_CUDA(cudaMemsetAsync(ctx->partial, 0, sizeof(double) * 3 * (size_t)N * slots, ctx->stream));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ctx->prof) {
@@ -713,9 +756,9 @@ int stokes_configure(lcp_ctx* ctx) {
 
 // ---------------------------------------------------------------- autotuner
 // Chooses the FP32 pair-kernel variant (targets per CTA = target-block size,
-// source bodies per shared-memory tile) for a size class by timing every
-// variant on this context's geometry; the choice is cached per (nodes per
-// sphere, bodies) class for the process.
+// source bodies per shared-memory tile, or the symmetric kernel) for a size
+// class by timing every candidate on this context's geometry; the choice is
+// cached per (nodes per sphere, bodies) class for the process.
 #include <map>
 #include <mutex>
 
@@ -734,7 +777,8 @@ int stokes_autotune(lcp_ctx* ctx) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      ctx->v32 = it->second;
+      ctx->sym = it->second == kNumPair32Variants;
+      ctx->v32 = ctx->sym ? 0 : it->second;
       return LCP_OK;
     }
   }
@@ -752,10 +796,16 @@ int stokes_autotune(lcp_ctx* ctx) {
   int best_v = 0;
   const bool prof = ctx->prof;
   ctx->prof = false;
-  for (int v = 0; v < kNumPair32Variants; v++) {
-    if (ctx->occ32v[v] <= 0) continue;
-    ctx->v32 = v;
-    if (pair_slots_v(ctx, pair_grid_v(ctx, LCP_MIXED, v), LCP_MIXED, v) > ctx->splits) continue;
+  // candidates: the plain variants, then (v = kNumPair32Variants) the symmetric kernel
+  for (int v = 0; v <= kNumPair32Variants; v++) {
+    ctx->sym = v == kNumPair32Variants;
+    if (ctx->sym) {
+      if (ctx->occsym <= 0 || ctx->sym_slots > ctx->splits) continue;
+    } else {
+      if (ctx->occ32v[v] <= 0) continue;
+      ctx->v32 = v;
+      if (pair_slots_v(ctx, pair_grid_v(ctx, LCP_MIXED, v), LCP_MIXED, v) > ctx->splits) continue;
+    }
     LCP_TRY(stokes_apply(ctx, phi, out, LCP_MIXED));   // warm-up
     LCP_CUDA(cudaEventRecord(a, ctx->stream));
     for (int r = 0; r < 3; r++) LCP_TRY(stokes_apply(ctx, phi, out, LCP_MIXED));
@@ -769,10 +819,11 @@ int stokes_autotune(lcp_ctx* ctx) {
   ctx->c_fp32 = 0;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  ctx->v32 = best_v;
+  ctx->sym = best_v == kNumPair32Variants;
+  ctx->v32 = ctx->sym ? 0 : best_v;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache[key] = best_v;
   return LCP_OK;
 }
 
-const char* stokes_variant_name(const lcp_ctx* ctx) { return kPair32Variants[ctx->v32].name; }
+const char* stokes_variant_name(const lcp_ctx* ctx) { return ctx->sym ? "sym" : kPair32Variants[ctx->v32].name; }
