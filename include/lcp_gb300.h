@@ -156,10 +156,18 @@ LCP_API int lcp_footprint(const lcp_ctx* ctx, size_t* bytes);
  * n_contacts contacts with this config, computable before creating it. */
 LCP_API int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n_contacts, size_t* bytes);
 
-/* Name of the FP32 pair-kernel variant in use ("t2c8" = 2 targets per thread,
- * 8 source bodies per shared-memory tile; chosen by the autotuner when
- * cfg.autotune is set). */
+/* Name of the FP32 pair-kernel variant in use: "sym*" = the symmetric pair sum
+ * (one evaluation per unordered node pair; the default is "sym_a4"), "t2c8" = the
+ * plain sum with 2 targets per thread and 8 source bodies per shared-memory
+ * tile, and so on; chosen by the autotuner when cfg.autotune is set. */
 LCP_API const char* lcp_kernel_variant(const lcp_ctx* ctx);
+
+/* Forces the FP32 pair-kernel variant by name (one of the names
+ * lcp_kernel_variant can return).  The operator is the same discrete K + P;
+ * variants differ in summation order (FP32 rounding) and speed.  Errors:
+ * LCP_ERR_INVALID_ARG for an unknown name or a variant that does not fit this
+ * context's size. */
+LCP_API int lcp_select_kernel_variant(lcp_ctx* ctx, const char* name);
 
 /* Batched solves: solves count independent contexts with `workers` host
  * threads; contexts created with own_stream run concurrently on the GPU.

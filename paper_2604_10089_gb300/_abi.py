@@ -88,6 +88,7 @@ PROTOTYPES = {
     "lcp_footprint": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "lcp_footprint_estimate": (_I, [ctypes.POINTER(lcp_config), _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "lcp_kernel_variant": (ctypes.c_char_p, [_P]),
+    "lcp_select_kernel_variant": (_I, [_P, ctypes.c_char_p]),
     "lcp_batch_solve": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.c_double, ctypes.POINTER(_P),
                              ctypes.POINTER(lcp_stats), ctypes.POINTER(_I), _I]),
     "lcp_server_create": (_I, [_I, ctypes.c_size_t, ctypes.POINTER(_P)]),

@@ -123,7 +123,9 @@ struct lcp_ctx {
   int occ32v[8] = {0};        // occupancy of each FP32 kernel variant
   int v32 = 0;                // FP32 kernel variant in use (autotuned per size class)
   bool sym = true;            // FP32 sums by the symmetric kernel (stokes_sym.cu)
-  int occsym = 0, sym_ntb = 0, sym_units = 0, sym_grid = 0, sym_slots = 0;
+  int sym_v = 0;              // symmetric kernel variant in use
+  int sym_ntb = 0, sym_units = 0, sym_slots = 0;   // sym_slots: largest over the variants
+  int symv_occ[8] = {0}, symv_grid[8] = {0}, symv_slots[8] = {0};
   int* sym_off = nullptr;          // [ntb + 1] first unit of each target block
   long long* sym_roff = nullptr;   // [ntb + 1] first float of each block's reverse rows
   float* sym_rev = nullptr;        // reverse partial sums, one row per unit

@@ -14,6 +14,7 @@ int stokes_configure(lcp_ctx* ctx);
 int stokes_max_splits(const lcp_ctx* ctx);
 int stokes_sym_configure(lcp_ctx* ctx);
 size_t stokes_sym_bytes(int M, int ns);
+int stokes_select_variant(lcp_ctx* ctx, const char* name);
 int stokes_velocity(lcp_ctx* ctx, const double* phi, double* UO);
 int pqn_configure(lcp_ctx* ctx, int rmax);
 int stokes_autotune(lcp_ctx* ctx);
@@ -324,6 +325,11 @@ extern "C" int lcp_footprint(const lcp_ctx* ctx, size_t* bytes) {
 }
 
 extern "C" const char* lcp_kernel_variant(const lcp_ctx* ctx) { return ctx ? stokes_variant_name(ctx) : ""; }
+
+extern "C" int lcp_select_kernel_variant(lcp_ctx* ctx, const char* name) {
+  if (!ctx || !name) return LCP_ERR_INVALID_ARG;
+  return stokes_select_variant(ctx, name);
+}
 
 extern "C" int lcp_launch_count(const lcp_ctx* ctx, unsigned long long* count) {
   if (!ctx || !count) return LCP_ERR_INVALID_ARG;

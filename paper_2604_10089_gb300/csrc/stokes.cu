@@ -13,6 +13,7 @@
 // r = ((c_i - c_j) + xi_p) - xi_q with c_i - c_j formed from hi/lo parts,
 // which keeps FP32 differences accurate for nodes of touching spheres.
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -771,14 +772,33 @@ static int size_class(int M) {   // bodies rounded up to a power of two
   return c;
 }
 
+int stokes_sym_variant_count();
+const char* stokes_sym_variant_name(int v);
+bool stokes_sym_variant_usable(const lcp_ctx* ctx, int v);
+
+// Candidate index: plain variants 0 .. kNumPair32Variants-1, then the
+// symmetric variants.
+static int candidate_count() { return kNumPair32Variants + stokes_sym_variant_count(); }
+static void set_candidate(lcp_ctx* ctx, int v) {
+  ctx->sym = v >= kNumPair32Variants;
+  ctx->v32 = ctx->sym ? 0 : v;
+  ctx->sym_v = ctx->sym ? v - kNumPair32Variants : 0;
+}
+static bool candidate_usable(lcp_ctx* ctx, int v) {
+  if (v >= kNumPair32Variants) return stokes_sym_variant_usable(ctx, v - kNumPair32Variants);
+  return ctx->occ32v[v] > 0 && pair_slots_v(ctx, pair_grid_v(ctx, LCP_MIXED, v), LCP_MIXED, v) <= ctx->splits;
+}
+static const char* candidate_name(int v) {
+  return v >= kNumPair32Variants ? stokes_sym_variant_name(v - kNumPair32Variants) : kPair32Variants[v].name;
+}
+
 int stokes_autotune(lcp_ctx* ctx) {
   const std::pair<int, int> key(ctx->ns, size_class(ctx->M));
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      ctx->sym = it->second == kNumPair32Variants;
-      ctx->v32 = ctx->sym ? 0 : it->second;
+      set_candidate(ctx, it->second);
       return LCP_OK;
     }
   }
@@ -796,16 +816,9 @@ int stokes_autotune(lcp_ctx* ctx) {
   int best_v = 0;
   const bool prof = ctx->prof;
   ctx->prof = false;
-  // candidates: the plain variants, then (v = kNumPair32Variants) the symmetric kernel
-  for (int v = 0; v <= kNumPair32Variants; v++) {
-    ctx->sym = v == kNumPair32Variants;
-    if (ctx->sym) {
-      if (ctx->occsym <= 0 || ctx->sym_slots > ctx->splits) continue;
-    } else {
-      if (ctx->occ32v[v] <= 0) continue;
-      ctx->v32 = v;
-      if (pair_slots_v(ctx, pair_grid_v(ctx, LCP_MIXED, v), LCP_MIXED, v) > ctx->splits) continue;
-    }
+  for (int v = 0; v < candidate_count(); v++) {
+    if (!candidate_usable(ctx, v)) continue;
+    set_candidate(ctx, v);
     LCP_TRY(stokes_apply(ctx, phi, out, LCP_MIXED));   // warm-up
     LCP_CUDA(cudaEventRecord(a, ctx->stream));
     for (int r = 0; r < 3; r++) LCP_TRY(stokes_apply(ctx, phi, out, LCP_MIXED));
@@ -819,11 +832,24 @@ int stokes_autotune(lcp_ctx* ctx) {
   ctx->c_fp32 = 0;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  ctx->sym = best_v == kNumPair32Variants;
-  ctx->v32 = ctx->sym ? 0 : best_v;
+  set_candidate(ctx, best_v);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache[key] = best_v;
   return LCP_OK;
 }
 
-const char* stokes_variant_name(const lcp_ctx* ctx) { return ctx->sym ? "sym" : kPair32Variants[ctx->v32].name; }
+const char* stokes_variant_name(const lcp_ctx* ctx) {
+  return candidate_name(ctx->sym ? kNumPair32Variants + ctx->sym_v : ctx->v32);
+}
+
+// Forces a variant by name (LCP_ERR_INVALID_ARG if unknown or unusable here).
+int stokes_select_variant(lcp_ctx* ctx, const char* name) {
+  for (int v = 0; v < candidate_count(); v++)
+    if (std::strcmp(candidate_name(v), name) == 0) {
+      if (!candidate_usable(ctx, v)) break;
+      set_candidate(ctx, v);
+      return LCP_OK;
+    }
+  ctx->err = std::string("kernel variant not available: ") + name;
+  return LCP_ERR_INVALID_ARG;
+}

@@ -10,38 +10,35 @@
 // operations per ordered pair.  Pairs within one body are summed one way
 // (forward only), as in the plain kernel.
 //
-// Work: target blocks of SYM_TB consecutive nodes (two per thread) times
-// source bodies j >= the block's first body; a unit (tb, j) adds the forward
-// terms of targets with body(p) <= j and the reverse terms of targets with
-// body(p) < j.  Units are dealt in equal contiguous ranges to one wave of
-// CTAs, as for the plain kernel.  Forward sums stay in registers along a row
-// and go to partial[slot][p]; the reverse sums of unit (tb, j) are reduced
-// over the CTA's 512 targets (a transposing warp reduction, then the 8 warps
-// in order) and written to a per-unit row of `rev` (FP32), which the finish
-// kernel adds in target-block order.  Everything is deterministic.
+// Work: target blocks of SYM_TB consecutive nodes times source bodies j >=
+// the block's first body; a unit (tb, j) adds the forward terms of targets
+// with body(p) <= j and the reverse terms of targets with body(p) < j.  Units
+// are dealt in equal contiguous ranges to one wave of CTAs, as for the plain
+// kernel.  Each thread holds four targets, packed two by two in FP32x2
+// registers, and takes the sources one at a time (duplicated (v, v) pairs in
+// shared memory).  Its four reverse contributions to a source are folded in
+// registers, then summed over the warp (a transposing shuffle reduction) and
+// over the CTA's warps in order, and written to a per-unit row of `rev`
+// (FP32) that the finish kernel adds in target-block order.  Forward sums are
+// FP64 per thread (shared memory) and go to partial[slot][p].  Everything is
+// deterministic.
 #include <vector>
 
 #include "common.cuh"
 
 namespace {
 
-constexpr int SYM_THREADS = 256;
-constexpr int SYM_TB = 2 * SYM_THREADS;   // targets per block
+constexpr int SYM_THREADS = 128;
+constexpr int SYM_TPT = 4;                         // targets per thread (two FP32x2 packs)
+constexpr int SYM_TB = SYM_TPT * SYM_THREADS;      // targets per block
 constexpr int SYM_WARPS = SYM_THREADS / 32;
-constexpr int SYM_CHUNK = 8;               // source bodies staged per tile
-constexpr float SYM_EPS = 1e-20f;          // r = 0 only for q = p: keeps |r|^-3 = 1e30 finite, the term 0
+constexpr int SYM_CHUNK = 2;                       // source bodies staged per tile
+constexpr float SYM_EPS = 1e-20f;   // r = 0 only for q = p: keeps |r|^-3 = 1e30 finite, the term 0
 
 __device__ __forceinline__ float rsqrt_fast(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-__device__ __forceinline__ void kahan(float& s, float& c, float v) {
-  const float y = v - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
 }
 
 struct SymUnits {
@@ -58,8 +55,8 @@ struct SymUnits {
   __device__ __forceinline__ int first_body(int tb) const { return (int)(((long long)tb * SYM_TB) / ns); }
 };
 
-// One target (broadcast in e, nf, wp) against the source pair (q, q+1) held
-// in the lanes of the float2 source values.
+// Two targets (the lanes of e, nf, wp) against one source (duplicated in the
+// lanes of n*, w*, f*).  acc += forward terms, rv += reverse terms.
 __device__ __forceinline__ void sym_pair(const float2 (&e)[3], const float2 (&nf)[3], const float2 (&wp)[3],
                                          float2 nx, float2 ny, float2 nz, float2 wx, float2 wy, float2 wz,
                                          float2 fx, float2 fy, float2 fz, float2 (&acc)[3], float2 (&rv)[3]) {
@@ -94,68 +91,77 @@ __device__ __forceinline__ void sym_pair(const float2 (&e)[3], const float2 (&nf
   rv[2] = __ffma2_rn(sr, rz, rv[2]);
 }
 
-// Sum 16 values over the 32 lanes of a warp with 16 shuffles: at each level
-// a lane keeps half of its values and sends the other half to its partner.
-// Afterwards lanes 2k and 2k+1 both hold the warp total of value k.
-__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane) {
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-  float w[8];
+// Sum NV values (NV = 8 or 16) over the 32 lanes of a warp: at each of the
+// first log2(NV) levels a lane keeps half of its values and sends the other
+// half to its partner (NV - 1 shuffles in all), then plain butterflies
+// finish.  Afterwards lane l holds the warp total of value l / (32 / NV).
+template <int NV>
+__device__ __forceinline__ float warp_transpose_sum(const float (&v)[NV], int lane) {
+  constexpr int LOG2NV = NV == 16 ? 4 : 3;
+  float a[NV];
 #pragma unroll
-  for (int i = 0; i < 8; i++) {
-    const float send = b4 ? v[i] : v[i + 8];
-    const float keep = b4 ? v[i + 8] : v[i];
-    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-  float x[4];
+  for (int i = 0; i < NV; i++) a[i] = v[i];
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
-    const float send = b3 ? w[i] : w[i + 4];
-    const float keep = b3 ? w[i + 4] : w[i];
-    x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  float y[2];
+  for (int L = 0; L < LOG2NV; L++) {
+    const int n = NV >> (L + 1), o = 16 >> L;
+    const bool hi = lane & o;
 #pragma unroll
-  for (int i = 0; i < 2; i++) {
-    const float send = b2 ? x[i] : x[i + 2];
-    const float keep = b2 ? x[i + 2] : x[i];
-    y[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    for (int i = 0; i < n; i++) {
+      const float send = hi ? a[i] : a[i + n];
+      const float keep = hi ? a[i + n] : a[i];
+      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
   }
-  const float send = b1 ? y[0] : y[1];
-  const float keep = b1 ? y[1] : y[0];
-  float z = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  z += __shfl_xor_sync(0xffffffffu, z, 1);
-  return z;
+#pragma unroll
+  for (int o = 16 >> LOG2NV; o >= 1; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+  return a[0];
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(SYM_THREADS, 2)
-k_pair32_sym(int N, int ns, int ns_pad, SymUnits su, const float* __restrict__ tmpl32, const float* __restrict__ c32,
-             const float* __restrict__ phi32, double* __restrict__ partial, float* __restrict__ rev) {
+// Kernel variants (autotuner candidates):
+//   AOS:   shared-memory layout of the sources: per-component arrays of (v, v)
+//          pairs, or one record per node read with 128-bit loads;
+//   BATCH: sources per warp reduction (2 or 4);
+//   MINB:  CTAs per SM the registers are sized for (4: 128, 3: 168 registers);
+//   PIPE:  reduce the previous batch after computing the current one, so
+//          the shuffle latency overlaps the arithmetic.
+template <bool AOS, int BATCH, int MINB, bool PIPE>
+__device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUnits su,
+                                                const float* __restrict__ tmpl32, const float* __restrict__ c32,
+                                                const float* __restrict__ phi32, double* __restrict__ partial,
+                                                float* __restrict__ rev) {
+  constexpr int NV = BATCH == 4 ? 16 : 8;
+  constexpr int LPV = 32 / NV;   // lanes holding each reduced value
   extern __shared__ float4 smem4[];
-  float* sm = reinterpret_cast<float*>(smem4);
-  float* s_nx = sm;                          // -xi per template node (padded)
-  float* s_ny = s_nx + ns_pad;
-  float* s_nz = s_ny + ns_pad;
-  float* s_wx = s_nz + ns_pad;               // wn = -(3/4pi) w n
-  float* s_wy = s_wx + ns_pad;
-  float* s_wz = s_wy + ns_pad;
-  float* s_f = s_wz + ns_pad;                // [3][SYM_CHUNK][ns_pad] staged source densities
-  float* s_rev = s_f + 3 * SYM_CHUNK * ns_pad;   // [2][SYM_WARPS][3][ns_pad] per-warp reverse sums
+  // AOS: s_t [ns_pad][3] float4 = (nx,nx,ny,ny) (nz,nz,wx,wx) (wy,wy,wz,wz);
+  //      s_f [SYM_CHUNK][ns_pad][2] float4 = (fx,fx,fy,fy) (fz,fz,0,0)
+  // SoA: s_t [6][ns_pad] float2; s_f [3][SYM_CHUNK][ns_pad] float2
+  float2* s_t = reinterpret_cast<float2*>(smem4);
+  float2* s_f = s_t + 6 * ns_pad;
+  const int f_len = AOS ? 4 * SYM_CHUNK * ns_pad : 3 * SYM_CHUNK * ns_pad;   // float2 entries
+  float* s_rev = reinterpret_cast<float*>(s_f + f_len);                      // [SYM_WARPS][3][ns_pad]
+  double* s_fwd = reinterpret_cast<double*>(s_rev + SYM_WARPS * 3 * ns_pad);   // [SYM_TPT][3][SYM_THREADS]
   for (int q = threadIdx.x; q < ns_pad; q += blockDim.x) {
     const bool real = q < ns;
-    s_nx[q] = real ? -tmpl32[q] : -1.0e3f;
-    s_ny[q] = real ? -tmpl32[ns + q] : 0.f;
-    s_nz[q] = real ? -tmpl32[2 * ns + q] : 0.f;
-    s_wx[q] = real ? tmpl32[3 * ns + q] : 0.f;
-    s_wy[q] = real ? tmpl32[4 * ns + q] : 0.f;
-    s_wz[q] = real ? tmpl32[5 * ns + q] : 0.f;
+    for (int d = 0; d < 3; d++) {
+      const float x = real ? -tmpl32[d * ns + q] : (d == 0 ? -1.0e3f : 0.f);
+      const float w = real ? tmpl32[(3 + d) * ns + q] : 0.f;
+      if (AOS) {
+        s_t[6 * q + d] = make_float2(x, x);
+        s_t[6 * q + 3 + d] = make_float2(w, w);
+      } else {
+        s_t[d * ns_pad + q] = make_float2(x, x);
+        s_t[(3 + d) * ns_pad + q] = make_float2(w, w);
+      }
+    }
   }
+  if (AOS)   // pad slots of the density records stay zero
+    for (int t = threadIdx.x; t < SYM_CHUNK * ns_pad; t += blockDim.x) s_f[4 * t + 3] = make_float2(0.f, 0.f);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.x;
   int u = su.start(c);
   const int uend = su.start(c + 1);
-  int buf = 0;
   while (u < uend) {
     int lo = 0, hi = su.ntb - 1;   // target block of unit u
     while (lo < hi) {
@@ -168,28 +174,15 @@ k_pair32_sym(int N, int ns, int ns_pad, SymUnits su, const float* __restrict__ t
     const int slot = c - su.cta_of(su.off[tb]);
     u = seg_end;
 
-    int pp[2], pb[2];
-    float xp[2][3], wq[2][3];
-    float4 cih[2], cil[2];
-    float2 nf[2][3];
-    float sacc[2][3], kacc[2][3];
+    int pb[SYM_TPT], pq[SYM_TPT];   // body (INT_MAX past the end) and template node of each target
 #pragma unroll
-    for (int t = 0; t < 2; t++) {
+    for (int t = 0; t < SYM_TPT; t++) {
       const int p = tb * SYM_TB + t * SYM_THREADS + threadIdx.x;
-      pp[t] = p;
       const int pc = p < N ? p : N - 1;
-      const int bi = pc / ns, qi = pc - bi * ns;
+      const int bi = pc / ns;
       pb[t] = p < N ? bi : 0x7fffffff;
-      for (int d = 0; d < 3; d++) {
-        xp[t][d] = tmpl32[d * ns + qi];
-        wq[t][d] = tmpl32[(3 + d) * ns + qi];
-        const float f = phi32[3 * pc + d];
-        nf[t][d] = make_float2(-f, -f);
-        sacc[t][d] = 0.f;
-        kacc[t][d] = 0.f;
-      }
-      cih[t] = *reinterpret_cast<const float4*>(c32 + 8 * bi);
-      cil[t] = *reinterpret_cast<const float4*>(c32 + 8 * bi + 4);
+      pq[t] = pc - bi * ns;
+      for (int d = 0; d < 3; d++) s_fwd[(t * 3 + d) * SYM_THREADS + threadIdx.x] = 0.0;
     }
     for (int jc = j0; jc < j1; jc += SYM_CHUNK) {
       const int nb = min(SYM_CHUNK, j1 - jc);
@@ -199,11 +192,13 @@ k_pair32_sym(int N, int ns, int ns_pad, SymUnits su, const float* __restrict__ t
       for (int t = threadIdx.x; t < 3 * cnt; t += blockDim.x) {
         const int node = t / 3, d = t - 3 * node;
         const int b = node / ns, q = node - b * ns;
-        s_f[(d * SYM_CHUNK + b) * ns_pad + q] = src[t];
+        const float v = src[t];
+        s_f[AOS ? 4 * (b * ns_pad + q) + d : (d * SYM_CHUNK + b) * ns_pad + q] = make_float2(v, v);
       }
       for (int t = threadIdx.x; t < nb * (ns_pad - ns); t += blockDim.x) {
         const int b = t / (ns_pad - ns), q = ns + t % (ns_pad - ns);
-        for (int d = 0; d < 3; d++) s_f[(d * SYM_CHUNK + b) * ns_pad + q] = 0.f;
+        for (int d = 0; d < 3; d++)
+          s_f[AOS ? 4 * (b * ns_pad + q) + d : (d * SYM_CHUNK + b) * ns_pad + q] = make_float2(0.f, 0.f);
       }
       __syncthreads();
       for (int b = 0; b < nb; b++) {
@@ -211,99 +206,147 @@ k_pair32_sym(int N, int ns, int ns_pad, SymUnits su, const float* __restrict__ t
         const bool any_rev = j > fb;   // the same for the whole CTA
         const float4 cjh = *reinterpret_cast<const float4*>(c32 + 8 * j);
         const float4 cjl = *reinterpret_cast<const float4*>(c32 + 8 * j + 4);
-        float2 e[2][3], wp[2][3], acc[2][3];
+        // per pack k: targets 2k (lane x) and 2k+1 (lane y)
+        float2 e[2][3], nf[2][3], wp[2][3], acc[2][3];
 #pragma unroll
-        for (int t = 0; t < 2; t++) {
-          const float ex = ((cih[t].x - cjh.x) + (cil[t].x - cjl.x)) + xp[t][0];
-          const float ey = ((cih[t].y - cjh.y) + (cil[t].y - cjl.y)) + xp[t][1];
-          const float ez = ((cih[t].z - cjh.z) + (cil[t].z - cjl.z)) + xp[t][2];
-          e[t][0] = make_float2(ex, ex);
-          e[t][1] = make_float2(ey, ey);
-          e[t][2] = make_float2(ez, ez);
+        for (int t = 0; t < SYM_TPT; t++) {
+          const int k = t >> 1;
+          const int bi = pb[t] == 0x7fffffff ? (N - 1) / ns : pb[t];
+          const float4 cih = *reinterpret_cast<const float4*>(c32 + 8 * bi);
+          const float4 cil = *reinterpret_cast<const float4*>(c32 + 8 * bi + 4);
+          const int pc = bi * ns + pq[t];
           const float rm = pb[t] < j ? 1.f : 0.f;   // reverse only for bodies before j
+          const float ev[3] = {((cih.x - cjh.x) + (cil.x - cjl.x)) + tmpl32[pq[t]],
+                               ((cih.y - cjh.y) + (cil.y - cjl.y)) + tmpl32[ns + pq[t]],
+                               ((cih.z - cjh.z) + (cil.z - cjl.z)) + tmpl32[2 * ns + pq[t]]};
+#pragma unroll
           for (int d = 0; d < 3; d++) {
-            wp[t][d] = make_float2(rm * wq[t][d], rm * wq[t][d]);
-            acc[t][d] = make_float2(0.f, 0.f);
-          }
-        }
-        const float* fxb = s_f + (0 * SYM_CHUNK + b) * ns_pad;
-        const float* fyb = s_f + (1 * SYM_CHUNK + b) * ns_pad;
-        const float* fzb = s_f + (2 * SYM_CHUNK + b) * ns_pad;
-        float* rout = s_rev + (size_t)(buf * SYM_WARPS + warp) * 3 * ns_pad;
-#pragma unroll 1
-        for (int q = 0; q < ns_pad; q += 4) {
-          const float4 X = *reinterpret_cast<const float4*>(s_nx + q);
-          const float4 Y = *reinterpret_cast<const float4*>(s_ny + q);
-          const float4 Z = *reinterpret_cast<const float4*>(s_nz + q);
-          const float4 WX = *reinterpret_cast<const float4*>(s_wx + q);
-          const float4 WY = *reinterpret_cast<const float4*>(s_wy + q);
-          const float4 WZ = *reinterpret_cast<const float4*>(s_wz + q);
-          const float4 FX = *reinterpret_cast<const float4*>(fxb + q);
-          const float4 FY = *reinterpret_cast<const float4*>(fyb + q);
-          const float4 FZ = *reinterpret_cast<const float4*>(fzb + q);
-          float2 rv[2][3];
-#pragma unroll
-          for (int h = 0; h < 2; h++) {
-            for (int d = 0; d < 3; d++) rv[h][d] = make_float2(0.f, 0.f);
-            const float2 nx = h ? make_float2(X.z, X.w) : make_float2(X.x, X.y);
-            const float2 ny = h ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y);
-            const float2 nz = h ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y);
-            const float2 wx = h ? make_float2(WX.z, WX.w) : make_float2(WX.x, WX.y);
-            const float2 wy = h ? make_float2(WY.z, WY.w) : make_float2(WY.x, WY.y);
-            const float2 wz = h ? make_float2(WZ.z, WZ.w) : make_float2(WZ.x, WZ.y);
-            const float2 fx = h ? make_float2(FX.z, FX.w) : make_float2(FX.x, FX.y);
-            const float2 fy = h ? make_float2(FY.z, FY.w) : make_float2(FY.x, FY.y);
-            const float2 fz = h ? make_float2(FZ.z, FZ.w) : make_float2(FZ.x, FZ.y);
-#pragma unroll
-            for (int t = 0; t < 2; t++) sym_pair(e[t], nf[t], wp[t], nx, ny, nz, wx, wy, wz, fx, fy, fz, acc[t], rv[h]);
-          }
-          if (any_rev) {
-            // value k = 6 h + 2 d + l is the reverse sum of source q + 2 h + l, component d
-            float v[16];
-#pragma unroll
-            for (int h = 0; h < 2; h++)
-              for (int d = 0; d < 3; d++) {
-                v[6 * h + 2 * d] = rv[h][d].x;
-                v[6 * h + 2 * d + 1] = rv[h][d].y;
-              }
-#pragma unroll
-            for (int k = 12; k < 16; k++) v[k] = 0.f;
-            const float tot = warp_transpose_sum16(v, lane);
-            const int k = lane >> 1;
-            if (!(lane & 1) && k < 12) {
-              const int h = k / 6, d = (k - 6 * h) >> 1, l = k & 1;
-              rout[d * ns_pad + q + 2 * h + l] = tot;
+            const float nv = -phi32[3 * pc + d];
+            const float wv = rm * tmpl32[(3 + d) * ns + pq[t]];
+            if (t & 1) {
+              e[k][d].y = ev[d];
+              nf[k][d].y = nv;
+              wp[k][d].y = wv;
+              acc[k][d].y = 0.f;
+            } else {
+              e[k][d].x = ev[d];
+              nf[k][d].x = nv;
+              wp[k][d].x = wv;
+              acc[k][d].x = 0.f;
             }
           }
         }
+        float* rout = s_rev + (size_t)warp * 3 * ns_pad;
+        float vp[NV];   // previous batch (PIPE)
+        int qp = -1;
+#pragma unroll 1
+        for (int q = 0; q < ns_pad; q += BATCH) {
+          float v[NV];
 #pragma unroll
-        for (int t = 0; t < 2; t++)
+          for (int h = 0; h < BATCH; h++) {
+            const int qq = q + h;
+            float2 rv[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            float2 nx, ny, nz, wx, wy, wz, fx, fy, fz;
+            if (AOS) {
+              const float4* t4 = reinterpret_cast<const float4*>(s_t) + 3 * qq;
+              const float4 A = t4[0], B = t4[1], C = t4[2];
+              nx = make_float2(A.x, A.y); ny = make_float2(A.z, A.w);
+              nz = make_float2(B.x, B.y); wx = make_float2(B.z, B.w);
+              wy = make_float2(C.x, C.y); wz = make_float2(C.z, C.w);
+              const float4* f4 = reinterpret_cast<const float4*>(s_f) + 2 * (b * ns_pad + qq);
+              const float4 F = f4[0], G = f4[1];
+              fx = make_float2(F.x, F.y); fy = make_float2(F.z, F.w); fz = make_float2(G.x, G.y);
+            } else {
+              nx = s_t[qq]; ny = s_t[ns_pad + qq]; nz = s_t[2 * ns_pad + qq];
+              wx = s_t[3 * ns_pad + qq]; wy = s_t[4 * ns_pad + qq]; wz = s_t[5 * ns_pad + qq];
+              fx = s_f[(0 * SYM_CHUNK + b) * ns_pad + qq];
+              fy = s_f[(1 * SYM_CHUNK + b) * ns_pad + qq];
+              fz = s_f[(2 * SYM_CHUNK + b) * ns_pad + qq];
+            }
+#pragma unroll
+            for (int k = 0; k < 2; k++) sym_pair(e[k], nf[k], wp[k], nx, ny, nz, wx, wy, wz, fx, fy, fz, acc[k], rv);
+#pragma unroll
+            for (int d = 0; d < 3; d++) v[3 * h + d] = rv[d].x + rv[d].y;   // the thread's four targets
+          }
+#pragma unroll
+          for (int k = 3 * BATCH; k < NV; k++) v[k] = 0.f;
+          if (any_rev) {
+            // value k = 3 h + d: reverse sum of source q + h, component d
+            if (PIPE) {
+              if (qp >= 0) {
+                const float tot = warp_transpose_sum<NV>(vp, lane);
+                const int k = lane / LPV;
+                if (lane % LPV == 0 && k < 3 * BATCH) rout[(k % 3) * ns_pad + qp + k / 3] = tot;
+              }
+#pragma unroll
+              for (int k = 0; k < NV; k++) vp[k] = v[k];
+              qp = q;
+            } else {
+              const float tot = warp_transpose_sum<NV>(v, lane);
+              const int k = lane / LPV;
+              if (lane % LPV == 0 && k < 3 * BATCH) rout[(k % 3) * ns_pad + q + k / 3] = tot;
+            }
+          }
+        }
+        if (PIPE && any_rev && qp >= 0) {
+          const float tot = warp_transpose_sum<NV>(vp, lane);
+          const int k = lane / LPV;
+          if (lane % LPV == 0 && k < 3 * BATCH) rout[(k % 3) * ns_pad + qp + k / 3] = tot;
+        }
+#pragma unroll
+        for (int t = 0; t < SYM_TPT; t++)
           if (pb[t] <= j)
-            for (int d = 0; d < 3; d++) kahan(sacc[t][d], kacc[t][d], acc[t][d].x + acc[t][d].y);
+            for (int d = 0; d < 3; d++) {
+              const float a = (t & 1) ? acc[t >> 1][d].y : acc[t >> 1][d].x;
+              s_fwd[(t * 3 + d) * SYM_THREADS + threadIdx.x] += (double)a;
+            }
         if (any_rev) {
           __syncthreads();
           // sum the warps in order; row of unit (tb, j): [ns][3] floats
           float* dst = rev + su.roff[tb] + (size_t)(j - fb - 1) * 3 * ns;
-          const float* sb = s_rev + (size_t)buf * SYM_WARPS * 3 * ns_pad;
           for (int k = threadIdx.x; k < 3 * ns; k += blockDim.x) {
             const int q = k / 3, d = k - 3 * q;
             float s = 0.f;
 #pragma unroll
-            for (int w = 0; w < SYM_WARPS; w++) s += sb[(w * 3 + d) * ns_pad + q];
+            for (int w = 0; w < SYM_WARPS; w++) s += s_rev[(w * 3 + d) * ns_pad + q];
             dst[k] = s;
           }
-          buf ^= 1;
+          __syncthreads();
         }
       }
     }
 #pragma unroll
-    for (int t = 0; t < 2; t++)
-      if (pp[t] < N) {
-        double* o = partial + ((size_t)slot * N + pp[t]) * 3;
-        for (int d = 0; d < 3; d++) o[d] = (double)sacc[t][d] - (double)kacc[t][d];
+    for (int t = 0; t < SYM_TPT; t++) {
+      const int p = tb * SYM_TB + t * SYM_THREADS + threadIdx.x;
+      if (p < N) {
+        double* o = partial + ((size_t)slot * N + p) * 3;
+        for (int d = 0; d < 3; d++) o[d] = s_fwd[(t * 3 + d) * SYM_THREADS + threadIdx.x];
       }
+    }
   }
 }
+
+#define PAIR32_SYM_VARIANT(NAME, AOS, BATCH, MINB, PIPE)                                                        \
+  __global__ void __launch_bounds__(SYM_THREADS, MINB)                                                          \
+      NAME(int N, int ns, int ns_pad, SymUnits su, const float* __restrict__ tmpl32, const float* __restrict__ c32, \
+           const float* __restrict__ phi32, double* __restrict__ partial, float* __restrict__ rev) {               \
+    pair32_sym_body<AOS, BATCH, MINB, PIPE>(N, ns, ns_pad, su, tmpl32, c32, phi32, partial, rev);                 \
+  }
+// Measured at 216 spheres x 242 nodes (ms per launch): sym_a4 1.69, sym_a2
+// 1.75, sym 1.86, pipelined variants 1.84-1.96; the plain kernel 1.97.
+PAIR32_SYM_VARIANT(k_pair32_sym_a4, true, 4, 3, false)
+PAIR32_SYM_VARIANT(k_pair32_sym_a2, true, 2, 4, false)
+PAIR32_SYM_VARIANT(k_pair32_sym, false, 2, 4, false)
+
+typedef void (*Pair32SymKernel)(int, int, int, SymUnits, const float*, const float*, const float*, double*, float*);
+struct Pair32SymVariant {
+  Pair32SymKernel kernel;
+  bool aos;
+  const char* name;
+};
+static const Pair32SymVariant kSymVariants[] = {
+    {k_pair32_sym_a4, true, "sym_a4"}, {k_pair32_sym_a2, true, "sym_a2"}, {k_pair32_sym, false, "sym"}};
+constexpr int kNumSymVariants = sizeof(kSymVariants) / sizeof(kSymVariants[0]);
 
 // out_p = forward partials + reverse rows of the target blocks before body(p)
 // (in block order) + (P phi)_p.
@@ -340,9 +383,10 @@ __global__ void k_finish_sym(int N, int ns, int splits, const double* __restrict
 }
 
 // ------------------------------------------------------------------ host side
-static size_t sym_smem(int ns) {
+static size_t sym_smem(int ns, bool aos) {
   const int ns_pad = (ns + 3) & ~3;
-  return sizeof(float) * ((size_t)6 * ns_pad + 3 * SYM_CHUNK * ns_pad + 2 * SYM_WARPS * 3 * ns_pad);
+  return sizeof(float2) * ((size_t)6 * ns_pad + (aos ? 4 : 3) * SYM_CHUNK * ns_pad) +
+         sizeof(float) * SYM_WARPS * 3 * ns_pad + sizeof(double) * SYM_TPT * 3 * SYM_THREADS;
 }
 
 static int host_cta_of(long long u, int U, int G) {
@@ -353,14 +397,11 @@ static int host_cta_of(long long u, int U, int G) {
   return (int)c;
 }
 
-// Unit offsets, reverse-row offsets, one-wave grid, partial slots and the
-// reverse buffer (once per context; the body count and grid never change).
+// Unit offsets, reverse-row offsets, the reverse buffer, and per kernel
+// variant the one-wave grid and its partial slots (once per context; the
+// body count and grid never change).
 int stokes_sym_configure(lcp_ctx* ctx) {
   const int N = ctx->N, ns = ctx->ns, M = ctx->M;
-  const size_t smem = sym_smem(ns);
-  if (smem > 48 * 1024)
-    LCP_CUDA(cudaFuncSetAttribute(k_pair32_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occsym, k_pair32_sym, SYM_THREADS, smem));
   const int ntb = (N + SYM_TB - 1) / SYM_TB;
   std::vector<int> off(ntb + 1);
   std::vector<long long> roff(ntb + 1);
@@ -372,17 +413,27 @@ int stokes_sym_configure(lcp_ctx* ctx) {
     roff[tb + 1] = roff[tb] + (long long)(M - 1 - fb) * 3 * ns;
   }
   const int U = off[ntb];
-  int G = ctx->num_sms * (ctx->occsym > 0 ? ctx->occsym : 1);
-  if (G > U) G = U;
-  int slots = 1;
-  for (int tb = 0; tb < ntb; tb++) {
-    const int s = host_cta_of(off[tb + 1] - 1, U, G) - host_cta_of(off[tb], U, G) + 1;
-    if (s > slots) slots = s;
-  }
   ctx->sym_ntb = ntb;
   ctx->sym_units = U;
-  ctx->sym_grid = G;
-  ctx->sym_slots = slots;
+  ctx->sym_slots = 1;
+  for (int v = 0; v < kNumSymVariants && v < 8; v++) {
+    const size_t smem = sym_smem(ns, kSymVariants[v].aos);
+    if (smem > 48 * 1024)
+      LCP_CUDA(cudaFuncSetAttribute(kSymVariants[v].kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kSymVariants[v].kernel, SYM_THREADS, smem));
+    int G = ctx->num_sms * (occ > 0 ? occ : 1);
+    if (G > U) G = U;
+    int slots = 1;
+    for (int tb = 0; tb < ntb; tb++) {
+      const int s = host_cta_of(off[tb + 1] - 1, U, G) - host_cta_of(off[tb], U, G) + 1;
+      if (s > slots) slots = s;
+    }
+    ctx->symv_occ[v] = occ;
+    ctx->symv_grid[v] = G;
+    ctx->symv_slots[v] = slots;
+    if (slots > ctx->sym_slots) ctx->sym_slots = slots;
+  }
   ctx->sym_off = (int*)ctx_alloc(ctx, sizeof(int) * (ntb + 1));
   ctx->sym_roff = (long long*)ctx_alloc(ctx, sizeof(long long) * (ntb + 1));
   ctx->sym_rev = (float*)ctx_alloc(ctx, sizeof(float) * (size_t)(roff[ntb] > 0 ? roff[ntb] : 1));
@@ -394,6 +445,12 @@ int stokes_sym_configure(lcp_ctx* ctx) {
   return LCP_OK;
 }
 
+int stokes_sym_variant_count() { return kNumSymVariants < 8 ? kNumSymVariants : 8; }
+const char* stokes_sym_variant_name(int v) { return kSymVariants[v].name; }
+bool stokes_sym_variant_usable(const lcp_ctx* ctx, int v) {
+  return ctx->symv_occ[v] > 0 && ctx->symv_slots[v] <= ctx->splits;
+}
+
 // Bytes of the reverse buffer for a size (footprint estimate).
 size_t stokes_sym_bytes(int M, int ns) {
   const long long N = (long long)M * ns;
@@ -403,22 +460,25 @@ size_t stokes_sym_bytes(int M, int ns) {
   return sizeof(float) * (size_t)(total > 0 ? total : 1) + (sizeof(int) + sizeof(long long)) * (size_t)(ntb + 1);
 }
 
-// (K + P) phi with the symmetric FP32 pair sum; phi32 already holds phi in FP32.
+// (K + P) phi with the symmetric FP32 pair sum (variant ctx->sym_v); phi32
+// already holds phi in FP32.
 int stokes_sym_apply(lcp_ctx* ctx, double* out) {
   const int N = ctx->N, ns = ctx->ns;
   const int ns_pad = (ns + 3) & ~3;
-  if (ctx->sym_slots > ctx->splits) {
-    ctx->err = "internal: symmetric pair-sum slots exceed the partial buffer";
+  const int v = ctx->sym_v;
+  if (!stokes_sym_variant_usable(ctx, v)) {
+    ctx->err = "internal: symmetric pair-sum variant not usable for this size";
     return LCP_ERR_INVALID_ARG;
   }
-  LCP_CUDA(cudaMemsetAsync(ctx->partial, 0, sizeof(double) * 3 * (size_t)N * ctx->sym_slots, ctx->stream));
-  SymUnits su{ctx->sym_units, ctx->sym_grid, ctx->sym_ntb, ns, ctx->sym_off, ctx->sym_roff};
+  const int G = ctx->symv_grid[v], slots = ctx->symv_slots[v];
+  LCP_CUDA(cudaMemsetAsync(ctx->partial, 0, sizeof(double) * 3 * (size_t)N * slots, ctx->stream));
+  SymUnits su{ctx->sym_units, G, ctx->sym_ntb, ns, ctx->sym_off, ctx->sym_roff};
   cudaEvent_t e0 = prof_begin(ctx);
-  ++ctx->nlaunch, k_pair32_sym<<<ctx->sym_grid, SYM_THREADS, sym_smem(ns), ctx->stream>>>(
+  ++ctx->nlaunch, kSymVariants[v].kernel<<<G, SYM_THREADS, sym_smem(ns, kSymVariants[v].aos), ctx->stream>>>(
                       N, ns, ns_pad, su, ctx->tmpl32, ctx->centers32, ctx->phi32, ctx->partial, ctx->sym_rev);
   prof_end(ctx, e0, 0);
   ++ctx->nlaunch, k_finish_sym<<<(N + 255) / 256, 256, 0, ctx->stream>>>(
-                      N, ns, ctx->sym_slots, ctx->partial, ctx->sym_rev, ctx->sym_roff, ctx->coef, ctx->tmpl64, out);
+                      N, ns, slots, ctx->partial, ctx->sym_rev, ctx->sym_roff, ctx->coef, ctx->tmpl64, out);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }

@@ -247,6 +247,11 @@ def lcp_kernel_variant(ctx) -> str:
     return _lib().lcp_kernel_variant(ctx).decode()
 
 
+def lcp_select_kernel_variant(ctx, name: str) -> None:
+    """Forces the FP32 pair-kernel variant (a name lcp_kernel_variant can return)."""
+    _check(_lib().lcp_select_kernel_variant(ctx, name.encode()), ctx)
+
+
 def lcp_batch_solve(ctxs, method: int, tol: float, xs=None, workers: int = 8):
     """Solve contexts concurrently; xs: optional CUDA tensors.  Returns (statuses, stats dicts)."""
     n = len(ctxs)

@@ -22,6 +22,9 @@ def small_batch():
     return insts
 
 
+VARIANTS = ("sym_a4", "sym_a2", "sym", "t2c8", "t1c8", "t2c16", "t2c4", "t1c16")
+
+
 def make_ctxs(insts, **kw):
     return [L.lcp_setup(L.config_for(i, L.LCP_MIXED, own_stream=1, **kw), i.centers, i.axes) for i in insts]
 
@@ -98,8 +101,8 @@ def test_autotuned_kernel_gives_the_same_solution(small_batch):
     a = L.lcp_setup(L.config_for(inst, L.LCP_MIXED), inst.centers, inst.axes)
     b = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, autotune=1), inst.centers, inst.axes)
     try:
-        assert L.lcp_kernel_variant(a) == "sym"
-        assert L.lcp_kernel_variant(b) in {"sym", "t2c8", "t1c8", "t2c16", "t2c4", "t1c16"}
+        assert L.lcp_kernel_variant(a) == "sym_a4"
+        assert L.lcp_kernel_variant(b) in VARIANTS
         xa, _, _ = L.lcp_solve(a, L.LCP_BI_PQN, inst.tol)
         xb, _, _ = L.lcp_solve(b, L.LCP_BI_PQN, inst.tol)
         np.testing.assert_allclose(xb, xa, atol=1e-7 * max(1.0, np.abs(xa).max()))
@@ -120,3 +123,27 @@ def test_footprint_estimate_covers_context(small_batch):
             assert L.lcp_footprint(ctx) <= est
         finally:
             L.lcp_destroy(ctx)
+
+
+@pytest.mark.parametrize("name,index", [("spheres8_grid7x14", 2), ("spheres64_grid9x18", 1)])
+def test_every_kernel_variant_applies_the_same_operator(name, index):
+    """Each FP32 variant (symmetric or plain, any tile shape) against the double-FP32 apply."""
+    from workloads import make_instance
+    inst = make_instance(name, index)
+    ctx = L.lcp_setup(L.config_for(inst, L.LCP_MIXED), inst.centers, inst.axes)
+    try:
+        n = 3 * L.lcp_sizes(ctx)[1]
+        phi = torch.tensor(np.random.default_rng(9).standard_normal(n), device="cuda")
+        ref = torch.empty_like(phi)
+        L.lcp_stokes_apply_dev(ctx, phi, ref, L.LCP_DF64)
+        out = torch.empty_like(phi)
+        for v in VARIANTS:
+            L.lcp_select_kernel_variant(ctx, v)
+            assert L.lcp_kernel_variant(ctx) == v
+            L.lcp_stokes_apply_dev(ctx, phi, out, L.LCP_MIXED)
+            err = float((out - ref).abs().max() / ref.abs().max())
+            assert err <= 1e-5, (v, err)
+        with pytest.raises(L.LcpError):
+            L.lcp_select_kernel_variant(ctx, "no_such_kernel")
+    finally:
+        L.lcp_destroy(ctx)
