@@ -74,7 +74,7 @@ typedef struct {
   int ir_maxit;             /* LCP_MIXED: maximum refinement sweeps */
   int kmax;                 /* PQN outer iteration limit */
   int kmax_inner;           /* Bi-PQN subproblem / low-fidelity init iteration limit */
-  int memory;               /* quasi-Newton pairs kept (FIFO beyond) */
+  int memory;               /* quasi-Newton pairs kept, 1..48 (oldest quarter dropped when full) */
   int ssn_maxit;            /* semi-smooth Newton iterations per prox */
   double forcing;           /* Bi-PQN subproblem tolerance = max(0.1 tol, forcing * kkt) */
   int precondition;         /* 1: flexible GMRES with the isolated-sphere block-diagonal inverse */

@@ -72,7 +72,8 @@ static int validate(const lcp_config* c, int M, const double* centers, std::stri
   if (c->precision != LCP_FP64 && c->precision != LCP_MIXED) { *err = "precision must be LCP_FP64 or LCP_MIXED"; return LCP_ERR_INVALID_ARG; }
   if (c->residual_precision != LCP_FP64 && c->residual_precision != LCP_DF64) { *err = "residual_precision must be LCP_FP64 or LCP_DF64"; return LCP_ERR_INVALID_ARG; }
   if (c->gmres_restart < 1 || c->gmres_restart > 200 || c->gmres_maxit < 1) { *err = "gmres_restart in [1, 200], gmres_maxit >= 1"; return LCP_ERR_INVALID_ARG; }
-  if (c->memory < 1 || c->memory > 60) { *err = "memory in [1, 60]"; return LCP_ERR_INVALID_ARG; }
+  // the direction kernel keeps its r x r systems in shared memory (<= 227 KB: r <= 48)
+  if (c->memory < 1 || c->memory > 48) { *err = "memory in [1, 48]"; return LCP_ERR_INVALID_ARG; }
   if (c->kmax < 1 || c->kmax > 120 || c->kmax_inner < 1) { *err = "kmax in [1, 120], kmax_inner >= 1"; return LCP_ERR_INVALID_ARG; }
   if (!(c->gmres_tol > 0) || !(c->inner_tol > 0) || c->ir_maxit < 1 || c->ssn_maxit < 1) { *err = "tolerances and iteration limits must be positive"; return LCP_ERR_INVALID_ARG; }
   for (int i = 0; i < 3 * M; i++)

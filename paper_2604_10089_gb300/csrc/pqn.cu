@@ -62,139 +62,68 @@ __device__ void bmultidot(const double* __restrict__ Mt, int n, int rows, const 
   __syncthreads();
 }
 
-// In-place Gaussian elimination with partial pivoting on A (m x m, row-major,
-// leading dim lda) and right-hand sides B (m x nr, leading dim ldb); on exit B
-// holds the solution.  Block-parallel; T = double or float.
+// Solves A X = B (A: m x m row-major, leading dimension lda; B: m x nr) by
+// Gaussian elimination with partial pivoting, block-parallel.  Rows are not
+// exchanged: step k takes the unused row with the largest |A[i][k]| (warp 0),
+// then all threads eliminate column k from the other unused rows (two block
+// barriers per step).  Back substitution runs one warp per right-hand side.
+// X (m x nr, leading dimension ldx) receives the solution; A and B are
+// overwritten.  perm, used: int[m] in shared memory.  T = double or float.
 template <typename T>
-__device__ void block_solve(T* A, int lda, T* B, int ldb, int m, int nr, int* piv_slot) {
+__device__ void pivot_solve(T* A, int lda, T* B, int ldb, int m, int nr, T* X, int ldx, int* perm, int* used) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) used[i] = 0;
+  __syncthreads();
   for (int k = 0; k < m; k++) {
-    if (threadIdx.x == 0) {
-      int p = k;
-      T best = fabs(A[k * lda + k]);
-      for (int i = k + 1; i < m; i++) {
-        const T v = fabs(A[i * lda + k]);
-        if (v > best) { best = v; p = i; }
-      }
-      *piv_slot = p;
-    }
-    __syncthreads();
-    const int p = *piv_slot;
-    if (p != k) {
-      for (int j = threadIdx.x; j < m; j += blockDim.x) { T t = A[k * lda + j]; A[k * lda + j] = A[p * lda + j]; A[p * lda + j] = t; }
-      for (int j = threadIdx.x; j < nr; j += blockDim.x) { T t = B[k * ldb + j]; B[k * ldb + j] = B[p * ldb + j]; B[p * ldb + j] = t; }
-    }
-    __syncthreads();
-    const T piv = A[k * lda + k];
-    const int rows = m - k - 1, cols = m - k - 1 + nr;
-    for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) {
-      const int i = k + 1 + t / cols, c = t % cols;
-      const T f = A[i * lda + k] / piv;
-      if (c < m - k - 1) {
-        const int j = k + 1 + c;
-        A[i * lda + j] -= f * A[k * lda + j];
-      } else {
-        const int j = c - (m - k - 1);
-        B[i * ldb + j] -= f * B[k * ldb + j];
-      }
-    }
-    __syncthreads();
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[i * lda + k] = 0;
-    __syncthreads();
-  }
-  for (int k = m - 1; k >= 0; k--) {
-    for (int j = threadIdx.x; j < nr; j += blockDim.x) B[k * ldb + j] /= A[k * lda + k];
-    __syncthreads();
-    for (int t = threadIdx.x; t < k * nr; t += blockDim.x) {
-      const int i = t / nr, j = t % nr;
-      B[i * ldb + j] -= A[i * lda + k] * B[k * ldb + j];
-    }
-    __syncthreads();
-  }
-}
-
-// Same system solved by warp 0 alone (no block barriers): partial pivoting by a
-// warp-wide argmax, lanes own rows during elimination and back substitution.
-// The other warps wait at the barrier that ends the call.
-template <typename T>
-__device__ void warp_solve(T* A, int lda, T* B, int ldb, int m, int nr) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int k = 0; k < m; k++) {
-      T best = -1;
-      int arg = k;
-      for (int i = k + lane; i < m; i += 32) {
-        const T v = fabs(A[i * lda + k]);
-        if (v > best) { best = v; arg = i; }
-      }
+    if (w == 0) {
+      T best = T(-1);
+      int arg = m;
+      for (int i = lane; i < m; i += 32)
+        if (!used[i]) {
+          const T v = fabs(A[i * lda + k]);
+          if (v > best) { best = v; arg = i; }
+        }
       for (int o = 16; o > 0; o >>= 1) {
         const T ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
         if (ov > best || (ov == best && oa < arg)) { best = ov; arg = oa; }
       }
-      if (arg != k) {
-        for (int j = lane; j < m; j += 32) { const T t = A[k * lda + j]; A[k * lda + j] = A[arg * lda + j]; A[arg * lda + j] = t; }
-        for (int j = lane; j < nr; j += 32) { const T t = B[k * ldb + j]; B[k * ldb + j] = B[arg * ldb + j]; B[arg * ldb + j] = t; }
-      }
-      __syncwarp();
-      const T inv = T(1) / A[k * lda + k];
-      for (int i = k + 1 + lane; i < m; i += 32) {
-        const T f = A[i * lda + k] * inv;
-        for (int j = k + 1; j < m; j++) A[i * lda + j] -= f * A[k * lda + j];
-        for (int j = 0; j < nr; j++) B[i * ldb + j] -= f * B[k * ldb + j];
-        A[i * lda + k] = 0;
-      }
-      __syncwarp();
+      if (lane == 0) { perm[k] = arg; used[arg] = 1; }
     }
+    __syncthreads();
+    const int p = perm[k];
+    const T piv = A[p * lda + k];
+    const int ca = m - k - 1, cols = ca + nr;
+    for (int t = threadIdx.x; t < m * cols; t += blockDim.x) {
+      const int i = t / cols, c = t - i * cols;
+      if (used[i]) continue;
+      const T f = A[i * lda + k] / piv;
+      if (c < ca) A[i * lda + k + 1 + c] -= f * A[p * lda + k + 1 + c];
+      else B[i * ldb + (c - ca)] -= f * B[p * ldb + (c - ca)];
+    }
+    __syncthreads();
+  }
+  for (int c = w; c < nr; c += nw) {
     for (int k = m - 1; k >= 0; k--) {
-      const T d = A[k * lda + k];
-      for (int j = lane; j < nr; j += 32) B[k * ldb + j] /= d;
-      __syncwarp();
-      for (int i = lane; i < k; i += 32) {
-        const T f = A[i * lda + k];
-        for (int j = 0; j < nr; j++) B[i * ldb + j] -= f * B[k * ldb + j];
+      const int p = perm[k];
+      const T xk = B[p * ldb + c] / A[p * lda + k];
+      for (int kk = lane; kk < k; kk += 32) {
+        const int q = perm[kk];
+        B[q * ldb + c] -= A[q * lda + k] * xk;
       }
+      if (lane == 0) X[k * ldx + c] = xk;
       __syncwarp();
     }
   }
   __syncthreads();
 }
 
-// q = H g with H_0 = I (Nocedal-Wright two-loop recursion over the r pairs).
-__device__ void two_loop(const PqnDev& pq, const PqnWork& wk, int r, const double* g, double* q, double* alpha,
-                         double* red) {
-  const int n = pq.n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) q[i] = g[i];
-  __syncthreads();
-  for (int k = r - 1; k >= 0; k--) {
-    const double* s = pq.S + (size_t)k * n;
-    const double* y = pq.Y + (size_t)k * n;
-    double part = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) part += s[i] * q[i];
-    const double a = bsum(part, red) / wk.ys[k];
-    if (threadIdx.x == 0) alpha[k] = a;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) q[i] -= a * y[i];
-    __syncthreads();
-  }
-  const double hd = 1.0 / delta_of(pq);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) q[i] *= hd;
-  __syncthreads();
-  for (int k = 0; k < r; k++) {
-    const double* s = pq.S + (size_t)k * n;
-    const double* y = pq.Y + (size_t)k * n;
-    double part = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) part += y[i] * q[i];
-    const double beta = bsum(part, red) / wk.ys[k];
-    const double a = alpha[k];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) q[i] += (a - beta) * s[i];
-    __syncthreads();
-  }
-}
-
-// Shared-memory layout of the prox for r <= R.
+// Shared-memory layout of the direction kernel for r <= R pairs.
+constexpr int GRAM_CHUNK = 64;   // contacts staged per chunk of the masked Grams
 struct ProxSmem {
-  double *X, *UCV, *VCV, *tmp, *al, *alt, *G, *Gt, *c, *udv;
-  float *J, *gf, *GUU, *GVU, *GVV, *T1, *T2;
-  int* piv;
+  double *X, *UCV, *VCV, *tmp, *XB, *XS, *al, *alt, *G, *Gt, *c, *udv, *wg, *cw;
+  float *J, *gf, *dx, *GUU, *GVU, *GVV, *T1, *T2, *Um, *Vm;
+  int *perm, *used;
 };
 
 __device__ ProxSmem prox_smem(void* base, int R) {
@@ -204,26 +133,123 @@ __device__ ProxSmem prox_smem(void* base, int R) {
   s.UCV = d; d += R * R;
   s.VCV = d; d += R * R;
   s.tmp = d; d += R * R;
+  s.XB = d; d += R * (R + 1);
+  s.XS = d; d += R * (R + 1);
   s.al = d; d += 2 * R;
   s.alt = d; d += 2 * R;
   s.G = d; d += 2 * R;
   s.Gt = d; d += 2 * R;
   s.c = d; d += 2 * R;
   s.udv = d; d += 2 * R;
+  s.wg = d; d += 2 * R;
+  s.cw = d; d += 2 * R;
   float* f = (float*)d;
   s.J = f; f += 4 * R * R;
   s.gf = f; f += 2 * R;
+  s.dx = f; f += 2 * R;
   s.GUU = f; f += R * R;
   s.GVU = f; f += R * R;
   s.GVV = f; f += R * R;
   s.T1 = f; f += R * R;
   s.T2 = f; f += R * R;
-  s.piv = (int*)f;
+  const int Re = (R + 1) & ~1;
+  s.Um = f; f += Re * (GRAM_CHUNK + 1);
+  s.Vm = f; f += Re * (GRAM_CHUNK + 1);
+  s.perm = (int*)f;
+  s.used = s.perm + 2 * R;
   return s;
 }
 
 __host__ __device__ inline size_t prox_smem_bytes(int R) {
-  return sizeof(double) * (4 * R * R + 12 * R) + sizeof(float) * (9 * R * R + 2 * R) + 64;
+  const int Re = (R + 1) & ~1;
+  return sizeof(double) * (4 * R * R + 2 * R * (R + 1) + 16 * R) +
+         sizeof(float) * (9 * R * R + 4 * R + 2 * Re * (GRAM_CHUNK + 1)) + sizeof(int) * 4 * R + 64;
+}
+
+// Masked Grams GUU = U^T L U, GVU = V^T L U, GVV = V^T L V (FP32, r x r,
+// row-major), L = diag(lam) with lam in {0, 1}: with Um = L U and Vm = L V
+// they are Um^T Um, Vm^T Um, Vm^T Vm.  Contacts are staged through shared
+// memory GRAM_CHUNK at a time (row stride GRAM_CHUNK + 1: conflict-free);
+// each thread accumulates 2 x 2 blocks, the symmetric Grams only on and
+// above the diagonal.
+__device__ void masked_grams(const PqnWork& wk, int n, int r, ProxSmem& sm) {
+  const int re = (r + 1) & ~1, h = re / 2;
+  const int ntri = h * (h + 1) / 2, nblk = 2 * ntri + h * h;
+  constexpr int LD = GRAM_CHUNK + 1;
+  float acc[2][4];
+  for (int q = 0; q < 2; q++)
+    for (int e = 0; e < 4; e++) acc[q][e] = 0.f;
+  for (int i0 = 0; i0 < n; i0 += GRAM_CHUNK) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < re * GRAM_CHUNK; t += blockDim.x) {
+      const int k = t / GRAM_CHUNK, ii = t - k * GRAM_CHUNK, i = i0 + ii;
+      const bool in = k < r && i < n;
+      const float l = in ? wk.lam[i] : 0.f;
+      sm.Um[k * LD + ii] = in ? l * wk.U32[(size_t)k * n + i] : 0.f;
+      sm.Vm[k * LD + ii] = in ? l * wk.V32[(size_t)k * n + i] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      const int bidx = threadIdx.x + q * blockDim.x;
+      if (bidx >= nblk) break;
+      int which, bk, bl;   // 0: UU (bk <= bl), 1: VU, 2: VV (bk <= bl)
+      if (bidx < ntri || bidx >= ntri + h * h) {
+        which = bidx < ntri ? 0 : 2;
+        int t = bidx < ntri ? bidx : bidx - ntri - h * h;
+        bk = 0;
+        while (t >= h - bk) { t -= h - bk; bk++; }
+        bl = bk + t;
+      } else {
+        which = 1;
+        const int t = bidx - ntri;
+        bk = t / h;
+        bl = t - bk * h;
+      }
+      const float* A = which == 0 ? sm.Um : sm.Vm;
+      const float* B = which == 2 ? sm.Vm : sm.Um;
+      const float* a0 = A + (2 * bk) * LD;
+      const float* a1 = a0 + LD;
+      const float* b0 = B + (2 * bl) * LD;
+      const float* b1 = b0 + LD;
+      float s00 = acc[q][0], s01 = acc[q][1], s10 = acc[q][2], s11 = acc[q][3];
+#pragma unroll 8
+      for (int ii = 0; ii < GRAM_CHUNK; ii++) {
+        const float x0 = a0[ii], x1 = a1[ii], y0 = b0[ii], y1 = b1[ii];
+        s00 = fmaf(x0, y0, s00);
+        s01 = fmaf(x0, y1, s01);
+        s10 = fmaf(x1, y0, s10);
+        s11 = fmaf(x1, y1, s11);
+      }
+      acc[q][0] = s00; acc[q][1] = s01; acc[q][2] = s10; acc[q][3] = s11;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; q++) {
+    const int bidx = threadIdx.x + q * blockDim.x;
+    if (bidx >= nblk) break;
+    int which, bk, bl;
+    if (bidx < ntri || bidx >= ntri + h * h) {
+      which = bidx < ntri ? 0 : 2;
+      int t = bidx < ntri ? bidx : bidx - ntri - h * h;
+      bk = 0;
+      while (t >= h - bk) { t -= h - bk; bk++; }
+      bl = bk + t;
+    } else {
+      which = 1;
+      const int t = bidx - ntri;
+      bk = t / h;
+      bl = t - bk * h;
+    }
+    float* Gm = which == 0 ? sm.GUU : (which == 1 ? sm.GVU : sm.GVV);
+    for (int e = 0; e < 4; e++) {
+      const int k = 2 * bk + (e >> 1), l = 2 * bl + (e & 1);
+      if (k >= r || l >= r) continue;
+      Gm[k * r + l] = acc[q][e];
+      if (which != 1) Gm[l * r + k] = acc[q][e];
+    }
+  }
+  __syncthreads();
 }
 
 // Residual of the prox root function at (al = [a; at]); writes z, the mask
@@ -266,36 +292,17 @@ __device__ double ssn_residual(const PqnDev& pq, const PqnWork& wk, int r, const
   return sqrt(bsum(part, red));
 }
 
-// z = prox^B(xt), B = I + U U^T - V V^T with r pairs.  Returns Newton steps
-// (negative when the fallback coordinate descent was needed).
+// z = prox^B(xt), B = delta I + U U^T - V V^T with r pairs.  The caller has
+// set sm.X = C^-1 U^T V (C = delta I + U^T U), sm.UCV = U^T V - U^T U X and
+// sm.VCV = V^T V - V^T U X.  Returns Newton steps (negative when the
+// fallback coordinate descent was needed).
 __device__ int prox_ssn(const PqnDev& pq, const PqnWork& wk, int r, const double* xt, double* zout,
-                        void* smem_base, double* red, int jmax) {
+                        ProxSmem& sm, double* red, int jmax) {
   const int n = pq.n;
   if (r == 0) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) zout[i] = xt[i] > 0.0 ? xt[i] : 0.0;
     __syncthreads();
     return 0;
-  }
-  const int R = pq.rmax;
-  ProxSmem sm = prox_smem(smem_base, R);
-  // small = I + U^T U (in tmp), X = small^{-1} U^T V
-  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
-    const int k = t / r, l = t % r;
-    sm.tmp[t] = pq.UU[k * R + l] + (k == l ? delta_of(pq) : 0.0);
-    sm.X[t] = pq.UV[k * R + l];
-  }
-  __syncthreads();
-  warp_solve<double>(sm.tmp, r, sm.X, r, r, r);
-  // UCV = UV - UU X ; VCV = VV - UV^T X
-  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
-    const int k = t / r, l = t % r;
-    double s1 = pq.UV[k * R + l], s2 = pq.VV[k * R + l];
-    for (int m = 0; m < r; m++) {
-      s1 -= pq.UU[k * R + m] * sm.X[m * r + l];
-      s2 -= pq.UV[m * R + k] * sm.X[m * r + l];
-    }
-    sm.UCV[t] = s1;
-    sm.VCV[t] = s2;
   }
   for (int k = threadIdx.x; k < 2 * r; k += blockDim.x) sm.al[k] = 0.0;
   __syncthreads();
@@ -311,26 +318,7 @@ __device__ int prox_ssn(const PqnDev& pq, const PqnWork& wk, int r, const double
   bool ok = false;
   for (; j < jmax; j++) {
     if (gn <= 1e-13 * scale) { ok = true; break; }
-    // masked Grams in FP32: one warp per entry, lanes stride the contacts
-    // (coalesced); the symmetric U^T L U and V^T L V only for l >= k
-    {
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-      for (int t = wid; t < 3 * r * r; t += PQN_W) {
-        const int which = t / (r * r), e = t % (r * r), k = e / r, l = e % r;
-        if (which != 1 && l < k) continue;
-        const float* ak = (which == 0 ? wk.U32 : wk.V32) + (size_t)k * n;
-        const float* bl = (which == 2 ? wk.V32 : wk.U32) + (size_t)l * n;
-        float acc = 0.f;
-        for (int i = lane; i < n; i += 32) acc = fmaf(ak[i] * wk.lam[i], bl[i], acc);
-        acc = warp_sumf(acc);
-        if (lane == 0) {
-          float* G = which == 0 ? sm.GUU : (which == 1 ? sm.GVU : sm.GVV);
-          G[k * r + l] = acc;
-          if (which != 1) G[l * r + k] = acc;
-        }
-      }
-    }
-    __syncthreads();
+    masked_grams(wk, n, r, sm);
     // T1 = GUU X, T2 = GVU X
     for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
       const int k = t / r, l = t % r;
@@ -361,11 +349,11 @@ __device__ int prox_ssn(const PqnDev& pq, const PqnWork& wk, int r, const double
     }
     for (int k = threadIdx.x; k < m2; k += blockDim.x) sm.gf[k] = (float)sm.G[k];
     __syncthreads();
-    warp_solve<float>(sm.J, m2, sm.gf, 1, m2, 1);
+    pivot_solve<float>(sm.J, m2, sm.gf, 1, m2, 1, sm.dx, 1, sm.perm, sm.used);
     // backtracking on ||G||
     double t = 1.0;
     for (int bt = 0; bt < 30; bt++) {
-      for (int k = threadIdx.x; k < m2; k += blockDim.x) sm.alt[k] = sm.al[k] - t * (double)sm.gf[k];
+      for (int k = threadIdx.x; k < m2; k += blockDim.x) sm.alt[k] = sm.al[k] - t * (double)sm.dx[k];
       __syncthreads();
       const double gt = ssn_residual(pq, wk, r, xt, sm.alt, sm, sm.Gt, red);
       if (gt <= (1.0 - 1e-4 * t) * gn || t < 1e-8) {
@@ -454,17 +442,84 @@ __global__ void __launch_bounds__(PQN_T) k_pqn_grad(PqnDev pq, const double* Ax,
 }
 
 // Direction of Algorithm 1: xt = x - H g, xh = prox^B(xt), p = xh - x, with
-// the projected-gradient fallback when p^T g >= 0 (memory reset).
+// the projected-gradient fallback when p^T g >= 0 (memory reset).  H g is
+// taken from the unrolled model B = delta I + W S W^T (W = [U V],
+// S = diag(I, -I)) by the Woodbury identity,
+//   H g = (g - W K^-1 W^T g) / delta,   K = delta S + W^T W,
+// with K eliminated in blocks through C = delta I + U^T U (whose solve with
+// U^T V the prox needs as well) and the Schur complement
+// V^T V - V^T U C^-1 U^T V - delta I; this is the same H as the two-loop
+// recursion over the stored pairs, in O(n r + r^3) work without a chain of
+// 2r reductions.
 __global__ void __launch_bounds__(PQN_T) k_pqn_direction(PqnDev pq, PqnWork wk, int jmax) {
   extern __shared__ double smem[];
   __shared__ double red[32];
-  __shared__ double alpha[128];
   const int n = pq.n;
   const int r = *pq.r;
-  two_loop(pq, wk, r, pq.g, pq.xt, alpha, red);     // xt = H g
-  for (int i = threadIdx.x; i < n; i += blockDim.x) pq.xt[i] = pq.x[i] - pq.xt[i];   // x_tilde = x - H g
-  __syncthreads();
-  const int it = prox_ssn(pq, wk, r, pq.xt, pq.xh, smem, red, jmax);
+  const int R = pq.rmax;
+  const double dl = delta_of(pq), idl = 1.0 / dl;
+  ProxSmem sm = prox_smem(smem, R);
+  if (r == 0) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) pq.xt[i] = pq.x[i] - idl * pq.g[i];
+    __syncthreads();
+  } else {
+    bmultidot(pq.U, n, r, pq.g, sm.wg);       // U^T g
+    bmultidot(pq.V, n, r, pq.g, sm.wg + r);   // V^T g
+    // C [X | y1] = [U^T V | U^T g]
+    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+      const int k = t / r, l = t - k * r;
+      sm.tmp[t] = pq.UU[k * R + l] + (k == l ? dl : 0.0);
+    }
+    for (int t = threadIdx.x; t < r * (r + 1); t += blockDim.x) {
+      const int k = t / (r + 1), l = t - k * (r + 1);
+      sm.XB[t] = l < r ? pq.UV[k * R + l] : sm.wg[k];
+    }
+    __syncthreads();
+    pivot_solve<double>(sm.tmp, r, sm.XB, r + 1, r, r + 1, sm.XS, r + 1, sm.perm, sm.used);
+    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+      const int k = t / r, l = t - k * r;
+      sm.X[t] = sm.XS[k * (r + 1) + l];
+    }
+    __syncthreads();
+    // UCV = UV - UU X ; VCV = VV - UV^T X
+    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+      const int k = t / r, l = t % r;
+      double s1 = pq.UV[k * R + l], s2 = pq.VV[k * R + l];
+      for (int m = 0; m < r; m++) {
+        s1 -= pq.UU[k * R + m] * sm.X[m * r + l];
+        s2 -= pq.UV[m * R + k] * sm.X[m * r + l];
+      }
+      sm.UCV[t] = s1;
+      sm.VCV[t] = s2;
+    }
+    __syncthreads();
+    // (VCV - delta I) c2 = V^T g - (U^T V)^T y1 ; c1 = y1 - X c2
+    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+      const int k = t / r, l = t - k * r;
+      sm.tmp[t] = sm.VCV[t] - (k == l ? dl : 0.0);
+    }
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+      double v = sm.wg[r + k];
+      for (int m = 0; m < r; m++) v -= pq.UV[m * R + k] * sm.XS[m * (r + 1) + r];
+      sm.c[k] = v;
+    }
+    __syncthreads();
+    pivot_solve<double>(sm.tmp, r, sm.c, 1, r, 1, sm.cw + r, 1, sm.perm, sm.used);
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+      double v = sm.XS[k * (r + 1) + r];
+      for (int m = 0; m < r; m++) v -= sm.X[k * r + m] * sm.cw[r + m];
+      sm.cw[k] = v;
+    }
+    __syncthreads();
+    // x_tilde = x - (g - U c1 - V c2) / delta
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double w = pq.g[i];
+      for (int k = 0; k < r; k++) w -= pq.U[(size_t)k * n + i] * sm.cw[k] + pq.V[(size_t)k * n + i] * sm.cw[r + k];
+      pq.xt[i] = pq.x[i] - idl * w;
+    }
+    __syncthreads();
+  }
+  const int it = prox_ssn(pq, wk, r, pq.xt, pq.xh, sm, red, jmax);
   double part = 0.0, amax = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double p = pq.xh[i] - pq.x[i];
