@@ -349,37 +349,41 @@ static const Pair32SymVariant kSymVariants[] = {
 constexpr int kNumSymVariants = sizeof(kSymVariants) / sizeof(kSymVariants[0]);
 
 // out_p = forward partials + reverse rows of the target blocks before body(p)
-// (in block order) + (P phi)_p.
+// (in block order) + (P phi)_p.  One thread per node component; the reverse
+// rows are read four blocks at a time (independent loads in flight).
 __global__ void k_finish_sym(int N, int ns, int splits, const double* __restrict__ partial,
                              const float* __restrict__ rev, const long long* __restrict__ roff,
                              const double* __restrict__ coef, const double* __restrict__ tmpl64,
                              double* __restrict__ out) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N) return;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-  for (int s = 0; s < splits; s++) {
-    const double* o = partial + ((size_t)s * N + p) * 3;
-    a0 += o[0];
-    a1 += o[1];
-    a2 += o[2];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * N) return;
+  const int p = t / 3, d = t - 3 * p;
+  double a = 0.0;
+  for (int s = 0; s < splits; s++) a += partial[(size_t)s * 3 * N + t];
+  const int i = p / ns, q = p - i * ns;
+  const int nbefore = (i * ns + SYM_TB - 1) / SYM_TB;   // blocks whose first body is before i
+  const long long within = 3LL * q + d;
+  float r4[4];
+  int tb = 0;
+  for (; tb + 4 <= nbefore; tb += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int fb = ((tb + u) * SYM_TB) / ns;
+      r4[u] = rev[roff[tb + u] + (long long)(i - fb - 1) * 3 * ns + within];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) a += (double)r4[u];
   }
-  const int i = p / ns, q = p % ns;
-  const int ntb_before = (int)(((long long)i * ns + SYM_TB - 1) / SYM_TB);   // blocks with first body < i
-  for (int tb = 0; tb < ntb_before; tb++) {
-    const int fb = (int)(((long long)tb * SYM_TB) / ns);
-    const float* r = rev + roff[tb] + ((size_t)(i - fb - 1) * ns + q) * 3;
-    a0 += (double)r[0];
-    a1 += (double)r[1];
-    a2 += (double)r[2];
+  for (; tb < nbefore; tb++) {
+    const int fb = (tb * SYM_TB) / ns;
+    a += (double)rev[roff[tb] + (long long)(i - fb - 1) * 3 * ns + within];
   }
   const double* c = coef + 6 * i;
   const double* xi = tmpl64 + 8 * q;
-  a0 += c[0] + (c[4] * xi[2] - c[5] * xi[1]);
-  a1 += c[1] + (c[5] * xi[0] - c[3] * xi[2]);
-  a2 += c[2] + (c[3] * xi[1] - c[4] * xi[0]);
-  out[3 * p] = a0;
-  out[3 * p + 1] = a1;
-  out[3 * p + 2] = a2;
+  if (d == 0) a += c[0] + (c[4] * xi[2] - c[5] * xi[1]);
+  else if (d == 1) a += c[1] + (c[5] * xi[0] - c[3] * xi[2]);
+  else a += c[2] + (c[3] * xi[1] - c[4] * xi[0]);
+  out[t] = a;
 }
 
 // ------------------------------------------------------------------ host side
@@ -434,6 +438,10 @@ int stokes_sym_configure(lcp_ctx* ctx) {
     ctx->symv_slots[v] = slots;
     if (slots > ctx->sym_slots) ctx->sym_slots = slots;
   }
+  // default: the symmetric sum when every CTA gets several units (otherwise
+  // the one-wave balance of the plain kernel's finer units wins)
+  ctx->sym = U >= 4 * ctx->symv_grid[0];
+  ctx->sym_v = 0;
   ctx->sym_off = (int*)ctx_alloc(ctx, sizeof(int) * (ntb + 1));
   ctx->sym_roff = (long long*)ctx_alloc(ctx, sizeof(long long) * (ntb + 1));
   ctx->sym_rev = (float*)ctx_alloc(ctx, sizeof(float) * (size_t)(roff[ntb] > 0 ? roff[ntb] : 1));
@@ -477,7 +485,7 @@ int stokes_sym_apply(lcp_ctx* ctx, double* out) {
   ++ctx->nlaunch, kSymVariants[v].kernel<<<G, SYM_THREADS, sym_smem(ns, kSymVariants[v].aos), ctx->stream>>>(
                       N, ns, ns_pad, su, ctx->tmpl32, ctx->centers32, ctx->phi32, ctx->partial, ctx->sym_rev);
   prof_end(ctx, e0, 0);
-  ++ctx->nlaunch, k_finish_sym<<<(N + 255) / 256, 256, 0, ctx->stream>>>(
+  ++ctx->nlaunch, k_finish_sym<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(
                       N, ns, slots, ctx->partial, ctx->sym_rev, ctx->sym_roff, ctx->coef, ctx->tmpl64, out);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;

@@ -101,7 +101,7 @@ def test_autotuned_kernel_gives_the_same_solution(small_batch):
     a = L.lcp_setup(L.config_for(inst, L.LCP_MIXED), inst.centers, inst.axes)
     b = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, autotune=1), inst.centers, inst.axes)
     try:
-        assert L.lcp_kernel_variant(a) == "sym_a4"
+        assert L.lcp_kernel_variant(a) == "t2c8"    # few units per CTA: the plain kernel
         assert L.lcp_kernel_variant(b) in VARIANTS
         xa, _, _ = L.lcp_solve(a, L.LCP_BI_PQN, inst.tol)
         xb, _, _ = L.lcp_solve(b, L.LCP_BI_PQN, inst.tol)
