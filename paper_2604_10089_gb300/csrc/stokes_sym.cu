@@ -97,7 +97,7 @@ __device__ __forceinline__ void sym_pair(const float2 (&e)[3], const float2 (&nf
 // finish.  Afterwards lane l holds the warp total of value l / (32 / NV).
 template <int NV>
 __device__ __forceinline__ float warp_transpose_sum(const float (&v)[NV], int lane) {
-  constexpr int LOG2NV = NV == 16 ? 4 : 3;
+  constexpr int LOG2NV = NV == 32 ? 5 : (NV == 16 ? 4 : 3);
   float a[NV];
 #pragma unroll
   for (int i = 0; i < NV; i++) a[i] = v[i];
@@ -131,7 +131,7 @@ __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUn
                                                 const float* __restrict__ tmpl32, const float* __restrict__ c32,
                                                 const float* __restrict__ phi32, double* __restrict__ partial,
                                                 float* __restrict__ rev) {
-  constexpr int NV = BATCH == 4 ? 16 : 8;
+  constexpr int NV = BATCH == 8 ? 32 : (BATCH == 4 ? 16 : 8);
   constexpr int LPV = 32 / NV;   // lanes holding each reduced value
   extern __shared__ float4 smem4[];
   // AOS: s_t [ns_pad][3] float4 = (nx,nx,ny,ny) (nz,nz,wx,wx) (wy,wy,wz,wz);
@@ -332,9 +332,13 @@ __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUn
            const float* __restrict__ phi32, double* __restrict__ partial, float* __restrict__ rev) {               \
     pair32_sym_body<AOS, BATCH, MINB, PIPE>(N, ns, ns_pad, su, tmpl32, c32, phi32, partial, rev);                 \
   }
-// Measured at 216 spheres x 242 nodes (ms per launch): sym_a4 1.69, sym_a2
-// 1.75, sym 1.86, pipelined variants 1.84-1.96; the plain kernel 1.97.
+// Measured at 216 spheres x 242 nodes (ms per launch): sym_a4 1.69, sym_a4m4
+// 1.67, sym_a8m2 1.70, sym_a2 1.75, sym 1.86, pipelined variants 1.84-1.96;
+// the plain kernel 1.97.  At 64 spheres x 162 nodes: sym_a4 0.100, sym_a8m2
+// 0.103, sym_a4m4 0.114 (plain 0.100).
 PAIR32_SYM_VARIANT(k_pair32_sym_a4, true, 4, 3, false)
+PAIR32_SYM_VARIANT(k_pair32_sym_a4m4, true, 4, 4, false)
+PAIR32_SYM_VARIANT(k_pair32_sym_a8m2, true, 8, 2, false)
 PAIR32_SYM_VARIANT(k_pair32_sym_a2, true, 2, 4, false)
 PAIR32_SYM_VARIANT(k_pair32_sym, false, 2, 4, false)
 
@@ -342,10 +346,13 @@ typedef void (*Pair32SymKernel)(int, int, int, SymUnits, const float*, const flo
 struct Pair32SymVariant {
   Pair32SymKernel kernel;
   bool aos;
+  int batch;   // sources per warp reduction: node padding is a multiple of max(4, batch)
   const char* name;
 };
 static const Pair32SymVariant kSymVariants[] = {
-    {k_pair32_sym_a4, true, "sym_a4"}, {k_pair32_sym_a2, true, "sym_a2"}, {k_pair32_sym, false, "sym"}};
+    {k_pair32_sym_a4, true, 4, "sym_a4"},     {k_pair32_sym_a4m4, true, 4, "sym_a4m4"},
+    {k_pair32_sym_a8m2, true, 8, "sym_a8m2"}, {k_pair32_sym_a2, true, 2, "sym_a2"},
+    {k_pair32_sym, false, 2, "sym"}};
 constexpr int kNumSymVariants = sizeof(kSymVariants) / sizeof(kSymVariants[0]);
 
 // out_p = forward partials + reverse rows of the target blocks before body(p)
@@ -387,8 +394,14 @@ __global__ void k_finish_sym(int N, int ns, int splits, const double* __restrict
 }
 
 // ------------------------------------------------------------------ host side
-static size_t sym_smem(int ns, bool aos) {
-  const int ns_pad = (ns + 3) & ~3;
+static int sym_ns_pad(int ns, int v) {
+  const int a = kSymVariants[v].batch > 4 ? kSymVariants[v].batch : 4;
+  return (ns + a - 1) / a * a;
+}
+
+static size_t sym_smem(int ns, int v) {
+  const int ns_pad = sym_ns_pad(ns, v);
+  const bool aos = kSymVariants[v].aos;
   return sizeof(float2) * ((size_t)6 * ns_pad + (aos ? 4 : 3) * SYM_CHUNK * ns_pad) +
          sizeof(float) * SYM_WARPS * 3 * ns_pad + sizeof(double) * SYM_TPT * 3 * SYM_THREADS;
 }
@@ -421,7 +434,7 @@ int stokes_sym_configure(lcp_ctx* ctx) {
   ctx->sym_units = U;
   ctx->sym_slots = 1;
   for (int v = 0; v < kNumSymVariants && v < 8; v++) {
-    const size_t smem = sym_smem(ns, kSymVariants[v].aos);
+    const size_t smem = sym_smem(ns, v);
     if (smem > 48 * 1024)
       LCP_CUDA(cudaFuncSetAttribute(kSymVariants[v].kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
@@ -472,8 +485,8 @@ size_t stokes_sym_bytes(int M, int ns) {
 // already holds phi in FP32.
 int stokes_sym_apply(lcp_ctx* ctx, double* out) {
   const int N = ctx->N, ns = ctx->ns;
-  const int ns_pad = (ns + 3) & ~3;
   const int v = ctx->sym_v;
+  const int ns_pad = sym_ns_pad(ns, v);
   if (!stokes_sym_variant_usable(ctx, v)) {
     ctx->err = "internal: symmetric pair-sum variant not usable for this size";
     return LCP_ERR_INVALID_ARG;
@@ -482,7 +495,7 @@ int stokes_sym_apply(lcp_ctx* ctx, double* out) {
   LCP_CUDA(cudaMemsetAsync(ctx->partial, 0, sizeof(double) * 3 * (size_t)N * slots, ctx->stream));
   SymUnits su{ctx->sym_units, G, ctx->sym_ntb, ns, ctx->sym_off, ctx->sym_roff};
   cudaEvent_t e0 = prof_begin(ctx);
-  ++ctx->nlaunch, kSymVariants[v].kernel<<<G, SYM_THREADS, sym_smem(ns, kSymVariants[v].aos), ctx->stream>>>(
+  ++ctx->nlaunch, kSymVariants[v].kernel<<<G, SYM_THREADS, sym_smem(ns, v), ctx->stream>>>(
                       N, ns, ns_pad, su, ctx->tmpl32, ctx->centers32, ctx->phi32, ctx->partial, ctx->sym_rev);
   prof_end(ctx, e0, 0);
   ++ctx->nlaunch, k_finish_sym<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(

@@ -22,7 +22,7 @@ def small_batch():
     return insts
 
 
-VARIANTS = ("sym_a4", "sym_a2", "sym", "t2c8", "t1c8", "t2c16", "t2c4", "t1c16")
+VARIANTS = ("sym_a4", "sym_a4m4", "sym_a8m2", "sym_a2", "sym", "t2c8", "t1c8", "t2c16", "t2c4", "t1c16")
 
 
 def make_ctxs(insts, **kw):
