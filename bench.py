@@ -43,8 +43,18 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 # the U_nc slip solve plus the high-fidelity MVPs of Bi-PQN measured on this
 # workload (11 on the first configuration).
 REFERENCE_SOLVES_PER_LCP = 12.0
-# DRAM traffic of one k_pair32 launch from an ncu capture (null once the kernel changes).
-PAIR32_TRAFFIC = {"source_sha1": "298b391165dc32f4d22c484bf6d970a4f86ee95e", "bytes_per_launch": 665088}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# FP32 pair kernel at 216 spheres x 242 nodes, from an ncu capture, with the SHA-1 of
+# the device code it was taken on (reported as null once that code changes).
+PAIR32_TRAFFIC = {
+    "k_pair32_sym_a4": {"file": "stokes_sym.cu", "source_sha1": "", "bytes_per_launch": 0},
+    "k_pair32": {"file": "stokes.cu", "source_sha1": "298b391165dc32f4d22c484bf6d970a4f86ee95e",
+                 "bytes_per_launch": 665088},
+}
+# FP32 operations of the symmetric kernel per unordered node pair (both ordered
+# terms): r 3, |r|^2 6, |r|^-2 1, d 3, r.d 5, t 3, r.wn_q 5, r.wn_p 5, scales 2,
+# two accumulations 12 = 45 flops (FMA = 2), i.e. 22.5 per ordered pair.
+SYM_FLOPS_PER_ORDERED_PAIR = 22.5
 
 
 def parse():
@@ -124,14 +134,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def source_sha1():
-    """SHA-1 of the FP32 pair kernel's source text (pair2 .. the variant table)."""
+def source_sha1(kernel: str) -> str:
+    """SHA-1 of the device code a traffic figure was taken on."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2604_10089_gb300", "csrc", "stokes.cu"), "rb") as f:
+    info = PAIR32_TRAFFIC[kernel]
+    with open(os.path.join(ROOT, "paper_2604_10089_gb300", "csrc", info["file"]), "rb") as f:
         text = f.read()
-    a = text.find(b"__device__ __forceinline__ void pair2(")
-    b = text.find(b"constexpr int kNumPair32Variants")
+    if info["file"] == "stokes.cu":   # pair2 .. the plain variant table
+        a = text.find(b"__device__ __forceinline__ void pair2(")
+        b = text.find(b"constexpr int kNumPair32Variants")
+    else:                              # everything before the host code
+        a, b = 0, text.find(b"// ------------------------------------------------------------------ host side")
     return hashlib.sha1(text[a:b] if 0 <= a < b else text).hexdigest()
+
+
+def pair32_kernel_name(variant: str) -> str:
+    return "k_pair32" if variant == "t2c8" else "k_pair32_" + variant
 
 
 def rank_seeds(rank: int, count: int) -> list:
@@ -174,6 +192,7 @@ def run_ours(args, rank, world, local):
         axs = [torch.tensor(i.axes, dtype=torch.float64, device=dev) for i in insts]
     stream.synchronize()
     ctx = L.lcp_setup(cfg, insts[0].centers, insts[0].axes)
+    variant = L.lcp_kernel_variant(ctx)
     M, N, _ = L.lcp_sizes(ctx)
     xbuf = torch.empty(M * (M - 1) // 2, dtype=torch.float64, device=dev)
     stats = []
@@ -287,12 +306,23 @@ def run_ours(args, rank, world, local):
     roof = None
     if avg32:
         ach = pairs * FLOPS_PER_PAIR / avg32 / 1e12
-        traffic = PAIR32_TRAFFIC["bytes_per_launch"] if PAIR32_TRAFFIC["source_sha1"] == source_sha1() else None
-        roof = {"kernel": "k_pair32", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+        kname = pair32_kernel_name(variant)
+        info = PAIR32_TRAFFIC.get(kname)
+        traffic = info["bytes_per_launch"] if info and info["bytes_per_launch"] and \
+            info["source_sha1"] == source_sha1(kname) else None
+        roof = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "launches": c32, "avg_launch_ms": avg32 * 1e3, "pairs_per_launch": pairs,
                 "flops_per_pair": FLOPS_PER_PAIR, "share_of_timed_region": t32 / 1e3 / t_total,
+                "flops_note": "algorithmic work of the operator: 32 flops per ordered node pair, N(N-1) pairs",
                 "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (nominal max clock)"}
+        if variant.startswith("sym"):
+            hw = pairs * SYM_FLOPS_PER_ORDERED_PAIR / avg32 / 1e12
+            roof["kernel_flops_per_pair"] = SYM_FLOPS_PER_ORDERED_PAIR
+            roof["executed_tflops"] = hw
+            roof["executed_frac"] = hw / FP32_PEAK_TFLOPS
+            roof["symmetric_note"] = ("one evaluation serves both ordered terms of a node pair; "
+                                      "executed_frac counts the FP32 operations the kernel performs")
     k64 = None
     if c64:
         a64 = pairs * FLOPS_PER_PAIR / (t64 / c64 / 1e3) / 1e12
