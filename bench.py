@@ -47,7 +47,8 @@ REFERENCE_SOLVES_PER_LCP = 12.0
 # FP32 pair kernel at 216 spheres x 242 nodes, from an ncu capture, with the SHA-1 of
 # the device code it was taken on (reported as null once that code changes).
 PAIR32_TRAFFIC = {
-    "k_pair32_sym_a4": {"file": "stokes_sym.cu", "source_sha1": "", "bytes_per_launch": 0},
+    "k_pair32_sym_a4": {"file": "stokes_sym.cu", "source_sha1": "9a438f5e284e4528cefbebfa614c0f5030181076",
+                        "bytes_per_launch": 691968},
     "k_pair32": {"file": "stokes.cu", "source_sha1": "298b391165dc32f4d22c484bf6d970a4f86ee95e",
                  "bytes_per_launch": 665088},
 }
@@ -66,6 +67,8 @@ def parse():
     p.add_argument("--workload", default="spheres216_grid11x22")
     p.add_argument("--method", default="bi", choices=["bi", "mono"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--lowfi", default="rpy",
+                   help="Bi-PQN low-fidelity operator: rpy, or a coarse boundary-integral grid NTxNP (e.g. 6x12)")
     p.add_argument("--fp64-compare", type=int, default=1)
     p.add_argument("--cpu-baseline", type=int, default=1)
     p.add_argument("--compare-methods", type=int, default=1,
@@ -148,6 +151,14 @@ def source_sha1(kernel: str) -> str:
     return hashlib.sha1(text[a:b] if 0 <= a < b else text).hexdigest()
 
 
+def lowfi_overrides(spec: str) -> dict:
+    """Config fields of the low-fidelity operator: {} for RPY, else the coarse grid."""
+    if spec == "rpy":
+        return {}
+    nt, nph = (int(v) for v in spec.lower().split("x"))
+    return {"lowfi_n_theta": nt, "lowfi_n_phi": nph}
+
+
 def pair32_kernel_name(variant: str) -> str:
     return "k_pair32" if variant == "t2c8" else "k_pair32_" + variant
 
@@ -185,7 +196,8 @@ def run_ours(args, rank, world, local):
     insts = [make_instance(args.workload, k) for k in rank_seeds(rank, n_inst)]
     prec = L.LCP_MIXED if args.precision == "mixed" else L.LCP_FP64
     method = L.LCP_BI_PQN if args.method == "bi" else L.LCP_MONO_PQN
-    cfg = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream)
+    lowfi = lowfi_overrides(args.lowfi)
+    cfg = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream, **lowfi)
     tol = insts[0].tol
     with torch.cuda.stream(stream):
         cen = [torch.tensor(i.centers, dtype=torch.float64, device=dev) for i in insts]
@@ -272,13 +284,19 @@ def run_ours(args, rank, world, local):
     if args.compare_methods and rank == 0:
         comparison = {}
         inst = insts[args.warmup]
-        for name, meth in (("bb_pgd", L.LCP_BB_PGD), ("mono_pqn", L.LCP_MONO_PQN), ("bi_pqn", L.LCP_BI_PQN)):
-            L.lcp_update(ctx, inst.centers, inst.axes)
+        runs = [("bb_pgd", L.LCP_BB_PGD, ctx), ("mono_pqn", L.LCP_MONO_PQN, ctx), ("bi_pqn", L.LCP_BI_PQN, ctx)]
+        # Bi-PQN with the other low-fidelity operator (RPY vs the coarse 6 x 12 grid)
+        other = {} if lowfi else lowfi_overrides("6x12")
+        ctx_o = L.lcp_setup(L.config_for(inst, prec, cuda_stream=stream.cuda_stream, **other), inst.centers, inst.axes)
+        runs.append(("bi_pqn_" + ("rpy" if lowfi else "lowfi_6x12"), L.LCP_BI_PQN, ctx_o))
+        for name, meth, c in runs:
+            L.lcp_update(c, inst.centers, inst.axes)
             ts = time.perf_counter()
-            _, st, status = L.lcp_solve(ctx, meth, tol, allow_not_converged=True)
+            _, st, status = L.lcp_solve(c, meth, tol, allow_not_converged=True)
             comparison[name] = {"hi_mvps": st["hi_mvps"], "lo_mvps": st["lo_mvps"], "e_mvps": round(st["e_mvps"], 3),
                                 "iterations": st["iterations"], "seconds": time.perf_counter() - ts,
                                 "converged": st["converged"] == 1}
+        L.lcp_destroy(ctx_o)
     traj = None
     if args.trajectory and rank == 0:
         inst = insts[args.warmup]
@@ -597,6 +615,8 @@ def main():
             "config": {"workload": f"{args.workload}: {r['M']} Janus spheres, {r['N']} surface nodes, "
                                    f"{3 * r['N']} unknowns",
                        "method": f"{args.method}_pqn", "precision": args.precision, "tol": 1e-8,
+                       "low_fidelity": "rpy" if args.lowfi == "rpy" else f"boundary integral, {args.lowfi} grid, "
+                                                                        "FP32 GMRES to 1e-6",
                        "gmres_tol": 1e-12, "step": "contacts + U_nc slip solve + b + LCP solve",
                        "l2": "inputs larger than L2 (Krylov basis 76 MB + operator sweeps per apply)",
                        "parallelism": f"instances x{world}"},

@@ -58,6 +58,7 @@ enum { LCP_DF64 = 2 };                          /* double-FP32 sums (refinement 
 enum { LCP_MONO_PQN = 0, LCP_BI_PQN = 1 };     /* Algorithm 1 / Algorithm 4 */
 enum { LCP_BB_PGD = 2 };                        /* baseline of Sec. 6: PGD with the Barzilai-Borwein step */
 enum { LCP_HIGH = 0, LCP_LOW_RPY = 1 };        /* mobility fidelity */
+enum { LCP_LOW_BIE = 2 };                       /* the boundary-integral mobility on the coarse low-fidelity grid */
 
 typedef struct {
   int n_theta, n_phi;       /* node grid per sphere; n_phi must be even */
@@ -84,6 +85,13 @@ typedef struct {
   int h0_scaling;           /* 0: B_0 = H_0 = I as printed in Algorithm 1; 1: B_0 = delta I with
                                delta = y^T s / s^T s of the first step (H_0 = I / delta) */
   void* cuda_stream;        /* cudaStream_t to run on; NULL = the legacy default stream */
+  /* Low-fidelity operator of Bi-PQN (Sec. 5.1: fidelity by coarseness of the
+   * discretisation).  lowfi_n_theta = 0: the pairwise RPY mobility.  > 0: the
+   * same boundary-integral mobility on a coarser lowfi_n_theta x lowfi_n_phi
+   * grid, its GMRES solved with FP32 sums (no refinement) to relative residual
+   * lowfi_tol (the paper's low-fidelity eps_gmres). */
+  int lowfi_n_theta, lowfi_n_phi;
+  double lowfi_tol;
 } lcp_config;
 
 typedef struct {
@@ -223,13 +231,16 @@ LCP_API int lcp_get_unc(lcp_ctx* ctx, double* U_nc);
 
 /* U = M F (Sec. 2, Eq. mobility).  FT, UO: host [M*6].  include_slip adds the
  * Janus slip-driven part (U_nc for FT = 0).  fidelity: LCP_HIGH (boundary
- * integral, GMRES, precision of the context) or LCP_LOW_RPY (pairwise RPY). */
+ * integral, GMRES, precision of the context), LCP_LOW_RPY (pairwise RPY) or
+ * LCP_LOW_BIE (boundary integral on the coarse grid; LCP_ERR_INVALID_ARG when
+ * cfg.lowfi_n_theta = 0).  Only LCP_HIGH has the slip term. */
 LCP_API int mobility_apply(lcp_ctx* ctx, const double* FT, double* UO, int include_slip, int fidelity);
 /* Same on device pointers FT [M*6], UO [M*6], on the context's stream. */
 LCP_API int mobility_apply_dev(lcp_ctx* ctx, const double* FT, double* UO, int include_slip, int fidelity);
 
 /* One matrix-vector product A[x] = D^T M D x (Sec. 3, Eq. defAandb) of the
- * given fidelity.  Host x [n], Ax [n]. */
+ * given fidelity (LCP_HIGH, LCP_LOW_RPY or LCP_LOW_BIE).  Host x [n], Ax [n].
+ * Bi-PQN uses LCP_LOW_BIE when cfg.lowfi_n_theta > 0, else LCP_LOW_RPY. */
 LCP_API int lcp_apply_A(lcp_ctx* ctx, const double* x, double* Ax, int fidelity);
 
 /* Solves 0 <= x perp A x + b >= 0 by Mono-PQN (Algorithm 1), Bi-PQN

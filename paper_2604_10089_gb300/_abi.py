@@ -17,7 +17,7 @@ LCP_ERR_TIMEOUT = -6
 LCP_ERR_REJECTED = -8
 LCP_FP64, LCP_MIXED, LCP_DF64 = 0, 1, 2
 LCP_MONO_PQN, LCP_BI_PQN, LCP_BB_PGD = 0, 1, 2
-LCP_HIGH, LCP_LOW_RPY = 0, 1
+LCP_HIGH, LCP_LOW_RPY, LCP_LOW_BIE = 0, 1, 2
 
 STATUS_NAMES = {0: "LCP_OK", -1: "LCP_ERR_INVALID_ARG", -2: "LCP_ERR_OOM", -3: "LCP_ERR_CUDA",
                 -4: "LCP_ERR_NOT_CONVERGED", -5: "LCP_ERR_NUMERICAL", -6: "LCP_ERR_TIMEOUT",
@@ -34,7 +34,8 @@ class lcp_config(ctypes.Structure):
                 ("memory", ctypes.c_int), ("ssn_maxit", ctypes.c_int), ("forcing", ctypes.c_double),
                 ("precondition", ctypes.c_int), ("residual_precision", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("own_stream", ctypes.c_int), ("h0_scaling", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("lowfi_n_theta", ctypes.c_int),
+                ("lowfi_n_phi", ctypes.c_int), ("lowfi_tol", ctypes.c_double)]
 
 
 class lcp_contact(ctypes.Structure):

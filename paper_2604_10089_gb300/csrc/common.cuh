@@ -164,6 +164,10 @@ struct lcp_ctx {
   std::vector<int> ev_kind;
   std::string err;
   unsigned long long nlaunch = 0;   // kernels launched by this context
+  // low-fidelity coarse-grid context (Bi-PQN, cfg.lowfi_n_theta > 0): same
+  // bodies and stream, no contacts; its mobility solves run FP32 GMRES only
+  lcp_ctx* lo = nullptr;
+  bool fp32_only = false;
   // counters of the current solve
   int c_gmres = 0, c_fp64 = 0, c_fp32 = 0, c_df64 = 0;
 };
@@ -217,7 +221,9 @@ int scatter_D(lcp_ctx* ctx, const double* x, double* FT);
 int gather_Dt(lcp_ctx* ctx, const double* UO, double* out, const double* add);
 int rpy_apply(lcp_ctx* ctx, const double* FT, double* UO);
 int mvp_high(lcp_ctx* ctx, const double* x, double* Ax);
-int mvp_low(lcp_ctx* ctx, const double* x, double* Ax);
+int mvp_low(lcp_ctx* ctx, const double* x, double* Ax);       // the configured low fidelity
+int mvp_rpy(lcp_ctx* ctx, const double* x, double* Ax);       // D^T M_RPY D x
+int mvp_lowbie(lcp_ctx* ctx, const double* x, double* Ax);    // D^T M_coarse D x
 size_t pqn_bytes(int n, int rmax);
 char* pqn_carve(PqnDev* pq, char* base, int n, int rmax);
 int pqn_reset(lcp_ctx* ctx, PqnDev* pq);

@@ -367,6 +367,15 @@ int density_solve(lcp_ctx* ctx, const double* rhs, double* phi) {
     }
     return LCP_OK;
   }
+  if (ctx->fp32_only) {   // low-fidelity grid: FP32-operator GMRES to the tolerance, no refinement
+    LCP_TRY(gmres(ctx, rhs, phi, 1, tol, LCP_MIXED, ctx->cfg.gmres_maxit, &its, &res));
+    ctx->c_gmres += its;
+    if (res > tol) {
+      ctx->err = "GMRES did not reach its tolerance";
+      return LCP_ERR_NOT_CONVERGED;
+    }
+    return LCP_OK;
+  }
   // mixed precision: phi = 0, r = rhs
   LCP_CUDA(cudaMemcpyAsync(ctx->res, rhs, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
   double rn = bn;
@@ -426,8 +435,24 @@ int mvp_high(lcp_ctx* ctx, const double* x, double* Ax) {
   return gather_Dt(ctx, ctx->UO, Ax, nullptr);
 }
 
-int mvp_low(lcp_ctx* ctx, const double* x, double* Ax) {
+int mvp_rpy(lcp_ctx* ctx, const double* x, double* Ax) {
   LCP_TRY(scatter_D(ctx, x, ctx->FT));
   LCP_TRY(rpy_apply(ctx, ctx->FT, ctx->UO));
   return gather_Dt(ctx, ctx->UO, Ax, nullptr);
+}
+
+// Low-fidelity MVP through the coarse-grid context: the same D and D^T, the
+// boundary-integral mobility of the coarse grid (Sec. 5.1, coarseness of the
+// discretisation as fidelity).
+int mvp_lowbie(lcp_ctx* ctx, const double* x, double* Ax) {
+  lcp_ctx* lo = ctx->lo;
+  if (!lo) { ctx->err = "no low-fidelity grid configured (lowfi_n_theta = 0)"; return LCP_ERR_INVALID_ARG; }
+  LCP_TRY(scatter_D(ctx, x, ctx->FT));
+  const int st = mobility_solve(lo, ctx->FT, 0, lo->UO);
+  if (st != LCP_OK) { ctx->err = "low-fidelity grid: " + lo->err; return st; }
+  return gather_Dt(ctx, lo->UO, Ax, nullptr);
+}
+
+int mvp_low(lcp_ctx* ctx, const double* x, double* Ax) {
+  return ctx->lo ? mvp_lowbie(ctx, x, Ax) : mvp_rpy(ctx, x, Ax);
 }

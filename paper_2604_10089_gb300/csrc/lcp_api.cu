@@ -50,6 +50,9 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->kmax = 100;
   c->kmax_inner = 100;
   c->memory = 32;
+  c->lowfi_n_theta = 0;
+  c->lowfi_n_phi = 0;
+  c->lowfi_tol = 1e-6;
   c->ssn_maxit = 50;
   c->forcing = 1e-3;
   c->precondition = 1;
@@ -72,6 +75,12 @@ static int validate(const lcp_config* c, int M, const double* centers, std::stri
   if (c->precision != LCP_FP64 && c->precision != LCP_MIXED) { *err = "precision must be LCP_FP64 or LCP_MIXED"; return LCP_ERR_INVALID_ARG; }
   if (c->residual_precision != LCP_FP64 && c->residual_precision != LCP_DF64) { *err = "residual_precision must be LCP_FP64 or LCP_DF64"; return LCP_ERR_INVALID_ARG; }
   if (c->gmres_restart < 1 || c->gmres_restart > 200 || c->gmres_maxit < 1) { *err = "gmres_restart in [1, 200], gmres_maxit >= 1"; return LCP_ERR_INVALID_ARG; }
+  if (c->lowfi_n_theta != 0 && (c->lowfi_n_theta < 2 || c->lowfi_n_phi < 4 || (c->lowfi_n_phi & 1) ||
+                                 (size_t)c->lowfi_n_theta * c->lowfi_n_phi > 512 || !(c->lowfi_tol > 0.0) ||
+                                 c->lowfi_tol > 0.1)) {
+    *err = "low-fidelity grid: lowfi_n_theta >= 2, even lowfi_n_phi >= 4, at most 512 nodes, lowfi_tol in (0, 0.1]";
+    return LCP_ERR_INVALID_ARG;
+  }
   // the direction kernel keeps its r x r systems in shared memory (<= 227 KB: r <= 48)
   if (c->memory < 1 || c->memory > 48) { *err = "memory in [1, 48]"; return LCP_ERR_INVALID_ARG; }
   if (c->kmax < 1 || c->kmax > 120 || c->kmax_inner < 1) { *err = "kmax in [1, 120], kmax_inner >= 1"; return LCP_ERR_INVALID_ARG; }
@@ -79,6 +88,35 @@ static int validate(const lcp_config* c, int M, const double* centers, std::stri
   for (int i = 0; i < 3 * M; i++)
     if (!std::isfinite(centers[i])) { *err = "non-finite centre coordinate"; return LCP_ERR_INVALID_ARG; }
   return LCP_OK;
+}
+
+static int alloc_static(lcp_ctx* ctx);
+
+// The coarse-grid context of the low-fidelity operator: same bodies and
+// stream, grid lowfi_n_theta x lowfi_n_phi, FP32-operator GMRES to lowfi_tol,
+// no contacts or quasi-Newton state of its own.  Owned by ctx.
+static int lowfi_create(lcp_ctx* ctx) {
+  lcp_ctx* lo = new (std::nothrow) lcp_ctx();
+  if (!lo) { ctx->err = "host allocation failed"; return LCP_ERR_OOM; }
+  lo->cfg = ctx->cfg;
+  lo->cfg.n_theta = ctx->cfg.lowfi_n_theta;
+  lo->cfg.n_phi = ctx->cfg.lowfi_n_phi;
+  lo->cfg.precision = LCP_MIXED;
+  lo->cfg.gmres_tol = ctx->cfg.lowfi_tol;
+  lo->cfg.memory = 1;
+  lo->cfg.own_stream = 0;
+  lo->cfg.lowfi_n_theta = 0;
+  lo->cfg.lowfi_n_phi = 0;
+  lo->stream = ctx->stream;
+  lo->device = ctx->device;
+  lo->M = ctx->M;
+  lo->ns = lo->cfg.n_theta * lo->cfg.n_phi;
+  lo->N = lo->M * lo->ns;
+  lo->fp32_only = true;
+  ctx->lo = lo;
+  const int st = alloc_static(lo);
+  if (st != LCP_OK) ctx->err = "low-fidelity grid: " + lo->err;
+  return st;
 }
 
 // Buffers whose size depends only on M and the grid (once per context).
@@ -127,6 +165,7 @@ static int alloc_static(lcp_ctx* ctx) {
   LCP_TRY(pqn_configure(ctx, ctx->cfg.memory));
   if (ctx->cfg.precondition) LCP_TRY(precond_build(ctx));
   if (ctx->cfg.autotune) LCP_TRY(stokes_autotune(ctx));
+  if (ctx->cfg.lowfi_n_theta > 0) LCP_TRY(lowfi_create(ctx));
   return LCP_OK;
 }
 
@@ -184,6 +223,13 @@ static int configure(lcp_ctx* ctx, const double* centers, const double* axes, in
   ctx->has_axes = axes != nullptr;
   if (axes) LCP_CUDA(cudaMemcpyAsync(ctx->axes, axes, sizeof(double) * 3 * M, kind, ctx->stream));
   LCP_TRY(geometry_update(ctx));
+  if (ctx->lo) {
+    LCP_CUDA(cudaMemcpyAsync(ctx->lo->centers, ctx->centers, sizeof(double) * 3 * M, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    ctx->lo->has_axes = false;
+    const int st = geometry_update(ctx->lo);
+    if (st != LCP_OK) { ctx->err = "low-fidelity grid: " + ctx->lo->err; return st; }
+  }
   if (contacts) {
     LCP_TRY(contacts_upload(ctx, n_contacts, contacts));
     ctx->n = n_contacts;
@@ -316,12 +362,22 @@ extern "C" int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n
   b += sizeof(double) * n * (6 + 2 * K) + sizeof(int) * (2 * n + 1);                         // arena
   b += 2 * sizeof(double) * (n * (8 + 6 * R) + 3 * R * R + 64);                              // PQN states
   *bytes = b + (b >> 4);                                                                     // 1/16 slack
+  if (cfg->lowfi_n_theta > 0) {   // the coarse-grid context
+    lcp_config lc = *cfg;
+    lc.n_theta = cfg->lowfi_n_theta;
+    lc.n_phi = cfg->lowfi_n_phi;
+    lc.memory = 1;
+    lc.lowfi_n_theta = 0;
+    size_t lb = 0;
+    lcp_footprint_estimate(&lc, n_bodies, 0, &lb);
+    *bytes += lb;
+  }
   return LCP_OK;
 }
 
 extern "C" int lcp_footprint(const lcp_ctx* ctx, size_t* bytes) {
   if (!ctx || !bytes) return LCP_ERR_INVALID_ARG;
-  *bytes = ctx->bytes;
+  *bytes = ctx->bytes + (ctx->lo ? ctx->lo->bytes : 0);
   return LCP_OK;
 }
 
@@ -392,6 +448,7 @@ extern "C" int lcp_setup(const lcp_config* cfg, int n_bodies, const double* cent
 
 extern "C" void lcp_destroy(lcp_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->lo) lcp_destroy(ctx->lo);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   for (void* p : ctx->allocs) cudaFree(p);
@@ -459,6 +516,12 @@ static int mobility_impl(lcp_ctx* ctx, const double* FT, double* UO, int include
   } else if (fidelity == LCP_LOW_RPY) {
     if (include_slip) { ctx->err = "the RPY operator has no slip term"; return LCP_ERR_INVALID_ARG; }
     return rpy_apply(ctx, FT, UO);
+  } else if (fidelity == LCP_LOW_BIE) {
+    if (include_slip) { ctx->err = "the low-fidelity grid has no slip term"; return LCP_ERR_INVALID_ARG; }
+    if (!ctx->lo) { ctx->err = "no low-fidelity grid configured (lowfi_n_theta = 0)"; return LCP_ERR_INVALID_ARG; }
+    const int st = mobility_solve(ctx->lo, FT, 0, UO);
+    if (st != LCP_OK) ctx->err = "low-fidelity grid: " + ctx->lo->err;
+    return st;
   }
   ctx->err = "unknown fidelity";
   return LCP_ERR_INVALID_ARG;
@@ -487,7 +550,9 @@ extern "C" int lcp_apply_A(lcp_ctx* ctx, const double* x, double* Ax, int fideli
   if (fidelity == LCP_HIGH) {
     LCP_TRY(mvp_high(ctx, ctx->tmp_n2, ctx->tmp_n3));
   } else if (fidelity == LCP_LOW_RPY) {
-    LCP_TRY(mvp_low(ctx, ctx->tmp_n2, ctx->tmp_n3));
+    LCP_TRY(mvp_rpy(ctx, ctx->tmp_n2, ctx->tmp_n3));
+  } else if (fidelity == LCP_LOW_BIE) {
+    LCP_TRY(mvp_lowbie(ctx, ctx->tmp_n2, ctx->tmp_n3));
   } else {
     ctx->err = "unknown fidelity";
     return LCP_ERR_INVALID_ARG;
