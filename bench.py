@@ -39,10 +39,12 @@ FLOPS_PER_PAIR = 32
 # (FMA) x 2.070 GHz maximum SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
-# Mobility solves per LCP solve used to scale the reference arm's per-apply sample:
-# the U_nc slip solve plus the high-fidelity MVPs of Bi-PQN measured on this
-# workload (11 on the first configuration).
-REFERENCE_SOLVES_PER_LCP = 12.0
+# Mobility solves per LCP solve used to scale the reference arm's per-apply sample,
+# in fine-grid units, for the bench's default configuration: the U_nc slip solve,
+# the 3 high-fidelity MVPs of Bi-PQN with the 8 x 16 low-fidelity grid, and its 27
+# low-fidelity solves at (128/242)^2 x 15/40 of a fine solve each (measured on this
+# workload).
+REFERENCE_SOLVES_PER_LCP = 6.8
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # FP32 pair kernel at 216 spheres x 242 nodes, from an ncu capture, with the SHA-1 of
 # the device code it was taken on (reported as null once that code changes).
@@ -67,8 +69,9 @@ def parse():
     p.add_argument("--workload", default="spheres216_grid11x22")
     p.add_argument("--method", default="bi", choices=["bi", "mono"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    p.add_argument("--lowfi", default="rpy",
-                   help="Bi-PQN low-fidelity operator: rpy, or a coarse boundary-integral grid NTxNP (e.g. 6x12)")
+    p.add_argument("--lowfi", default="auto",
+                   help="Bi-PQN low-fidelity operator: rpy, a coarse boundary-integral grid NTxNP (e.g. 8x16), "
+                        "or auto = (n_theta - 3) x 2(n_theta - 3) of the workload's grid")
     p.add_argument("--fp64-compare", type=int, default=1)
     p.add_argument("--cpu-baseline", type=int, default=1)
     p.add_argument("--compare-methods", type=int, default=1,
@@ -151,10 +154,13 @@ def source_sha1(kernel: str) -> str:
     return hashlib.sha1(text[a:b] if 0 <= a < b else text).hexdigest()
 
 
-def lowfi_overrides(spec: str) -> dict:
+def lowfi_overrides(spec: str, n_theta: int = 0) -> dict:
     """Config fields of the low-fidelity operator: {} for RPY, else the coarse grid."""
     if spec == "rpy":
         return {}
+    if spec == "auto":   # measured optimum at 64 and 216 spheres; FP32 GMRES to 1e-4 (see design notes)
+        nt = max(2, n_theta - 3)
+        return {"lowfi_n_theta": nt, "lowfi_n_phi": 2 * max(2, nt), "lowfi_tol": 1e-4}
     nt, nph = (int(v) for v in spec.lower().split("x"))
     return {"lowfi_n_theta": nt, "lowfi_n_phi": nph}
 
@@ -196,7 +202,7 @@ def run_ours(args, rank, world, local):
     insts = [make_instance(args.workload, k) for k in rank_seeds(rank, n_inst)]
     prec = L.LCP_MIXED if args.precision == "mixed" else L.LCP_FP64
     method = L.LCP_BI_PQN if args.method == "bi" else L.LCP_MONO_PQN
-    lowfi = lowfi_overrides(args.lowfi)
+    lowfi = lowfi_overrides(args.lowfi, insts[0].n_theta)
     cfg = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream, **lowfi)
     tol = insts[0].tol
     with torch.cuda.stream(stream):
@@ -286,9 +292,9 @@ def run_ours(args, rank, world, local):
         inst = insts[args.warmup]
         runs = [("bb_pgd", L.LCP_BB_PGD, ctx), ("mono_pqn", L.LCP_MONO_PQN, ctx), ("bi_pqn", L.LCP_BI_PQN, ctx)]
         # Bi-PQN with the other low-fidelity operator (RPY vs the coarse 6 x 12 grid)
-        other = {} if lowfi else lowfi_overrides("6x12")
+        other = {} if lowfi else lowfi_overrides("auto", inst.n_theta)
         ctx_o = L.lcp_setup(L.config_for(inst, prec, cuda_stream=stream.cuda_stream, **other), inst.centers, inst.axes)
-        runs.append(("bi_pqn_" + ("rpy" if lowfi else "lowfi_6x12"), L.LCP_BI_PQN, ctx_o))
+        runs.append(("bi_pqn_" + ("rpy" if lowfi else "coarse_grid"), L.LCP_BI_PQN, ctx_o))
         for name, meth, c in runs:
             L.lcp_update(c, inst.centers, inst.axes)
             ts = time.perf_counter()
@@ -361,7 +367,13 @@ def run_ours(args, rank, world, local):
         kdf = {"kernel": "k_pair_df", "launches": cdf, "avg_launch_ms": tdf / cdf,
                "fp32_ops_per_pair_note": "double-FP32 arithmetic, ~250 FP32 operations per pair",
                "pairs_per_s": pairs / (tdf / cdf / 1e3), "share_of_timed_region": tdf / 1e3 / t_total}
+    lowfi_desc = ("rpy" if not lowfi else
+                  f"boundary integral on a {lowfi['lowfi_n_theta']}x{lowfi['lowfi_n_phi']} grid, FP32 GMRES to "
+                  f"{lowfi.get('lowfi_tol', 1e-6):g}")
     return dict(t_total=t_total, lat=lat, clocks=clk, launches=launches, roof=roof, k64=k64, kdf=kdf, e2e=e2e, traj=traj,
+                lowfi=lowfi_desc,
+                lowfi_ns_ratio=(lowfi["lowfi_n_theta"] * lowfi["lowfi_n_phi"] / (insts[0].n_theta * insts[0].n_phi)
+                                if lowfi else 0.0),
                 comparison=comparison,
                 fp64=fp64, summary=summary, N=N, M=M)
 
@@ -605,7 +617,12 @@ def main():
         s = r["summary"]
         cpu = None
         if args.cpu_baseline:
+            # mobility solves per LCP solve in fine-grid units: U_nc + high-fidelity MVPs, plus the
+            # coarse-grid low-fidelity solves at their pair-count ratio (GMRES to 1e-6: ~15 of the
+            # ~40 iterations of a 1e-12 solve)
             per = 1.0 + float(np.mean(s["hi_mvps"]))
+            if r["lowfi_ns_ratio"]:
+                per += float(np.mean(s["lo_mvps"])) * r["lowfi_ns_ratio"] ** 2 * 15.0 / 40.0
             cpu = cpu_oracle_rate(args.workload, 0, per)
         line = {
             "metric": "LCP solves/s", "value": value, "unit": "LCP solves/s", "n_gpus": world,
@@ -615,8 +632,7 @@ def main():
             "config": {"workload": f"{args.workload}: {r['M']} Janus spheres, {r['N']} surface nodes, "
                                    f"{3 * r['N']} unknowns",
                        "method": f"{args.method}_pqn", "precision": args.precision, "tol": 1e-8,
-                       "low_fidelity": "rpy" if args.lowfi == "rpy" else f"boundary integral, {args.lowfi} grid, "
-                                                                        "FP32 GMRES to 1e-6",
+                       "low_fidelity": r["lowfi"],
                        "gmres_tol": 1e-12, "step": "contacts + U_nc slip solve + b + LCP solve",
                        "l2": "inputs larger than L2 (Krylov basis 76 MB + operator sweeps per apply)",
                        "parallelism": f"instances x{world}"},
