@@ -160,7 +160,7 @@ def lowfi_overrides(spec: str, n_theta: int = 0) -> dict:
         return {}
     if spec == "auto":   # measured optimum at 64 and 216 spheres; FP32 GMRES to 1e-4 (see design notes)
         nt = max(2, n_theta - 3)
-        return {"lowfi_n_theta": nt, "lowfi_n_phi": 2 * max(2, nt), "lowfi_tol": 1e-4}
+        return {"lowfi_n_theta": nt, "lowfi_n_phi": 2 * max(2, nt), "lowfi_tol": 1e-4, "init_forcing": 1e-3}
     nt, nph = (int(v) for v in spec.lower().split("x"))
     return {"lowfi_n_theta": nt, "lowfi_n_phi": nph}
 
@@ -369,7 +369,8 @@ def run_ours(args, rank, world, local):
                "pairs_per_s": pairs / (tdf / cdf / 1e3), "share_of_timed_region": tdf / 1e3 / t_total}
     lowfi_desc = ("rpy" if not lowfi else
                   f"boundary integral on a {lowfi['lowfi_n_theta']}x{lowfi['lowfi_n_phi']} grid, FP32 GMRES to "
-                  f"{lowfi.get('lowfi_tol', 1e-6):g}")
+                  f"{lowfi.get('lowfi_tol', 1e-6):g}, initialisation to {lowfi.get('init_forcing', 0.0):g} of its "
+                  f"initial KKT error")
     return dict(t_total=t_total, lat=lat, clocks=clk, launches=launches, roof=roof, k64=k64, kdf=kdf, e2e=e2e, traj=traj,
                 lowfi=lowfi_desc,
                 lowfi_ns_ratio=(lowfi["lowfi_n_theta"] * lowfi["lowfi_n_phi"] / (insts[0].n_theta * insts[0].n_phi)

@@ -92,6 +92,9 @@ typedef struct {
    * lowfi_tol (the paper's low-fidelity eps_gmres). */
   int lowfi_n_theta, lowfi_n_phi;
   double lowfi_tol;
+  /* Bi-PQN's low-fidelity initialisation (Sec. 5.2, solved "approximately"):
+   * stops at max(tol, init_forcing * its initial KKT error); 0 = to tol. */
+  double init_forcing;
 } lcp_config;
 
 typedef struct {

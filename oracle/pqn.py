@@ -206,13 +206,14 @@ class PQNResult:
 
 
 def mono_pqn(mvp, b, x0, tol=1e-8, kmax=100, d=None, pairs=(), r_max=32,
-             g0=None, extra_mvp=None, scale0=False):
+             g0=None, extra_mvp=None, scale0=False, tol_rel=0.0):
     """Algorithm 1 (Mono-PQN).
 
     mvp(v) returns A[v].  With g0 given the initial gradient is taken as is
     (no MVP).  pairs = [(s, y), ...] seeds the quasi-Newton memory.  If
     extra_mvp is given, mvp(v) returns (A[v], E[v]) and E[x - x0] is
     accumulated with the same MVP reuse as the gradient (Appendix D.2).
+    Stops at ||min(x, g)|| <= max(tol, tol_rel * ||min(x0, g0)||).
     """
     b = np.asarray(b, float)
     n = b.shape[0]
@@ -232,6 +233,8 @@ def mono_pqn(mvp, b, x0, tol=1e-8, kmax=100, d=None, pairs=(), r_max=32,
     for k in range(kmax):
         kkt = float(np.linalg.norm(np.minimum(x, g)))
         hist.append(kkt)
+        if k == 0:
+            tol = max(tol, tol_rel * kkt)
         if kkt <= tol:
             return PQNResult(x, g, k, mvps, kkt, True, model, hist, extra)
         xt = x - model.H(g)
@@ -276,18 +279,22 @@ class BiPQNResult:
 
 
 def bi_pqn(mvp_hi, mvp_lo, b, x_init, tol=1e-8, kmax=50, kmax_inner=100,
-           forcing=1e-3, r_max=32, scale0=False):
+           forcing=1e-3, r_max=32, scale0=False, init_forcing=0.0):
     """Algorithm 4 (Bi-PQN) with B^(0) = A_hat.
 
     The subproblem min_{z>=0} 1/2 z^T B z + (g - B x)^T z (Eq. pqnSubproblem)
     is solved by Algorithm 1 started at x with gradient g, using only
     low-fidelity MVPs B[v] = A_hat[v] + U_h U_h^T v - V_h V_h^T v.  Its
-    tolerance is max(0.1 tol, forcing * ||min(x, g)||).
+    tolerance is max(0.1 tol, forcing * ||min(x, g)||).  The low-fidelity
+    initialisation (Sec. 5.2, solved "approximately") stops at
+    max(tol, init_forcing * its initial KKT error); init_forcing = 0 solves it
+    to tol.
     """
     b = np.asarray(b, float)
     n = b.shape[0]
     # low-fidelity initialisation (Sec. 5.2)
-    init = mono_pqn(mvp_lo, b, x_init, tol=tol, kmax=kmax_inner, r_max=r_max, scale0=scale0)
+    init = mono_pqn(mvp_lo, b, x_init, tol=tol, kmax=kmax_inner, r_max=r_max, scale0=scale0,
+                    tol_rel=init_forcing)
     d_inner = init.model.d
     lo = init.mvps
     S_low = list(init.model.S)

@@ -35,7 +35,8 @@ class lcp_config(ctypes.Structure):
                 ("precondition", ctypes.c_int), ("residual_precision", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("own_stream", ctypes.c_int), ("h0_scaling", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("lowfi_n_theta", ctypes.c_int),
-                ("lowfi_n_phi", ctypes.c_int), ("lowfi_tol", ctypes.c_double)]
+                ("lowfi_n_phi", ctypes.c_int), ("lowfi_tol", ctypes.c_double),
+                ("init_forcing", ctypes.c_double)]
 
 
 class lcp_contact(ctypes.Structure):

@@ -53,6 +53,7 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->lowfi_n_theta = 0;
   c->lowfi_n_phi = 0;
   c->lowfi_tol = 1e-6;
+  c->init_forcing = 0.0;
   c->ssn_maxit = 50;
   c->forcing = 1e-3;
   c->precondition = 1;
@@ -81,6 +82,7 @@ static int validate(const lcp_config* c, int M, const double* centers, std::stri
     *err = "low-fidelity grid: lowfi_n_theta >= 2, even lowfi_n_phi >= 4, at most 512 nodes, lowfi_tol in (0, 0.1]";
     return LCP_ERR_INVALID_ARG;
   }
+  if (!(c->init_forcing >= 0.0) || c->init_forcing >= 1.0) { *err = "init_forcing in [0, 1)"; return LCP_ERR_INVALID_ARG; }
   // the direction kernel keeps its r x r systems in shared memory (<= 227 KB: r <= 48)
   if (c->memory < 1 || c->memory > 48) { *err = "memory in [1, 48]"; return LCP_ERR_INVALID_ARG; }
   if (c->kmax < 1 || c->kmax > 120 || c->kmax_inner < 1) { *err = "kmax in [1, 120], kmax_inner >= 1"; return LCP_ERR_INVALID_ARG; }

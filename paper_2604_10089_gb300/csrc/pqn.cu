@@ -18,6 +18,7 @@
 //
 // The n-vectors are small (one entry per contact), so each phase runs in a
 // single thread block; the MVPs in between use the whole GPU.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -1090,8 +1091,9 @@ struct RunStats {
 
 // Algorithm 1 on state pq.  mode 0: MVP = A (fidelity hi/lo via mvp), g from
 // A x + b; mode 1: Bi-PQN subproblem (MVP = B^(k), g0 given, extra tracked).
+// Algorithm 1 on pq; stops at ||min(x, g)|| <= max(tol, tol_rel * initial value).
 static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* b, const double* g0, double tol,
-                    int kmax, RunStats* rs) {
+                    int kmax, RunStats* rs, double tol_rel = 0.0) {
   const bool track = !sub && mvp == mvp_high;   // body velocities M D x for the time step
   const int m6 = 6 * ctx->M;
   PqnWork wk = work_of(ctx, pq);
@@ -1111,6 +1113,7 @@ static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* 
   }
   LCP_CUDA(cudaGetLastError());
   LCP_TRY(read_scal(ctx, pq, sc));
+  tol = std::max(tol, tol_rel * sc[S_KKT]);
   int k = 0;
   for (; k < kmax; k++) {
     if (!(sc[S_KKT] == sc[S_KKT])) { ctx->err = "PQN: NaN in the KKT error"; return LCP_ERR_NUMERICAL; }
@@ -1191,7 +1194,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
     // low-fidelity initialisation: Mono-PQN on A_hat from x0, its pairs kept in pi
     RunStats r0;
     ++ctx->nlaunch, k_pqn_init<<<1, PQN_T, 0, ctx->stream>>>(pi, x0);
-    LCP_TRY(run_mono(ctx, pi, mvp_low, 0, ctx->b, nullptr, tol, ctx->cfg.kmax_inner, &r0));
+    LCP_TRY(run_mono(ctx, pi, mvp_low, 0, ctx->b, nullptr, tol, ctx->cfg.kmax_inner, &r0, ctx->cfg.init_forcing));
     int lo = r0.mvps, hi = 0, inner_total = r0.iterations;
     double t_lo = r0.t_mvp, t_hi = 0.0;
     ctx->nh = 0;

@@ -49,12 +49,13 @@ def test_lowfi_mvp_matches_coarse_grid_oracle(grid):
         L.lcp_destroy(ctx)
 
 
+@pytest.mark.parametrize("init_forcing", [0.0, 1e-3])
 @pytest.mark.parametrize("index", [0, 1, 2])
-def test_bi_pqn_with_coarse_grid_low_fidelity(index):
+def test_bi_pqn_with_coarse_grid_low_fidelity(index, init_forcing):
     case = dense_case("spheres8_grid7x14", index)
     inst = case["inst"]
     A, b, xs = case["A"], case["b"], case["x"]
-    cfg = L.config_for(inst, L.LCP_MIXED, lowfi_n_theta=5, lowfi_n_phi=10)
+    cfg = L.config_for(inst, L.LCP_MIXED, lowfi_n_theta=5, lowfi_n_phi=10, init_forcing=init_forcing)
     ctx = L.lcp_setup(cfg, inst.centers, inst.axes)
     try:
         x, st, status = L.lcp_solve(ctx, L.LCP_BI_PQN, inst.tol)

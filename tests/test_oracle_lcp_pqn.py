@@ -189,6 +189,28 @@ def test_bi_pqn_exact_low_fidelity_needs_one_high_fidelity_mvp():
     assert bi.converged and bi.hi_mvps == 1
 
 
+def test_bi_pqn_approximate_initialisation():
+    """Sec. 5.2 solves the low-fidelity initialisation only approximately: with
+    init_forcing the init stops at a relative KKT decrease; the outer loop still
+    reaches the LCP solution, and with an exact low fidelity it needs at most the
+    gradient MVP plus two corrections (each subproblem is then the exact problem,
+    solved to the forcing tolerance)."""
+    inst, A, b, Ahat = dense_instance("spheres8_grid7x14", 1)
+    xs = pgs(A, b)
+    exact = P.bi_pqn(lambda v: A @ v, lambda v: A @ v, b, np.zeros(b.size), tol=inst.tol, init_forcing=1e-3)
+    assert exact.converged and 1 <= exact.hi_mvps <= 3
+    np.testing.assert_allclose(exact.x, xs, atol=1e-6)
+    full = P.bi_pqn(lambda v: A @ v, lambda v: Ahat @ v, b, np.zeros(b.size), tol=inst.tol)
+    approx = P.bi_pqn(lambda v: A @ v, lambda v: Ahat @ v, b, np.zeros(b.size), tol=inst.tol, init_forcing=1e-3)
+    assert approx.converged
+    np.testing.assert_allclose(approx.x, xs, atol=1e-6)
+    assert approx.lo_mvps <= full.lo_mvps
+    # the init stops at the relative decrease: its KKT history ends at <= 1e-3 of its start
+    init = P.mono_pqn(lambda v: Ahat @ v, b, np.zeros(b.size), tol=inst.tol, tol_rel=1e-3)
+    assert init.history[-1] <= max(inst.tol, 1e-3 * init.history[0])
+    assert len(init.history) < len(P.mono_pqn(lambda v: Ahat @ v, b, np.zeros(b.size), tol=inst.tol).history)
+
+
 def _secant_trace(sign):
     """Run Bi-PQN's outer loop and report max |B^(k+1) S_low - Y_low|.
 
