@@ -109,6 +109,7 @@ static int lowfi_create(lcp_ctx* ctx) {
   lo->cfg.own_stream = 0;
   lo->cfg.lowfi_n_theta = 0;
   lo->cfg.lowfi_n_phi = 0;
+  lo->cfg.autotune = 1;   // its pair kernel runs ~10x per high-fidelity MVP: pick the fastest variant once
   lo->stream = ctx->stream;
   lo->device = ctx->device;
   lo->M = ctx->M;
