@@ -164,6 +164,15 @@ struct lcp_ctx {
   std::vector<int> ev_kind;
   std::string err;
   unsigned long long nlaunch = 0;   // kernels launched by this context
+  // captured CUDA graphs of the GMRES Arnoldi step, one per (column j,
+  // operator precision); re-captured when the FP32 kernel variant changes
+  struct ArnoldiGraph {
+    cudaGraphExec_t exec = nullptr;
+    int stamp = -1;
+    unsigned long long kernels = 0;
+    int c32 = 0, c64 = 0, cdf = 0;
+  };
+  std::vector<ArnoldiGraph> agraphs;
   // low-fidelity coarse-grid context (Bi-PQN, cfg.lowfi_n_theta > 0): same
   // bodies and stream, no contacts; its mobility solves run FP32 GMRES only
   lcp_ctx* lo = nullptr;

@@ -254,6 +254,89 @@ static int read_status(lcp_ctx* ctx, double* vals, int count) {
   return LCP_OK;
 }
 
+// Arnoldi step j of GMRES: z_j = Minv v_j (flexible right preconditioning),
+// w = (K + P) z_j, classical Gram-Schmidt twice (each update fused with the
+// next dots), the Givens column of H, v_{j+1} = w / H[j+1][j], and the copy of
+// the residual estimate and H[j+1][j] to the pinned host mirror.
+static int arnoldi_step(lcp_ctx* ctx, int j, int prec) {
+  const int L = 3 * ctx->N, m = ctx->m, T = 256;
+  const size_t ldv = (size_t)L;
+  double* base = ctx->H;
+  const size_t oH = 0, ocs = oH + (size_t)(m + 1) * m, osn = ocs + m, og = osn + m, oy = og + (m + 1),
+               oh1 = oy + m, oh2 = oh1 + (m + 1), ohn = oh2 + (m + 1);
+  double* h1 = base + oh1;
+  double* h2 = base + oh2;
+  double* hn = base + ohn;
+  double* vj = ctx->V + (size_t)j * ldv;
+  double* vn = ctx->V + (size_t)(j + 1) * ldv;
+  if (ctx->Z) {
+    double* zj = ctx->Z + (size_t)j * ldv;
+    LCP_TRY(precond_apply(ctx, vj, zj));
+    vj = zj;
+  }
+  LCP_TRY(stokes_apply(ctx, vj, vn, prec));
+  LCP_TRY(dots(ctx, L, j + 1, ctx->V, ldv, vn, h1));
+  LCP_TRY(update_dots(ctx, L, j + 1, ctx->V, ldv, h1, vn, j + 1, ctx->V, ldv, h2));
+  LCP_TRY(update_dots(ctx, L, j + 1, ctx->V, ldv, h2, vn, 1, vn, ldv, hn));
+  ++ctx->nlaunch, k_gmres_column<<<1, 1, 0, ctx->stream>>>(base, m, j, ctx->dscal);
+  ++ctx->nlaunch, k_scale<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, vn, hn, vn, 0, 0);
+  LCP_CUDA(cudaMemcpyAsync(ctx->hscal, ctx->dscal, sizeof(double) * 2, cudaMemcpyDeviceToHost, ctx->stream));
+  LCP_CUDA(cudaGetLastError());
+  return LCP_OK;
+}
+
+// Launches Arnoldi step j as a captured CUDA graph (one per column and
+// operator precision, captured on first use and replayed by every later
+// solve of the context), or directly when the context runs on the legacy
+// default stream (not capturable) or kernel profiling is on.
+static int arnoldi_launch(lcp_ctx* ctx, int j, int prec) {
+  if (!ctx->stream || ctx->prof) return arnoldi_step(ctx, j, prec);
+  const int key = j * 3 + prec;
+  const int stamp = ctx->sym ? 1000 + ctx->sym_v : ctx->v32;
+  if ((int)ctx->agraphs.size() <= key) ctx->agraphs.resize(key + 1);
+  lcp_ctx::ArnoldiGraph& g = ctx->agraphs[key];
+  if (!g.exec || g.stamp != stamp) {
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    const unsigned long long n0 = ctx->nlaunch;
+    const int c32 = ctx->c_fp32, c64 = ctx->c_fp64, cdf = ctx->c_df64;
+    LCP_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const int st = arnoldi_step(ctx, j, prec);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st != LCP_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (st != LCP_OK) return st;
+      ctx->err = std::string("GMRES graph capture: ") + cudaGetErrorString(ce);
+      return LCP_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      g.exec = nullptr;
+      ctx->err = std::string("GMRES graph instantiation: ") + cudaGetErrorString(ie);
+      return LCP_ERR_CUDA;
+    }
+    g.kernels = ctx->nlaunch - n0;
+    g.c32 = ctx->c_fp32 - c32;
+    g.c64 = ctx->c_fp64 - c64;
+    g.cdf = ctx->c_df64 - cdf;
+    ctx->nlaunch = n0;   // nothing ran during the capture
+    ctx->c_fp32 = c32;
+    ctx->c_fp64 = c64;
+    ctx->c_df64 = cdf;
+    g.stamp = stamp;
+  }
+  LCP_CUDA(cudaGraphLaunch(g.exec, ctx->stream));
+  ctx->nlaunch += g.kernels;
+  ctx->c_fp32 += g.c32;
+  ctx->c_fp64 += g.c64;
+  ctx->c_df64 += g.cdf;
+  return LCP_OK;
+}
+
 // Restarted GMRES(m) on (K + P) phi = rhs with operator precision `prec`;
 // flexible GMRES (Saad 1993) with the block-diagonal preconditioner when it
 // is enabled: the solution is assembled from the stored preconditioned
@@ -270,11 +353,8 @@ static int gmres(lcp_ctx* ctx, const double* rhs, double* phi, int zero_init, do
   // offsets of the scalar slots inside the work array (host mirror of gw_map)
   const size_t oH = 0, ocs = oH + (size_t)(m + 1) * m, osn = ocs + m, og = osn + m, oy = og + (m + 1),
                oh1 = oy + m, oh2 = oh1 + (m + 1), ohn = oh2 + (m + 1);
-  double* h1 = base + oh1;
-  double* h2 = base + oh2;
   double* hn = base + ohn;
   double* y = base + oy;
-  (void)og;
   int total = 0;
   double res = 0.0;
   bool first = true;
@@ -298,22 +378,11 @@ static int gmres(lcp_ctx* ctx, const double* rhs, double* phi, int zero_init, do
     ++ctx->nlaunch, k_scale<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, ctx->V, base + ohn + 1, ctx->V, 1, 0);  // V0 /= beta
     int j = 0;
     for (; j < m; j++) {
-      double* vj = ctx->V + (size_t)j * ldv;
-      double* vn = ctx->V + (size_t)(j + 1) * ldv;
-      if (ctx->Z) {   // flexible right preconditioning: z_j = Minv v_j, w = A z_j
-        double* zj = ctx->Z + (size_t)j * ldv;
-        LCP_TRY(precond_apply(ctx, vj, zj));
-        vj = zj;
-      }
-      LCP_TRY(stokes_apply(ctx, vj, vn, prec));
+      LCP_TRY(arnoldi_launch(ctx, j, prec));
       total++;
-      // classical Gram-Schmidt twice; each update is fused with the next dots
-      LCP_TRY(dots(ctx, L, j + 1, ctx->V, ldv, vn, h1));
-      LCP_TRY(update_dots(ctx, L, j + 1, ctx->V, ldv, h1, vn, j + 1, ctx->V, ldv, h2));
-      LCP_TRY(update_dots(ctx, L, j + 1, ctx->V, ldv, h2, vn, 1, vn, ldv, hn));
-      ++ctx->nlaunch, k_gmres_column<<<1, 1, 0, ctx->stream>>>(base, m, j, ctx->dscal);
-      ++ctx->nlaunch, k_scale<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, vn, hn, vn, 0, 0);   // v_{j+1} = w / H[j+1][j]
-      LCP_TRY(read_status(ctx, st, 2));
+      LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+      st[0] = ctx->hscal[0];
+      st[1] = ctx->hscal[1];
       res = st[0];
       if (!(res == res)) { ctx->err = "GMRES: NaN residual"; return LCP_ERR_NUMERICAL; }
       if (res <= tol_abs || total >= maxit || st[1] == 0.0) { j++; break; }

@@ -452,6 +452,8 @@ extern "C" int lcp_setup(const lcp_config* cfg, int n_bodies, const double* cent
 extern "C" void lcp_destroy(lcp_ctx* ctx) {
   if (!ctx) return;
   if (ctx->lo) lcp_destroy(ctx->lo);
+  for (auto& g : ctx->agraphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   for (void* p : ctx->allocs) cudaFree(p);

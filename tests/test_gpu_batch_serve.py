@@ -147,3 +147,26 @@ def test_every_kernel_variant_applies_the_same_operator(name, index):
             L.lcp_select_kernel_variant(ctx, "no_such_kernel")
     finally:
         L.lcp_destroy(ctx)
+
+
+def test_captured_arnoldi_graphs_match_direct_launches(small_batch):
+    """Contexts on their own stream replay each GMRES Arnoldi step as a captured
+    CUDA graph; on the legacy stream the same kernels are launched directly.  The
+    arithmetic is identical, so the results are bitwise equal, also on replay."""
+    inst = small_batch[1]
+    direct = L.lcp_setup(L.config_for(inst, L.LCP_MIXED), inst.centers, inst.axes)
+    graphed = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, own_stream=1), inst.centers, inst.axes)
+    try:
+        xa, sa, _ = L.lcp_solve(direct, L.LCP_BI_PQN, inst.tol)
+        n0 = L.lcp_launch_count(graphed)
+        xb, sb, _ = L.lcp_solve(graphed, L.LCP_BI_PQN, inst.tol)
+        n1 = L.lcp_launch_count(graphed)
+        xc, sc, _ = L.lcp_solve(graphed, L.LCP_BI_PQN, inst.tol)
+        n2 = L.lcp_launch_count(graphed)
+        assert np.array_equal(xa, xb) and np.array_equal(xb, xc)
+        assert sa["gmres_iterations"] == sb["gmres_iterations"] == sc["gmres_iterations"]
+        assert sa["fp32_applies"] == sb["fp32_applies"]
+        assert n2 - n1 == n1 - n0 > 0      # replayed kernels are counted like launched ones
+    finally:
+        L.lcp_destroy(direct)
+        L.lcp_destroy(graphed)
