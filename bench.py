@@ -72,6 +72,8 @@ def parse():
     p.add_argument("--lowfi", default="auto",
                    help="Bi-PQN low-fidelity operator: rpy, a coarse boundary-integral grid NTxNP (e.g. 8x16), "
                         "or auto = (n_theta - 3) x 2(n_theta - 3) of the workload's grid")
+    p.add_argument("--lowfi-min-bodies", type=int, default=10 ** 9,
+                   help="batched/serving modes: use --lowfi only for instances with at least this many spheres")
     p.add_argument("--fp64-compare", type=int, default=1)
     p.add_argument("--cpu-baseline", type=int, default=1)
     p.add_argument("--compare-methods", type=int, default=1,
@@ -159,8 +161,10 @@ def lowfi_overrides(spec: str, n_theta: int = 0) -> dict:
     if spec == "rpy":
         return {}
     if spec == "auto":   # measured optimum at 64 and 216 spheres; FP32 GMRES to 1e-4 (see design notes)
-        nt = max(2, n_theta - 3)
-        return {"lowfi_n_theta": nt, "lowfi_n_phi": 2 * max(2, nt), "lowfi_tol": 1e-4, "init_forcing": 1e-3}
+        nt = n_theta - 3
+        if nt < 6:       # coarser grids do not resolve neighbouring spheres: RPY
+            return {}
+        return {"lowfi_n_theta": nt, "lowfi_n_phi": 2 * nt, "lowfi_tol": 1e-4, "init_forcing": 1e-3}
     nt, nph = (int(v) for v in spec.lower().split("x"))
     return {"lowfi_n_theta": nt, "lowfi_n_phi": nph}
 
@@ -390,7 +394,13 @@ def run_batched(args):
     insts = batched_instances(args.batch_count)
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    ctxs = [L.lcp_setup(L.config_for(i, L.LCP_MIXED, own_stream=1, autotune=1), i.centers, i.axes) for i in insts]
+    # low fidelity per instance: the coarse grid for instances of at least --lowfi-min-bodies
+    # spheres (where it cuts high-fidelity MVPs), RPY below
+    def lowfi_of(i):
+        return lowfi_overrides(args.lowfi, i.n_theta) if i.n_bodies >= args.lowfi_min_bodies else {}
+
+    ctxs = [L.lcp_setup(L.config_for(i, L.LCP_MIXED, own_stream=1, autotune=1, **lowfi_of(i)), i.centers, i.axes)
+            for i in insts]
     t_setup = time.perf_counter() - t0
     xs = [torch.empty(max(L.lcp_sizes(c)[2], 1), dtype=torch.float64, device="cuda") for c in ctxs]
     for _ in range(max(1, args.warmup // 3)):

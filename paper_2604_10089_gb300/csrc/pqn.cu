@@ -383,7 +383,9 @@ __device__ int prox_ssn(const PqnDev& pq, const PqnWork& wk, int r, const double
   bmultidot(pq.V, n, r, wk.d, sm.udv + r);
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    for (int sweep = 0; sweep < 20000; sweep++) {
+    // bounded: a model that needs more sweeps is far from convex (e.g. a low-fidelity
+    // operator that is not positive definite); the best iterate is returned
+    for (int sweep = 0; sweep < 400; sweep++) {
       double worst = 0.0;
       for (int l = 0; l < n; l++) {
         double gr = 0.0, bll = 0.0;
