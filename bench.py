@@ -648,6 +648,11 @@ def main():
                        "l2": "inputs larger than L2 (Krylov basis 76 MB + operator sweeps per apply)",
                        "parallelism": f"instances x{world}"},
             "latency_s": {"p50": pct(r["lat"], 50), "p99": pct(r["lat"], 99)},
+            "matvecs_per_s": {
+                "high_fidelity_mvps": float(np.sum(s["hi_mvps"])) / r["t_total"],
+                "low_fidelity_mvps": float(np.sum(s["lo_mvps"])) / r["t_total"],
+                "fp32_pair_sum_applies": float(np.sum(s["fp32_applies"])) / r["t_total"],
+                "note": "per second of the timed region; the FP32 applies are the high-fidelity grid's"},
             "roofline": r["roof"], "fp64_kernel": r["k64"], "df64_kernel": r["kdf"], "clocks": r["clocks"],
             "e2e": r["e2e"], "gpu_launches": r["launches"], "cpu_baseline": cpu,
             "fp64_mono_pqn": r["fp64"], "method_comparison_mixed": r["comparison"], "trajectory": r["traj"],
