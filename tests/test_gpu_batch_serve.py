@@ -137,12 +137,18 @@ def test_every_kernel_variant_applies_the_same_operator(name, index):
         ref = torch.empty_like(phi)
         L.lcp_stokes_apply_dev(ctx, phi, ref, L.LCP_DF64)
         out = torch.empty_like(phi)
+        ref64 = torch.empty_like(phi)
+        L.lcp_stokes_apply_dev(ctx, phi, ref64, L.LCP_FP64)
         for v in VARIANTS:
             L.lcp_select_kernel_variant(ctx, v)
             assert L.lcp_kernel_variant(ctx) == v
             L.lcp_stokes_apply_dev(ctx, phi, out, L.LCP_MIXED)
             err = float((out - ref).abs().max() / ref.abs().max())
             assert err <= 1e-5, (v, err)
+            # the double-float residual sum keeps FP64 accuracy whichever FP32 variant is chosen
+            L.lcp_stokes_apply_dev(ctx, phi, out, L.LCP_DF64)
+            err = float((out - ref64).abs().max() / ref64.abs().max())
+            assert err <= 1e-12, (v, "df", err)
         with pytest.raises(L.LcpError):
             L.lcp_select_kernel_variant(ctx, "no_such_kernel")
     finally:
