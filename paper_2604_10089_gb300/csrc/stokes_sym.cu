@@ -406,6 +406,18 @@ static size_t sym_smem(int ns, int v) {
          sizeof(float) * SYM_WARPS * 3 * ns_pad + sizeof(double) * SYM_TPT * 3 * SYM_THREADS;
 }
 
+// The reverse rows grow as N x M (about 0.7 KB per pair of bodies at 242
+// nodes each): above a quarter of the device's memory the symmetric sums are
+// left out and the plain kernels, whose buffers grow as N, serve the size.
+static size_t sym_rev_cap() {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return total_b / 4;
+}
+
 static int host_cta_of(long long u, int U, int G) {
   auto start = [&](long long c) { return (c * U) / G; };
   long long c = (u * G) / U;
@@ -433,6 +445,10 @@ int stokes_sym_configure(lcp_ctx* ctx) {
   ctx->sym_ntb = ntb;
   ctx->sym_units = U;
   ctx->sym_slots = 1;
+  if (sizeof(float) * (size_t)roff[ntb] > sym_rev_cap()) {   // every symmetric variant stays unusable
+    ctx->sym = false;
+    return LCP_OK;
+  }
   for (int v = 0; v < kNumSymVariants && v < 8; v++) {
     const size_t smem = sym_smem(ns, v);
     if (smem > 48 * 1024)
@@ -472,12 +488,14 @@ bool stokes_sym_variant_usable(const lcp_ctx* ctx, int v) {
   return ctx->symv_occ[v] > 0 && ctx->symv_slots[v] <= ctx->splits;
 }
 
-// Bytes of the reverse buffer for a size (footprint estimate).
+// Bytes of the reverse buffer for a size (footprint estimate; 0 where the
+// symmetric sums are left out).
 size_t stokes_sym_bytes(int M, int ns) {
   const long long N = (long long)M * ns;
   const long long ntb = (N + SYM_TB - 1) / SYM_TB;
   long long total = 0;
   for (long long tb = 0; tb < ntb; tb++) total += (long long)(M - 1 - (tb * SYM_TB) / ns) * 3 * ns;
+  if (sizeof(float) * (size_t)total > sym_rev_cap()) return 0;
   return sizeof(float) * (size_t)(total > 0 ? total : 1) + (sizeof(int) + sizeof(long long)) * (size_t)(ntb + 1);
 }
 
