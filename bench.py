@@ -47,9 +47,11 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 REFERENCE_SOLVES_PER_LCP = 6.8
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # FP32 pair kernel at 216 spheres x 242 nodes, from an ncu capture, with the SHA-1 of
-# the device code it was taken on (reported as null once that code changes).
+# the device code it was taken on (reported as null once that code changes; the
+# hash of the symmetric kernel's file was renewed when its unit bookkeeping moved
+# to a shared header, the kernel's code unchanged).
 PAIR32_TRAFFIC = {
-    "k_pair32_sym_a4": {"file": "stokes_sym.cu", "source_sha1": "9a438f5e284e4528cefbebfa614c0f5030181076",
+    "k_pair32_sym_a4": {"file": "stokes_sym.cu", "source_sha1": "4427e4d20dd6e9c5f57c04daec13adec0fb13d50",
                         "bytes_per_launch": 691968},
     "k_pair32": {"file": "stokes.cu", "source_sha1": "298b391165dc32f4d22c484bf6d970a4f86ee95e",
                  "bytes_per_launch": 665088},
@@ -368,8 +370,10 @@ def run_ours(args, rank, world, local):
     }
     kdf = None
     if cdf:
-        kdf = {"kernel": "k_pair_df", "launches": cdf, "avg_launch_ms": tdf / cdf,
-               "fp32_ops_per_pair_note": "double-FP32 arithmetic, ~250 FP32 operations per pair",
+        sym_df = variant.startswith("sym")
+        kdf = {"kernel": "k_pair_df_sym" if sym_df else "k_pair_df", "launches": cdf, "avg_launch_ms": tdf / cdf,
+               "fp32_ops_per_pair_note": "double-FP32 arithmetic, ~250 FP32 operations per ordered pair"
+                                         + (", one evaluation per unordered pair (symmetric)" if sym_df else ""),
                "pairs_per_s": pairs / (tdf / cdf / 1e3), "share_of_timed_region": tdf / 1e3 / t_total}
     lowfi_desc = ("rpy" if not lowfi else
                   f"boundary integral on a {lowfi['lowfi_n_theta']}x{lowfi['lowfi_n_phi']} grid, FP32 GMRES to "

@@ -171,10 +171,11 @@ LCP_API int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n_co
  * (one evaluation per unordered node pair; the default is "sym_a4"), "t2c8" = the
  * plain sum with 2 targets per thread and 8 source bodies per shared-memory
  * tile, and so on; chosen by the autotuner when cfg.autotune is set.  The
- * symmetric variants keep one reverse row per (512-node target block, later
- * body), about 0.7 KB per pair of bodies at 242 nodes each; where those rows
- * would exceed a quarter of the device's memory (above about 10 000 bodies at
- * 242 nodes) they are not set up and the plain variants serve the context. */
+ * symmetric variants (and the symmetric double-float residual sum that goes
+ * with them) keep one reverse row per (512-node target block, later body),
+ * about 1.4 KB per pair of bodies at 242 nodes each; where those rows would
+ * exceed a quarter of the device's memory (above about 7 000 bodies at 242
+ * nodes) they are not set up and the plain variants serve the context. */
 LCP_API const char* lcp_kernel_variant(const lcp_ctx* ctx);
 
 /* Forces the FP32 pair-kernel variant by name (one of the names

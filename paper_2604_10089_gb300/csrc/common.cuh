@@ -126,9 +126,10 @@ struct lcp_ctx {
   int sym_v = 0;              // symmetric kernel variant in use
   int sym_ntb = 0, sym_units = 0, sym_slots = 0;   // sym_slots: largest over the variants
   int symv_occ[8] = {0}, symv_grid[8] = {0}, symv_slots[8] = {0};
+  int symdf_grid = 0, symdf_slots = 0;   // the symmetric double-float kernel (stokes_sym_df.cu)
   int* sym_off = nullptr;          // [ntb + 1] first unit of each target block
   long long* sym_roff = nullptr;   // [ntb + 1] first float of each block's reverse rows
-  float* sym_rev = nullptr;        // reverse partial sums, one row per unit
+  float* sym_rev = nullptr;        // reverse partial sums, one row per unit (FP32, or (hi, lo) pairs)
   double *V = nullptr, *H = nullptr;  // Krylov basis [(m+1)][3N], Hessenberg etc.
   double* Z = nullptr;                 // preconditioned basis [m][3N] (flexible GMRES)
   float* pinv = nullptr;               // isolated-sphere inverse (3 ns x 3 ns, FP32)

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace {
 
@@ -239,21 +240,8 @@ static const Pair32Variant kPair32Variants[] = {
 constexpr int kNumPair32Variants = sizeof(kPair32Variants) / sizeof(kPair32Variants[0]);
 
 // ---------------------------------------------------------------------------
-// Double-FP32 ("double-float") stresslet sum for the refinement residual.
-// Every quantity is an unevaluated sum hi + lo of two floats; sums and
-// products use the error-free transformations TwoSum (Knuth) and TwoProd (one
-// FMA), renormalised with Fast2Sum (Dekker).  Relative accuracy per operation
-// is about 2^-44, so (K phi)_p is accurate to ~1e-13 of its terms while
-// running on the FP32 pipe (64x the FP64 rate on GB300).  The reciprocal
-// square root is a MUFU seed refined by one Newton step in double-float.
-struct dfl {
-  float hi, lo;
-};
-__device__ __forceinline__ dfl df_split(double v) {
-  const float h = __double2float_rn(v);
-  return {h, __double2float_rn(v - (double)h)};
-}
-
+// Double-FP32 ("double-float") stresslet sum for the refinement residual; the
+// arithmetic (TwoSum, TwoProd, Fast2Sum on hi + lo float pairs) is in dfloat.cuh.
 __global__ void k_split_df(int L, const double* __restrict__ x, float* __restrict__ y) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= L) return;
@@ -261,59 +249,6 @@ __global__ void k_split_df(int L, const double* __restrict__ x, float* __restric
   const dfl v = df_split(x[t]);
   y[6 * node + d] = v.hi;
   y[6 * node + 3 + d] = v.lo;
-}
-
-// Packed double-float arithmetic on two lanes at once (FP32x2 instructions):
-// every D2 holds two independent double-float numbers, here the terms of two
-// source nodes q, q+1 for one target.  Intermediate results stay
-// unnormalised (lo may exceed half an ulp of hi by a few ulps; the dropped
-// lo*lo products are then ~2^-44 of the operands' product) and are
-// renormalised with Fast2Sum only where cancellation is expected (the
-// separation r and the dot products r.n, r.(phi_q - phi_p)), after the
-// Newton step of |r|^-1, and in the running sums.
-struct D2 {
-  float2 hi, lo;
-};
-__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b, rounded once
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-// TwoSum (Knuth): s + e = a + b exactly.
-__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
-  s = add2(a, b);
-  const float2 bb = sub2(s, a);
-  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
-}
-__device__ __forceinline__ D2 fast2sum2(float2 a, float2 b) {   // |a| >= |b|
-  const float2 s = add2(a, b);
-  return {s, sub2(b, sub2(s, a))};
-}
-__device__ __forceinline__ D2 dadd_u(D2 a, D2 b) {
-  float2 s, e;
-  two_sum2(a.hi, b.hi, s, e);
-  return {s, add2(e, add2(a.lo, b.lo))};
-}
-__device__ __forceinline__ D2 dadd_n(D2 a, D2 b) {
-  const D2 t = dadd_u(a, b);
-  return fast2sum2(t.hi, t.lo);
-}
-// TwoProd by FMA plus the cross terms.
-__device__ __forceinline__ D2 dmul_u(D2 a, D2 b) {
-  const float2 p = mul2(a.hi, b.hi);
-  float2 e = fma2(a.hi, b.hi, neg2(p));
-  e = fma2(a.hi, b.lo, e);
-  e = fma2(a.lo, b.hi, e);
-  return {p, e};
-}
-__device__ __forceinline__ D2 dsq_u(D2 a) {
-  const float2 p = mul2(a.hi, a.hi);
-  float2 e = fma2(a.hi, a.hi, neg2(p));
-  e = fma2(a.hi, add2(a.lo, a.lo), e);
-  return {p, e};
 }
 
 // Double-float stresslet sum: same (target block, source body) decomposition
@@ -600,6 +535,7 @@ __global__ void k_neg(int L, const double* __restrict__ x, double* __restrict__ 
 // ------------------------------------------------------------------ host side
 size_t stokes_pair_smem(int ns, int precision);
 int stokes_sym_apply(lcp_ctx* ctx, double* out);
+int stokes_sym_df_apply(lcp_ctx* ctx, double* out);
 // One full wave of CTAs for a pair kernel: SMs x resident CTAs per SM, capped
 // by the number of (target block, source body) units.
 static int pair_targets(int precision, int v32) {
@@ -654,6 +590,11 @@ int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
     ++ctx->nlaunch, k_to_f32<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(3 * N, phi, ctx->phi32);
     ctx->c_fp32++;
     return stokes_sym_apply(ctx, out);
+  }
+  if (precision == LCP_DF64 && ctx->sym && ctx->symdf_grid > 0 && ctx->symdf_slots <= ctx->splits) {
+    ++ctx->nlaunch, k_split_df<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(3 * N, phi, ctx->phidf);
+    ctx->c_df64++;
+    return stokes_sym_df_apply(ctx, out);
   }
   LCP_CUDA(cudaMemsetAsync(ctx->partial, 0, sizeof(double) * 3 * (size_t)N * slots, ctx->stream));
   cudaEvent_t e0 = nullptr, e1 = nullptr;

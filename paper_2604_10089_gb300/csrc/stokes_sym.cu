@@ -25,12 +25,13 @@
 #include <vector>
 
 #include "common.cuh"
+#include "sym_units.cuh"
 
 namespace {
 
 constexpr int SYM_THREADS = 128;
 constexpr int SYM_TPT = 4;                         // targets per thread (two FP32x2 packs)
-constexpr int SYM_TB = SYM_TPT * SYM_THREADS;      // targets per block
+static_assert(SYM_TPT * SYM_THREADS == SYM_TB, "target block of the symmetric units");
 constexpr int SYM_WARPS = SYM_THREADS / 32;
 constexpr int SYM_CHUNK = 2;                       // source bodies staged per tile
 constexpr float SYM_EPS = 1e-20f;   // r = 0 only for q = p: keeps |r|^-3 = 1e30 finite, the term 0
@@ -41,19 +42,6 @@ __device__ __forceinline__ float rsqrt_fast(float x) {
   return y;
 }
 
-struct SymUnits {
-  int U, G, ntb, ns;
-  const int* off;          // [ntb + 1]: first unit of each target block
-  const long long* roff;   // [ntb]: first float of each target block's reverse rows
-  __device__ __forceinline__ int start(int c) const { return (int)(((long long)c * U) / G); }
-  __device__ __forceinline__ int cta_of(int u) const {
-    int c = (int)(((long long)u * G) / U);
-    while (c + 1 < G && start(c + 1) <= u) c++;
-    while (c > 0 && start(c) > u) c--;
-    return c;
-  }
-  __device__ __forceinline__ int first_body(int tb) const { return (int)(((long long)tb * SYM_TB) / ns); }
-};
 
 // Two targets (the lanes of e, nf, wp) against one source (duplicated in the
 // lanes of n*, w*, f*).  acc += forward terms, rv += reverse terms.
@@ -406,6 +394,8 @@ static size_t sym_smem(int ns, int v) {
          sizeof(float) * SYM_WARPS * 3 * ns_pad + sizeof(double) * SYM_TPT * 3 * SYM_THREADS;
 }
 
+int stokes_sym_df_configure(lcp_ctx* ctx, const int* off, int ntb);
+
 // The reverse rows grow as N x M (about 0.7 KB per pair of bodies at 242
 // nodes each): above a quarter of the device's memory the symmetric sums are
 // left out and the plain kernels, whose buffers grow as N, serve the size.
@@ -445,7 +435,7 @@ int stokes_sym_configure(lcp_ctx* ctx) {
   ctx->sym_ntb = ntb;
   ctx->sym_units = U;
   ctx->sym_slots = 1;
-  if (sizeof(float) * (size_t)roff[ntb] > sym_rev_cap()) {   // every symmetric variant stays unusable
+  if (2 * sizeof(float) * (size_t)roff[ntb] > sym_rev_cap()) {   // every symmetric variant stays unusable
     ctx->sym = false;
     return LCP_OK;
   }
@@ -467,13 +457,16 @@ int stokes_sym_configure(lcp_ctx* ctx) {
     ctx->symv_slots[v] = slots;
     if (slots > ctx->sym_slots) ctx->sym_slots = slots;
   }
+  const int df_slots = stokes_sym_df_configure(ctx, off.data(), ntb);
+  if (df_slots > ctx->sym_slots) ctx->sym_slots = df_slots;
   // default: the symmetric sum when every CTA gets several units (otherwise
   // the one-wave balance of the plain kernel's finer units wins)
   ctx->sym = U >= 4 * ctx->symv_grid[0];
   ctx->sym_v = 0;
   ctx->sym_off = (int*)ctx_alloc(ctx, sizeof(int) * (ntb + 1));
   ctx->sym_roff = (long long*)ctx_alloc(ctx, sizeof(long long) * (ntb + 1));
-  ctx->sym_rev = (float*)ctx_alloc(ctx, sizeof(float) * (size_t)(roff[ntb] > 0 ? roff[ntb] : 1));
+  // room for double-float (hi, lo) rows: the symmetric double-float kernel shares the buffer
+  ctx->sym_rev = (float*)ctx_alloc(ctx, 2 * sizeof(float) * (size_t)(roff[ntb] > 0 ? roff[ntb] : 1));
   if (!ctx->sym_off || !ctx->sym_roff || !ctx->sym_rev) return LCP_ERR_OOM;
   LCP_CUDA(cudaMemcpyAsync(ctx->sym_off, off.data(), sizeof(int) * (ntb + 1), cudaMemcpyHostToDevice, ctx->stream));
   LCP_CUDA(cudaMemcpyAsync(ctx->sym_roff, roff.data(), sizeof(long long) * (ntb + 1), cudaMemcpyHostToDevice,
@@ -495,8 +488,8 @@ size_t stokes_sym_bytes(int M, int ns) {
   const long long ntb = (N + SYM_TB - 1) / SYM_TB;
   long long total = 0;
   for (long long tb = 0; tb < ntb; tb++) total += (long long)(M - 1 - (tb * SYM_TB) / ns) * 3 * ns;
-  if (sizeof(float) * (size_t)total > sym_rev_cap()) return 0;
-  return sizeof(float) * (size_t)(total > 0 ? total : 1) + (sizeof(int) + sizeof(long long)) * (size_t)(ntb + 1);
+  if (2 * sizeof(float) * (size_t)total > sym_rev_cap()) return 0;
+  return 2 * sizeof(float) * (size_t)(total > 0 ? total : 1) + (sizeof(int) + sizeof(long long)) * (size_t)(ntb + 1);
 }
 
 // (K + P) phi with the symmetric FP32 pair sum (variant ctx->sym_v); phi32

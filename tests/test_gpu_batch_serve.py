@@ -145,7 +145,7 @@ def test_every_kernel_variant_applies_the_same_operator(name, index):
             L.lcp_stokes_apply_dev(ctx, phi, out, L.LCP_MIXED)
             err = float((out - ref).abs().max() / ref.abs().max())
             assert err <= 1e-5, (v, err)
-            # the double-float residual sum keeps FP64 accuracy whichever FP32 variant is chosen
+            # the double-float residual sum follows the choice (symmetric or plain): FP64 accuracy
             L.lcp_stokes_apply_dev(ctx, phi, out, L.LCP_DF64)
             err = float((out - ref64).abs().max() / ref64.abs().max())
             assert err <= 1e-12, (v, "df", err)
