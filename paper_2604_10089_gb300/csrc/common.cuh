@@ -239,3 +239,8 @@ char* pqn_carve(PqnDev* pq, char* base, int n, int rmax);
 int pqn_reset(lcp_ctx* ctx, PqnDev* pq);
 int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, double* x, lcp_stats* st);
 void* ctx_alloc(lcp_ctx* ctx, size_t bytes);
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes` and never lowers it: contexts of different sizes share the
+// kernels, and a smaller context set up after a larger one must not cut the
+// limit below the larger one's launches.  Thread-safe.
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes);

@@ -1,6 +1,8 @@
 // Geometry and contact set-up kernels (Sec. 3 of the paper: Eq. collisional-set
 // and the contact matrix D; Sec. 5.1: order-p surface discretisation).
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <cstring>
 
 #include "common.cuh"
@@ -200,6 +202,20 @@ __global__ void k_scan_small(int M, const int* cnt, int* ptr) {
   int s = 0;
   for (int i = 0; i < M; i++) { ptr[i] = s; s += cnt[i]; }
   ptr[M] = s;
+}
+
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limits;
+  int dev = 0;
+  const cudaError_t ed = cudaGetDevice(&dev);
+  if (ed != cudaSuccess) return ed;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limits[std::make_pair(dev, kernel)];
+  if (bytes <= cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 void* ctx_alloc(lcp_ctx* ctx, size_t bytes) {

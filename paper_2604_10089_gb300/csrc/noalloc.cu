@@ -118,10 +118,10 @@ extern "C" int lcp_stokes_apply_noalloc(int n_bodies, int n_theta, int n_phi, do
   int sms = 0, occ = 0;
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (precision == LCP_MIXED) {
-    if (smem > 48 * 1024) NA_CUDA(cudaFuncSetAttribute(k_pair32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) NA_CUDA(raise_smem_limit((const void*)k_pair32, smem));
     NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair32, PAIR_THREADS_PUBLIC, smem));
   } else {
-    if (smem > 48 * 1024) NA_CUDA(cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) NA_CUDA(raise_smem_limit((const void*)k_pair64, smem));
     NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair64, PAIR_THREADS_PUBLIC, smem));
   }
   const int min_per = (M + NA_SLOTS - 2) / (NA_SLOTS - 1);   // ceil(M / (slots - 1)) units per CTA

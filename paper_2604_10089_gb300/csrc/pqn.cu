@@ -1153,7 +1153,7 @@ static int run_mono(lcp_ctx* ctx, PqnDev& pq, MvpFn mvp, int sub, const double* 
 int pqn_configure(lcp_ctx* ctx, int rmax) {
   const size_t smem = prox_smem_bytes(rmax);
   if (smem > 48 * 1024)
-    LCP_CUDA(cudaFuncSetAttribute(k_pqn_direction, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LCP_CUDA(raise_smem_limit((const void*)k_pqn_direction, smem));
   return LCP_OK;
 }
 

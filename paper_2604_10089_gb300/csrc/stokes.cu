@@ -679,11 +679,11 @@ size_t stokes_pair_smem(int ns, int precision) {
 // Shared-memory limits and one-wave grid sizes (occupancy) of the pair kernels.
 int stokes_configure(lcp_ctx* ctx) {
   const size_t s64 = stokes_pair_smem(ctx->ns, LCP_FP64);
-  if (s64 > 48 * 1024) LCP_CUDA(cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64));
+  if (s64 > 48 * 1024) LCP_CUDA(raise_smem_limit((const void*)k_pair64, s64));
   for (int v = 0; v < kNumPair32Variants; v++) {
     const size_t sv = pair32_smem(ctx->ns, v);
     if (sv > 48 * 1024)
-      LCP_CUDA(cudaFuncSetAttribute(kPair32Variants[v].kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv));
+      LCP_CUDA(raise_smem_limit((const void*)kPair32Variants[v].kernel, sv));
     LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occ32v[v], kPair32Variants[v].kernel, PAIR_THREADS, sv));
   }
   int dev = 0;
@@ -691,7 +691,7 @@ int stokes_configure(lcp_ctx* ctx) {
   LCP_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev));
   LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occ64, k_pair64, PAIR_THREADS, s64));
   const size_t sdf = stokes_pair_smem(ctx->ns, LCP_DF64);
-  if (sdf > 48 * 1024) LCP_CUDA(cudaFuncSetAttribute(k_pair_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sdf));
+  if (sdf > 48 * 1024) LCP_CUDA(raise_smem_limit((const void*)k_pair_df, sdf));
   LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->occdf, k_pair_df, PAIR_THREADS, sdf));
   return LCP_OK;
 }

@@ -442,7 +442,7 @@ int stokes_sym_configure(lcp_ctx* ctx) {
   for (int v = 0; v < kNumSymVariants && v < 8; v++) {
     const size_t smem = sym_smem(ns, v);
     if (smem > 48 * 1024)
-      LCP_CUDA(cudaFuncSetAttribute(kSymVariants[v].kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      LCP_CUDA(raise_smem_limit((const void*)kSymVariants[v].kernel, smem));
     int occ = 0;
     LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kSymVariants[v].kernel, SYM_THREADS, smem));
     int G = ctx->num_sms * (occ > 0 ? occ : 1);

@@ -303,7 +303,7 @@ static int host_cta_of_df(long long u, int U, int G) {
 int stokes_sym_df_configure(lcp_ctx* ctx, const int* off, int ntb) {
   const size_t smem = sdf_smem(ctx->ns);
   if (smem > 227 * 1024) return 0;
-  if (smem > 48 * 1024) LCP_CUDA(cudaFuncSetAttribute(k_pair_df_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) LCP_CUDA(raise_smem_limit((const void*)k_pair_df_sym, smem));
   int occ = 0;
   LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_df_sym, SDF_THREADS, smem));
   if (occ <= 0) return 0;

@@ -115,3 +115,27 @@ def test_lowfi_errors_and_footprint():
             L.lcp_destroy(plain)
     finally:
         L.lcp_destroy(ctx)
+
+
+def test_coarse_child_keeps_parent_shared_memory_limits():
+    """A coarse-grid child context set up after its parent needs less shared
+    memory per pair kernel; the parent's launches must still be allowed theirs
+    (11 x 22 parent: the symmetric double-float kernel takes 105 KB, the 8 x 16
+    child 61 KB)."""
+    inst = make_instance("spheres8_grid7x14", 0)
+    cfg = L.config_for(inst, L.LCP_MIXED, n_theta=11, n_phi=22, lowfi_n_theta=8, lowfi_n_phi=16)
+    ctx = L.lcp_setup(cfg, inst.centers, inst.axes)
+    try:
+        n = 3 * L.lcp_sizes(ctx)[1]
+        phi = torch.tensor(np.random.default_rng(4).standard_normal(n), device="cuda")
+        ref = torch.empty_like(phi)
+        L.lcp_stokes_apply_dev(ctx, phi, ref, L.LCP_FP64)
+        out = torch.empty_like(phi)
+        for v in ("sym_a4", "t2c8"):
+            L.lcp_select_kernel_variant(ctx, v)
+            L.lcp_stokes_apply_dev(ctx, phi, out, L.LCP_DF64)
+            assert rel(out.cpu().numpy(), ref.cpu().numpy()) <= 1e-12, v
+            L.lcp_stokes_apply_dev(ctx, phi, out, L.LCP_MIXED)
+            assert rel(out.cpu().numpy(), ref.cpu().numpy()) <= 1e-5, v
+    finally:
+        L.lcp_destroy(ctx)
