@@ -738,7 +738,9 @@ int stokes_autotune(lcp_ctx* ctx) {
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end()) {
+    // a size class spans a factor of two in bodies: the cached choice is taken
+    // only where it also fits this context (slots, or no symmetric buffers)
+    if (it != g_tune_cache.end() && candidate_usable(ctx, it->second)) {
       set_candidate(ctx, it->second);
       return LCP_OK;
     }
