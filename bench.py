@@ -162,7 +162,7 @@ def lowfi_overrides(spec: str, n_theta: int = 0) -> dict:
     """Config fields of the low-fidelity operator: {} for RPY, else the coarse grid."""
     if spec == "rpy":
         return {}
-    if spec == "auto":   # measured optimum at 64 and 216 spheres; FP32 GMRES to 1e-4 (see design notes)
+    if spec == "auto":   # measured optimum at 64 and 216 spheres: grid n_theta - 3, FP32 GMRES to 1e-4
         nt = n_theta - 3
         if nt < 6:       # coarser grids do not resolve neighbouring spheres: RPY
             return {}
