@@ -110,3 +110,25 @@ def test_matrix_free_gmres_matches_dense_lu():
     u_d = d.apply(FT, inst.axes)
     u_m = m.apply(FT, inst.axes)
     assert np.abs(u_d - u_m).max() <= 1e-10 * np.abs(u_d).max()
+
+
+def test_both_ordered_terms_of_a_node_pair_share_one_evaluation():
+    """The symmetric pair sums evaluate, for nodes p, q on different bodies,
+    t = r.(phi_q - phi_p) / |r|^5 with r = x_p - x_q once and form both ordered
+    terms of the double layer from it: (r.wn_q) t r on target p and (r.wn_p) t r
+    on target q, wn = -(3/4 pi) w n.  Checked against the oracle's dense K
+    (off-diagonal blocks; the singularity subtraction puts -phi_p on the diagonal)."""
+    c = np.array([[0.0, 0.0, 0.0], [2.3, -0.5, 0.4]])
+    x, n, w, body = surface_nodes(c, 5, 10)
+    K = stresslet_matrix(x, n, w)
+    phi = np.random.default_rng(5).standard_normal(x.shape)
+    wn = -3.0 / (4.0 * np.pi) * w[:, None] * n
+    for p in np.flatnonzero(body == 0)[::7]:
+        for q in np.flatnonzero(body == 1)[::5]:
+            r = x[p] - x[q]
+            t = r @ (phi[q] - phi[p]) / np.linalg.norm(r) ** 5
+            on_p = K[3 * p:3 * p + 3, 3 * q:3 * q + 3] @ (phi[q] - phi[p])
+            on_q = K[3 * q:3 * q + 3, 3 * p:3 * p + 3] @ (phi[p] - phi[q])
+            scale = np.abs(t * r).max() * np.abs(wn).max() * np.linalg.norm(r) + 1e-300
+            assert np.abs(on_p - (r @ wn[q]) * t * r).max() <= 1e-13 * scale
+            assert np.abs(on_q - (r @ wn[p]) * t * r).max() <= 1e-13 * scale
