@@ -19,6 +19,12 @@ stop when ||min(x, g)||_2 <= tol (Sec. 6); the root function of Prop. 1 is
 the carried secant matrix is Y_hat + (u u^T - v v^T) S_hat, which makes
 B^(k+1) S = Y hold exactly; a direction with p^T g >= 0 resets the memory and
 falls back to the projected-gradient direction.
+
+Memory: Sec. 6 keeps every secant pair (full memory), which is the default
+here (r_max=None).  A finite r_max models a storage bound: once more than
+r_max pairs are held, the oldest quarter is dropped at once and the unrolled
+factors are rebuilt from the pairs that remain (the GPU library's limit is 32
+pairs; runs that stay below it do not depend on the rule).
 """
 from __future__ import annotations
 
@@ -48,7 +54,7 @@ def step_size(x, p, g, Ap):
 class QNModel:
     """B = diag(d) + U U^T - V V^T built from secant pairs (s, y) in order."""
 
-    def __init__(self, d, r_max=32):
+    def __init__(self, d, r_max=None):
         self.d = np.asarray(d, dtype=np.float64)
         self.r_max = r_max
         self.S, self.Y, self.B0S = [], [], []
@@ -108,7 +114,7 @@ class QNModel:
         self.S.append(s)
         self.Y.append(y)
         self.B0S.append(b0s)
-        if len(self.S) > self.r_max:
+        if self.r_max is not None and len(self.S) > self.r_max:
             # memory full: the oldest quarter of the pairs is dropped at once
             drop = max(1, self.r_max // 4)
             del self.S[:drop], self.Y[:drop], self.B0S[:drop]
@@ -205,7 +211,7 @@ class PQNResult:
     extra: np.ndarray | None = None
 
 
-def mono_pqn(mvp, b, x0, tol=1e-8, kmax=100, d=None, pairs=(), r_max=32,
+def mono_pqn(mvp, b, x0, tol=1e-8, kmax=100, d=None, pairs=(), r_max=None,
              g0=None, extra_mvp=None, scale0=False, tol_rel=0.0):
     """Algorithm 1 (Mono-PQN).
 
@@ -279,7 +285,7 @@ class BiPQNResult:
 
 
 def bi_pqn(mvp_hi, mvp_lo, b, x_init, tol=1e-8, kmax=50, kmax_inner=100,
-           forcing=1e-3, r_max=32, scale0=False, init_forcing=0.0):
+           forcing=1e-3, r_max=None, scale0=False, init_forcing=0.0):
     """Algorithm 4 (Bi-PQN) with B^(0) = A_hat.
 
     The subproblem min_{z>=0} 1/2 z^T B z + (g - B x)^T z (Eq. pqnSubproblem)

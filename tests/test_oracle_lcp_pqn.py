@@ -107,6 +107,68 @@ def test_two_loop_inverts_unrolled_bfgs():
     np.testing.assert_allclose(B @ m.S[-1], m.Y[-1], rtol=1e-10, atol=1e-12)
 
 
+def _dense_bfgs(d, pairs):
+    """Textbook BFGS recursion on dense matrices (Nocedal-Wright Eq. 6.19):
+    B+ = B - B s s^T B / (s^T B s) + y y^T / (y^T s), from B_0 = diag(d)."""
+    B = np.diag(d).astype(float)
+    for s, y in pairs:
+        Bs = B @ s
+        B = B - np.outer(Bs, Bs) / (s @ Bs) + np.outer(y, y) / (y @ s)
+    return B
+
+
+def test_full_memory_keeps_every_pair():
+    """Sec. 6 keeps every secant pair: with the default (no bound) the model
+    after 20 updates equals the dense BFGS recursion over all 20 pairs."""
+    rng = np.random.default_rng(11)
+    n = 12
+    A = random_spd(n, rng, cond=30)
+    d = rng.uniform(0.5, 2.0, n)
+    m = P.QNModel(d)
+    pairs = []
+    for _ in range(20):
+        s = rng.standard_normal(n)
+        pairs.append((s, A @ s))
+        assert m.update(s, A @ s)
+    assert m.r == 20
+    U, V = m._Umat()
+    B = np.diag(d) + U @ U.T - V @ V.T
+    np.testing.assert_allclose(B, _dense_bfgs(d, pairs), rtol=1e-9, atol=1e-9)
+    g = rng.standard_normal(n)
+    np.testing.assert_allclose(m.H(g), np.linalg.solve(B, g), rtol=1e-8, atol=1e-10)
+
+
+def test_bounded_memory_drops_the_oldest_quarter():
+    """With a storage bound r_max = 8, the ninth pair drops the two oldest pairs
+    at once; the rebuilt unrolled B must be the BFGS matrix of exactly the kept
+    (most recent) pairs in order, the two-loop H must invert it, and the newest
+    pair must satisfy the secant condition."""
+    rng = np.random.default_rng(12)
+    n = 12
+    A = random_spd(n, rng, cond=30)
+    d = rng.uniform(0.5, 2.0, n)
+    m = P.QNModel(d, r_max=8)
+    pairs = []
+    counts = []
+    for _ in range(13):
+        s = rng.standard_normal(n)
+        pairs.append((s, A @ s))
+        assert m.update(s, A @ s)
+        counts.append(m.r)
+    # 1..8 kept, 9th -> 7 (drop 2), 10th -> 8, 11th -> 7, 12th -> 8, 13th -> 7
+    assert counts == [1, 2, 3, 4, 5, 6, 7, 8, 7, 8, 7, 8, 7]
+    kept = pairs[-7:]
+    for (s_m, y_m), (s_k, y_k) in zip(zip(m.S, m.Y), kept):
+        np.testing.assert_array_equal(s_m, s_k)
+        np.testing.assert_array_equal(y_m, y_k)
+    U, V = m._Umat()
+    B = np.diag(d) + U @ U.T - V @ V.T
+    np.testing.assert_allclose(B, _dense_bfgs(d, kept), rtol=1e-9, atol=1e-9)
+    g = rng.standard_normal(n)
+    np.testing.assert_allclose(m.H(g), np.linalg.solve(B, g), rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(B @ m.S[-1], m.Y[-1], rtol=1e-9, atol=1e-10)
+
+
 def test_mono_pqn_reduces_to_cg_without_active_constraints():
     rng = np.random.default_rng(11)
     n = 8

@@ -132,3 +132,46 @@ def test_both_ordered_terms_of_a_node_pair_share_one_evaluation():
             scale = np.abs(t * r).max() * np.abs(wn).max() * np.linalg.norm(r) + 1e-300
             assert np.abs(on_p - (r @ wn[q]) * t * r).max() <= 1e-13 * scale
             assert np.abs(on_q - (r @ wn[p]) * t * r).max() <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("grid", [(7, 14), (9, 18), (11, 22)])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_single_janus_sphere_swims_at_a_third_of_the_slip(grid, seed):
+    """A force- and torque-free sphere with surface slip s translates at
+    U = -<s> (the surface mean, by the reciprocal theorem).  For the Janus slip
+    s = -(I - n n^T) e on the hemisphere n.e >= 0 the continuum mean is -e/3,
+    so U = e/3.  On the product grid with an even number of azimuthal nodes the
+    nodes come in antipodal pairs of equal weight and the hemisphere takes one of
+    each, so the discrete mean is half the full-sphere integral of (I - n n^T) e,
+    which the rule integrates exactly: U = e/3 holds to rounding.  A flipped slip
+    sign gives -e/3, a dropped hemisphere cut 2e/3, a normal instead of tangential
+    slip 0 in the mean."""
+    e = np.random.default_rng(40 + seed).standard_normal(3)
+    e /= np.linalg.norm(e)
+    m = DenseMobility(np.array([[0.4, -1.1, 0.2]]), *grid)
+    U = m.apply(np.zeros(6), axes=e[None, :])
+    np.testing.assert_allclose(U[:3], e / 3.0, atol=1e-12)
+
+
+def test_single_janus_sphere_rotation_vanishes_under_refinement():
+    """By axial symmetry the continuum Janus sphere does not rotate (Omega = 0).
+    With the axis along the grid's pole the discrete problem keeps the grid's
+    rotational symmetry, so Omega = 0 to rounding (an even number of polar
+    nodes keeps nodes off the cut n.e = 0).  For other axes the hemisphere
+    cut breaks the symmetry at the scale of the node spacing: the error varies
+    from axis to axis, but its root mean square over a fixed set of axes must
+    fall as the grid is refined."""
+    m = DenseMobility(np.zeros((1, 3)), 8, 16)
+    for sgn in (1.0, -1.0):
+        U = m.apply(np.zeros(6), axes=np.array([[0.0, 0.0, sgn]]))
+        assert np.linalg.norm(U[3:]) < 1e-13
+        np.testing.assert_allclose(U[:3], [0.0, 0.0, sgn / 3.0], atol=1e-13)
+    E = np.random.default_rng(7).standard_normal((12, 3))
+    E /= np.linalg.norm(E, axis=1)[:, None]
+    rms = []
+    for grid in [(7, 14), (11, 22), (15, 30)]:
+        m = DenseMobility(np.zeros((1, 3)), *grid)
+        om = [np.linalg.norm(m.apply(np.zeros(6), axes=e[None, :])[3:]) for e in E]
+        rms.append(float(np.sqrt(np.mean(np.square(om)))))
+    assert rms[0] > rms[1] > rms[2]
+    assert rms[2] < 0.6 * rms[0]
