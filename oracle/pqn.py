@@ -209,6 +209,8 @@ class PQNResult:
     model: QNModel
     history: list
     extra: np.ndarray | None = None
+    resets: int = 0
+    prox_fallbacks: int = 0
 
 
 def mono_pqn(mvp, b, x0, tol=1e-8, kmax=100, d=None, pairs=(), r_max=None,
@@ -236,21 +238,24 @@ def mono_pqn(mvp, b, x0, tol=1e-8, kmax=100, d=None, pairs=(), r_max=None,
     else:
         g = np.array(g0, float)
     hist = []
+    resets = fallbacks = 0
     for k in range(kmax):
         kkt = float(np.linalg.norm(np.minimum(x, g)))
         hist.append(kkt)
         if k == 0:
             tol = max(tol, tol_rel * kkt)
         if kkt <= tol:
-            return PQNResult(x, g, k, mvps, kkt, True, model, hist, extra)
+            return PQNResult(x, g, k, mvps, kkt, True, model, hist, extra, resets, fallbacks)
         xt = x - model.H(g)
-        xh, _, _ = weighted_prox(model, xt)
+        xh, _, ok = weighted_prox(model, xt)
+        fallbacks += 0 if ok else 1
         p = xh - x
         if float(p @ g) >= 0.0:
             model.reset()
+            resets += 1
             p = np.maximum(x - g, 0.0) - x
         if not np.any(p):
-            return PQNResult(x, g, k, mvps, kkt, kkt <= tol, model, hist, extra)
+            return PQNResult(x, g, k, mvps, kkt, kkt <= tol, model, hist, extra, resets, fallbacks)
         out = mvp(p)
         mvps += 1
         Ap = out[0] if extra_mvp else out
@@ -268,7 +273,7 @@ def mono_pqn(mvp, b, x0, tol=1e-8, kmax=100, d=None, pairs=(), r_max=None,
         model.update(eta * p, eta * Ap)
     kkt = float(np.linalg.norm(np.minimum(x, g)))
     hist.append(kkt)
-    return PQNResult(x, g, kmax, mvps, kkt, kkt <= tol, model, hist, extra)
+    return PQNResult(x, g, kmax, mvps, kkt, kkt <= tol, model, hist, extra, resets, fallbacks)
 
 
 # -------------------------------------------------------------- Algorithm 4
@@ -282,6 +287,8 @@ class BiPQNResult:
     kkt: float
     converged: bool
     history: list
+    resets: int = 0
+    prox_fallbacks: int = 0
 
 
 def bi_pqn(mvp_hi, mvp_lo, b, x_init, tol=1e-8, kmax=50, kmax_inner=100,
@@ -303,6 +310,7 @@ def bi_pqn(mvp_hi, mvp_lo, b, x_init, tol=1e-8, kmax=50, kmax_inner=100,
                     tol_rel=init_forcing)
     d_inner = init.model.d
     lo = init.mvps
+    resets, fallbacks = init.resets, init.prox_fallbacks
     S_low = list(init.model.S)
     Y_low = list(init.model.Y)
     x = init.x
@@ -325,15 +333,17 @@ def bi_pqn(mvp_hi, mvp_lo, b, x_init, tol=1e-8, kmax=50, kmax_inner=100,
         kkt = float(np.linalg.norm(np.minimum(x, g)))
         hist.append(kkt)
         if kkt <= tol:
-            return BiPQNResult(x, g, k, hi, lo, kkt, True, hist)
+            return BiPQNResult(x, g, k, hi, lo, kkt, True, hist, resets, fallbacks)
         sub = mono_pqn(sub_mvp, b, x, tol=max(0.1 * tol, forcing * kkt), kmax=kmax_inner, d=d_inner,
                        pairs=list(zip(S_low, Y_low)), r_max=r_max, g0=g, extra_mvp=True)
         lo += sub.mvps
+        resets += sub.resets
+        fallbacks += sub.prox_fallbacks
         p = sub.x - x
         if float(p @ g) >= 0.0 or not np.any(p):
             p = np.maximum(x - g, 0.0) - x
             if not np.any(p):
-                return BiPQNResult(x, g, k, hi, lo, kkt, kkt <= tol, hist)
+                return BiPQNResult(x, g, k, hi, lo, kkt, kkt <= tol, hist, resets, fallbacks)
             ahp = mvp_lo(p)
             lo += 1
             a_lo_s_over_eta = ahp
@@ -360,4 +370,4 @@ def bi_pqn(mvp_hi, mvp_lo, b, x_init, tol=1e-8, kmax=50, kmax_inner=100,
         S_low, Y_low = S_hat, Y_hat
     kkt = float(np.linalg.norm(np.minimum(x, g)))
     hist.append(kkt)
-    return BiPQNResult(x, g, kmax, hi, lo, kkt, kkt <= tol, hist)
+    return BiPQNResult(x, g, kmax, hi, lo, kkt, kkt <= tol, hist, resets, fallbacks)

@@ -1198,6 +1198,7 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
     ++ctx->nlaunch, k_pqn_init<<<1, PQN_T, 0, ctx->stream>>>(pi, x0);
     LCP_TRY(run_mono(ctx, pi, mvp_low, 0, ctx->b, nullptr, tol, ctx->cfg.kmax_inner, &r0, ctx->cfg.init_forcing));
     int lo = r0.mvps, hi = 0, inner_total = r0.iterations;
+    s.resets = r0.resets;
     double t_lo = r0.t_mvp, t_hi = 0.0;
     ctx->nh = 0;
     int* nh_dev = (int*)(ctx->dscal + 62);
