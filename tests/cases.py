@@ -41,3 +41,33 @@ def rhs_oracle(mob: DenseMobility, FT, axes=None):
     if axes is not None:
         r = r + janus_slip(mob.n, mob.body, np.asarray(axes, float))
     return r.reshape(-1)
+
+
+# Relative accuracy of one GPU mobility solve inside an MVP: GMRES (or its
+# refinement) stops at a relative residual of 1e-12 on (K + P), whose condition
+# number is 2-3 on these packings; 1e-11 leaves a margin of more than 3.
+MVP_SOLVE_REL = 1e-11
+
+# Bound on the measured gap ||A_oracle x + b_oracle - (A_gpu x + b_gpu)||_2 at a
+# solution, relative to ||b||_2: both sides solve the same discrete mobility
+# problem to a relative residual of 1e-12.
+MISMATCH_REL = 1e-10
+
+
+def kkt_bound(tol, x, g_oracle, g_gpu, b, hi_mvps):
+    """Tolerance for ||min(x, A_oracle x + b)||_2 at a GPU solution x.
+
+    The GPU stops when ||min(x, g_int)||_2 <= tol for its incrementally updated
+    gradient g_int.  min(x, .) is 1-Lipschitz, so the oracle's KKT error is at
+    most tol + ||g_oracle - g_int||_2, and
+      ||g_oracle - g_int|| <= ||g_oracle - g_gpu|| + ||g_gpu - g_int||,
+    with g_gpu = A_gpu x + b_gpu one fresh GPU MVP at x (the measured operator
+    and b mismatch) and the second term the drift of g_int: each of the
+    hi_mvps + 1 MVPs that built it carries a solve error of at most
+    MVP_SOLVE_REL times its increment, and every increment eta A p is below
+    ||b|| on these packings (measured <= 2.3 %).  Returns (eps_op, mismatch).
+    tol is the solve tolerance the bound is added to (kept for the call's
+    readability; eps_op does not depend on it)."""
+    mismatch = float(np.linalg.norm(np.asarray(g_oracle) - np.asarray(g_gpu)))
+    drift = MVP_SOLVE_REL * (hi_mvps + 1) * float(np.linalg.norm(b))
+    return mismatch + drift, mismatch

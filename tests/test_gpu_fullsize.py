@@ -17,6 +17,8 @@ from oracle.lcp import kkt_abs  # noqa: E402
 from oracle.mf import MatrixFreeMobility  # noqa: E402
 from workloads import make_instance  # noqa: E402
 
+from .cases import MISMATCH_REL, kkt_bound  # noqa: E402
+
 
 def rel(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
@@ -54,5 +56,8 @@ def test_fullsize_slip_velocities_and_lcp_solution(big):
     x, st, _ = L.lcp_solve(ctx, L.LCP_BI_PQN, inst.tol)
     assert st["converged"] == 1
     Ax = D.T @ mf.apply(D @ x)          # the oracle's MVP at the GPU's solution
-    assert kkt_abs(x, Ax + b) <= 10 * inst.tol
+    g_gpu = L.lcp_apply_A(ctx, x, L.LCP_HIGH) + L.lcp_get_b(ctx)
+    eps_op, mismatch = kkt_bound(inst.tol, x, Ax + b, g_gpu, b, st["hi_mvps"])
+    assert mismatch <= MISMATCH_REL * max(1.0, np.linalg.norm(b)), (eps_op, mismatch)
+    assert kkt_abs(x, Ax + b) <= inst.tol + eps_op
     assert np.count_nonzero(x) >= 0.1 * x.size     # a non-trivial LCP

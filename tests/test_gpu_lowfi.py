@@ -22,7 +22,7 @@ from oracle.lcp import kkt_abs  # noqa: E402
 from oracle.mf import MatrixFreeMobility  # noqa: E402
 from workloads import make_instance  # noqa: E402
 
-from .cases import active_set, dense_case  # noqa: E402
+from .cases import MISMATCH_REL, active_set, dense_case, kkt_bound  # noqa: E402
 
 
 def rel(a, b):
@@ -61,7 +61,10 @@ def test_bi_pqn_with_coarse_grid_low_fidelity(index, init_forcing):
         x, st, status = L.lcp_solve(ctx, L.LCP_BI_PQN, inst.tol)
         assert status == L.LCP_OK and st["converged"] == 1 and st["lo_mvps"] >= 1
         g = A @ x + b
-        assert kkt_abs(x, g) <= 10 * inst.tol
+        g_gpu = L.lcp_apply_A(ctx, x, L.LCP_HIGH) + L.lcp_get_b(ctx)
+        eps_op, mismatch = kkt_bound(inst.tol, x, g, g_gpu, b, st["hi_mvps"])
+        assert mismatch <= MISMATCH_REL * max(1.0, np.linalg.norm(b)), mismatch
+        assert kkt_abs(x, g) <= inst.tol + eps_op
         act, amb = active_set(x, g)
         act_ref, amb_ref = active_set(xs, A @ xs + b)
         assert act - amb_ref == act_ref - amb
@@ -82,11 +85,15 @@ def test_bi_pqn_coarse_low_fidelity_64_spheres():
             x, st, _ = L.lcp_solve(ctx, L.LCP_BI_PQN, inst.tol)
             assert st["converged"] == 1
             b = L.lcp_get_b(ctx)
-            res[name] = (x, st)
+            res[name] = (x, st, L.lcp_apply_A(ctx, x, L.LCP_HIGH) + b)
         finally:
             L.lcp_destroy(ctx)
-    x = res["bie"][0]
-    assert kkt_abs(x, D.T @ mf.apply(D @ x) + b) <= 10 * inst.tol
+    x, st, g_gpu = res["bie"]
+    b_or = gaps / inst.dt + D.T @ mf.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes)
+    g = D.T @ mf.apply(D @ x) + b_or
+    eps_op, mismatch = kkt_bound(inst.tol, x, g, g_gpu, b_or, st["hi_mvps"])
+    assert mismatch <= MISMATCH_REL * max(1.0, np.linalg.norm(b_or)), mismatch
+    assert kkt_abs(x, g) <= inst.tol + eps_op
     assert res["bie"][1]["hi_mvps"] < res["rpy"][1]["hi_mvps"]
 
 

@@ -6,8 +6,10 @@ Tolerances (relative, max-norm over the compared vector):
   FP32 stresslet apply (unrefined) 1e-4    (the mixed-mode bound of the spec; measured ~1e-6)
   mobility solve, FP64 and mixed   1e-9    (GMRES tol 1e-12 on a well-conditioned second-kind system)
   RPY, D, D^T, b                   1e-12 / 1e-9
-  LCP solutions: same active set as the oracle and ||min(x, A x + b)||_2 <= 10 tol with the
-  oracle's A and b (the GPU operator differs from the oracle's by ~1e-11).
+  LCP solutions: same active set as the oracle and ||min(x, A x + b)||_2 <= tol + eps_op with
+  the oracle's A and b, eps_op = the measured gap between the oracle's gradient and a fresh GPU
+  MVP at x plus the bounded drift of the GPU's updated gradient (cases.kkt_bound); the measured
+  gap itself must stay below 1e-10 ||b||_2.
 """
 import numpy as np
 import pytest
@@ -22,7 +24,7 @@ from oracle.mf import MatrixFreeMobility  # noqa: E402
 from oracle.rpy import rpy_matrix  # noqa: E402
 from workloads import make_instance  # noqa: E402
 
-from .cases import active_set, dense_case, rhs_oracle  # noqa: E402
+from .cases import MISMATCH_REL, active_set, dense_case, kkt_bound, rhs_oracle  # noqa: E402
 
 DEV = "cuda"
 
@@ -137,10 +139,13 @@ def test_rpy_and_apply_A(c1):
     assert rel(L.lcp_apply_A(ctx, x, L.LCP_LOW_RPY), case["Ahat"] @ x) <= 1e-12
 
 
-def check_solution(case, x, tol):
+def check_solution(case, x, tol, ctx, hi_mvps):
     A, b, xs = case["A"], case["b"], case["x"]
     g = A @ x + b
-    assert kkt_abs(x, g) <= 10 * tol, kkt_abs(x, g)
+    g_gpu = L.lcp_apply_A(ctx, x, L.LCP_HIGH) + L.lcp_get_b(ctx)
+    eps_op, mismatch = kkt_bound(tol, x, g, g_gpu, b, hi_mvps)
+    assert mismatch <= MISMATCH_REL * max(1.0, np.linalg.norm(b)), mismatch
+    assert kkt_abs(x, g) <= tol + eps_op, (kkt_abs(x, g), eps_op)
     act, amb = active_set(x, g)
     act_ref, amb_ref = active_set(xs, A @ xs + b)
     assert act - amb_ref == act_ref - amb, (sorted(act), sorted(act_ref))
@@ -157,7 +162,7 @@ def test_lcp_solve_matches_oracle(index, method, precision):
     try:
         x, st, status = L.lcp_solve(ctx, method, inst.tol)
         assert status == L.LCP_OK and st["converged"] == 1
-        check_solution(case, x, inst.tol)
+        check_solution(case, x, inst.tol, ctx, st["hi_mvps"])
         assert st["hi_mvps"] >= 1
         if method == L.LCP_BI_PQN:
             assert st["lo_mvps"] >= 1
@@ -173,7 +178,7 @@ def test_lcp_solve_device_pointers_and_warm_start():
         n = case["b"].size
         x = torch.empty(n, dtype=torch.float64, device=DEV)
         st, _ = L.lcp_solve_dev(ctx, L.LCP_MONO_PQN, inst.tol, None, x)
-        check_solution(case, x.cpu().numpy(), inst.tol)
+        check_solution(case, x.cpu().numpy(), inst.tol, ctx, st["hi_mvps"])
         # warm start at the solution: one MVP, no iteration
         x2 = torch.empty_like(x)
         st2, _ = L.lcp_solve_dev(ctx, L.LCP_MONO_PQN, inst.tol, x, x2)
@@ -283,7 +288,7 @@ def test_bb_pgd_baseline_matches_oracle(index):
     ctx = L.lcp_setup(L.config_for(inst), inst.centers, inst.axes)
     try:
         x, st, _ = L.lcp_solve(ctx, L.LCP_BB_PGD, inst.tol)
-        check_solution(case, x, inst.tol)
+        check_solution(case, x, inst.tol, ctx, st["hi_mvps"])
         _, _, it, mvps, ok = bb_pgd(lambda v: case["A"] @ v, case["b"], np.zeros(case["b"].size),
                                     tau0=3 * np.pi * inst.viscosity * inst.radius, tol=inst.tol)
         assert ok and abs(st["hi_mvps"] - mvps) <= 1
