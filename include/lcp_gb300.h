@@ -289,7 +289,10 @@ LCP_API int lcp_rigid_velocity_dev(lcp_ctx* ctx, const double* phi, double* UO);
  * Larger sizes return LCP_ERR_INVALID_ARG; the message is available from
  * lcp_last_error(NULL).
  * The first call on a device looks up the scratch area's device address;
- * make that first call before any stream capture.  All calls share the
+ * make that first call before any stream capture.  The address (like the
+ * raised shared-memory limits of the pair kernels) is kept for the life of
+ * the process and does not survive cudaDeviceReset: do not call this entry
+ * point after a reset of a device it has used.  All calls share the
  * scratch area: calls whose GPU work may overlap (other streams or threads
  * without ordering) race and must be serialised by the caller. */
 LCP_API int lcp_stokes_apply_noalloc(int n_bodies, int n_theta, int n_phi, double radius, const double* centers,

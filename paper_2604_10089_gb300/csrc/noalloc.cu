@@ -42,7 +42,9 @@ constexpr size_t NA_BYTES = OFF_PART + al(sizeof(double) * 3 * NA_MAX_NODES * NA
 // The fixed scratch area (about 1.8 MB).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
-// Device address of the scratch area, looked up once per device.
+// Device address of the scratch area, looked up once per device and kept for
+// the life of the process (a cudaDeviceReset invalidates it; the header tells
+// callers not to use this entry point on a device after a reset).
 static int scratch_address(int dev, unsigned char** out) {
   static std::mutex mu;
   static unsigned char* addr[64] = {nullptr};
