@@ -39,12 +39,6 @@ FLOPS_PER_PAIR = 32
 # (FMA) x 2.070 GHz maximum SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
-# Mobility solves per LCP solve used to scale the reference arm's per-apply sample,
-# in fine-grid units, for the bench's default configuration: the U_nc slip solve,
-# the 3 high-fidelity MVPs of Bi-PQN with the 8 x 16 low-fidelity grid, and its 27
-# low-fidelity solves at (128/242)^2 x 15/40 of a fine solve each (measured on this
-# workload).
-REFERENCE_SOLVES_PER_LCP = 6.8
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # FP32 pair kernel at 216 spheres x 242 nodes, from an ncu capture, with the SHA-1 of
 # the device code it was taken on (reported as null once that code changes; the
@@ -375,14 +369,9 @@ def run_ours(args, rank, world, local):
                "fp32_ops_per_pair_note": "double-FP32 arithmetic, ~250 FP32 operations per ordered pair"
                                          + (", one evaluation per unordered pair (symmetric)" if sym_df else ""),
                "pairs_per_s": pairs / (tdf / cdf / 1e3), "share_of_timed_region": tdf / 1e3 / t_total}
-    lowfi_desc = ("rpy" if not lowfi else
-                  f"boundary integral on a {lowfi['lowfi_n_theta']}x{lowfi['lowfi_n_phi']} grid, FP32 GMRES to "
-                  f"{lowfi.get('lowfi_tol', 1e-6):g}, initialisation to {lowfi.get('init_forcing', 0.0):g} of its "
-                  f"initial KKT error")
+    lowfi_desc = lowfi_description(lowfi)
     return dict(t_total=t_total, lat=lat, clocks=clk, launches=launches, roof=roof, k64=k64, kdf=kdf, e2e=e2e, traj=traj,
-                lowfi=lowfi_desc,
-                lowfi_ns_ratio=(lowfi["lowfi_n_theta"] * lowfi["lowfi_n_phi"] / (insts[0].n_theta * insts[0].n_phi)
-                                if lowfi else 0.0),
+                lowfi=lowfi_desc, lowfi_cfg=lowfi,
                 comparison=comparison,
                 fp64=fp64, summary=summary, N=N, M=M)
 
@@ -554,57 +543,166 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_oracle_rate(workload: str, index: int, mobility_solves_per_lcp: float, budget_s: float = 20.0):
-    """Oracle (plain C, FP64, all host cores) on a bounded sample of the workload.
+# Mean high- and low-fidelity MVPs per LCP solve of the GPU path on this workload (mixed
+# Bi-PQN, 8 x 16 coarse-grid low fidelity): the mean over the 20 timed solves of a GPU
+# bench run.  The reference arm has no GPU, so it takes its solve count from here; the
+# main arm uses the counts it measures itself.
+REFERENCE_MVPS = {"hi": 3.2, "lo": 18.3,
+                  "source": "mean over the 20 timed solves of a GB300 bench run at spheres216_grid11x22 "
+                            "(mixed Bi-PQN, 8 x 16 low fidelity)"}
 
-    Sample: matrix-free applications of K + P for one configuration; the rate is
-    scaled to LCP solves with the GMRES iterations the oracle needs per mobility
-    solve (measured on a short solve) times the mobility solves per LCP solve.
+
+def oracle_mobility_solves(workload: str, index: int, lowfi: dict, coarse_solves: int = 1, fine: bool = True):
+    """Complete oracle mobility solves (plain C, FP64, all host cores), timed.
+
+    fine: the U_nc slip solve of one configuration on the workload's grid, FP64 GMRES
+    to 1e-12 (one high-fidelity solve of the LCP path).  Then `coarse_solves` complete
+    low-fidelity solves with random forces: GMRES to the low fidelity's tolerance on
+    its coarse grid, or the RPY pair mobility when the low fidelity is RPY.
     """
     from oracle.mf import MatrixFreeMobility
+    from oracle.rpy import rpy_matrix
     from workloads import make_instance
 
     inst = make_instance(workload, index)
-    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, tol=1e-12)
-    phi = np.random.default_rng(0).standard_normal(3 * mf.x.shape[0])
+    out = {"cores": len(os.sched_getaffinity(0))}
+    if fine:
+        mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, tol=1e-12)
+        t0 = time.perf_counter()
+        mf.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes)
+        out["fine_seconds"] = time.perf_counter() - t0
+        out["fine_gmres_iterations"] = mf.last_iterations
+    rng = np.random.default_rng(1000 + index)
+    times, iters = [], []
+    if lowfi:
+        mc = MatrixFreeMobility(inst.centers, lowfi["lowfi_n_theta"], lowfi["lowfi_n_phi"], a=inst.radius,
+                                tol=lowfi.get("lowfi_tol", 1e-6))
+    for _ in range(coarse_solves):
+        FT = rng.standard_normal(6 * inst.n_bodies)
+        t0 = time.perf_counter()
+        if lowfi:
+            mc.apply(FT)
+            iters.append(mc.last_iterations)
+        else:
+            rpy_matrix(inst.centers, a=inst.radius, mu=inst.viscosity) @ FT
+        times.append(time.perf_counter() - t0)
+    out["coarse_seconds"] = times
+    out["coarse_gmres_iterations"] = iters
+    return out
+
+
+def oracle_lcp_rate(fine_s: float, coarse_s: float, hi: float, lo: float) -> float:
+    """LCP solves/s of the oracle on this path: one slip solve plus `hi` high-fidelity
+    MVPs at the measured fine-solve time, `lo` low-fidelity MVPs at the coarse one."""
+    return 1.0 / ((1.0 + hi) * fine_s + lo * coarse_s)
+
+
+def c1_oracle_solve(index: int = 1) -> dict:
+    """One complete oracle collision resolution at 8 spheres (7 x 14 nodes): dense K + P by
+    LU, dense M and A = D^T M D, the slip solve for b, and the LCP by projected Gauss-Seidel."""
+    from oracle.bie import DenseMobility
+    from oracle.contacts import contact_matrix, detect_contacts
+    from oracle.lcp import kkt_abs, lcp_data, pgs
+    from workloads import make_instance
+
+    inst = make_instance("spheres8_grid7x14", index)
     t0 = time.perf_counter()
-    applies = 0
-    while True:
-        mf.apply_operator(phi)
-        applies += 1
-        if time.perf_counter() - t0 > budget_s or applies >= 50:
-            break
-    t_apply = (time.perf_counter() - t0) / applies
-    gmres_per_solve = 40.0   # measured on the workload's packings (FP64 GMRES to 1e-12)
-    t_solve = t_apply * gmres_per_solve * mobility_solves_per_lcp
-    cores = len(os.sched_getaffinity(0))
-    return {"value": 1.0 / t_solve, "unit": "LCP solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{applies} matrix-free FP64 K+P applications of one {workload} configuration "
-                      f"({t_apply:.3f} s each), scaled by {gmres_per_solve:.0f} GMRES iterations per mobility "
-                      f"solve and {mobility_solves_per_lcp:.1f} mobility solves per LCP solve",
-            "seconds_per_apply": t_apply}
+    mob = DenseMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, mu=inst.viscosity)
+    pairs, normals, gaps = detect_contacts(inst.centers, inst.contact_radius, inst.delta)
+    D = contact_matrix(inst.n_bodies, pairs, normals)
+    A, b = lcp_data(D, mob.matrix(), mob.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes), gaps, inst.dt)
+    x = pgs(A, b)
+    t = time.perf_counter() - t0
+    return {"seconds": t, "contacts": int(b.size), "active": int((x > 0).sum()),
+            "kkt": float(kkt_abs(x, A @ x + b)), "solves_per_s": 1.0 / t}
+
+
+def c1_anchor() -> dict:
+    """The complete 8-sphere oracle solve on one core and on all host cores (subprocesses,
+    so that the BLAS thread count is fixed before numpy loads)."""
+    res = {"workload": "spheres8_grid7x14 (8 spheres, 2352 unknowns): dense LU of K + P, dense A, PGS"}
+    for name, env in (("single_core", {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1",
+                                       "MKL_NUM_THREADS": "1"}), ("all_cores", {})):
+        try:
+            out = subprocess.run([sys.executable, os.path.abspath(__file__), "--c1-oracle"], capture_output=True,
+                                 text=True, timeout=300, env={**os.environ, **env}, check=True)
+            res[name] = json.loads(out.stdout.strip().splitlines()[-1])
+        except (subprocess.SubprocessError, ValueError, IndexError) as e:
+            res[name] = {"error": str(e)[:200]}
+    res["cores"] = len(os.sched_getaffinity(0))
+    return res
+
+
+def config_dict(args, M: int, N: int, lowfi_desc: str, world: int) -> dict:
+    """The workload description both arms print."""
+    return {"workload": f"{args.workload}: {M} Janus spheres, {N} surface nodes, {3 * N} unknowns",
+            "method": f"{args.method}_pqn", "precision": args.precision, "tol": 1e-8,
+            "low_fidelity": lowfi_desc,
+            "gmres_tol": 1e-12, "step": "contacts + U_nc slip solve + b + LCP solve",
+            "l2": "inputs larger than L2 (Krylov basis 76 MB + operator sweeps per apply)",
+            "parallelism": f"instances x{world}"}
+
+
+def lowfi_description(lowfi: dict) -> str:
+    if not lowfi:
+        return "rpy"
+    return (f"boundary integral on a {lowfi['lowfi_n_theta']}x{lowfi['lowfi_n_phi']} grid, FP32 GMRES to "
+            f"{lowfi.get('lowfi_tol', 1e-6):g}, initialisation to {lowfi.get('init_forcing', 0.0):g} of its "
+            f"initial KKT error")
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores, on this workload.
+
+    Warm-up: one complete fine-grid slip solve (FP64 GMRES to 1e-12) of the first
+    configuration, timed with its iteration count.  Each further step, warm-up or timed:
+    one complete low-fidelity mobility solve of the next configuration.  The rate is one
+    LCP solve's worth of these measured solves: (1 + hi) fine solves and lo coarse ones,
+    with the GPU path's measured MVP counts on this workload (REFERENCE_MVPS).
+    """
     if rank != 0:
         return
-    steps = []
+    from workloads import make_instance
+    inst = make_instance(args.workload, 0)
+    lowfi = lowfi_overrides(args.lowfi, inst.n_theta)
+    first = oracle_mobility_solves(args.workload, 0, lowfi, coarse_solves=0)
+    coarse, iters, step_s = [], [], []
     for k in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(args.workload, k, mobility_solves_per_lcp=REFERENCE_SOLVES_PER_LCP, budget_s=0.0)
+        t0 = time.perf_counter()
+        r = oracle_mobility_solves(args.workload, 1 + k, lowfi, coarse_solves=1, fine=False)
         if k >= args.warmup:
-            steps.append(1.0 / r["value"])
-    value = len(steps) / sum(steps)
+            coarse.extend(r["coarse_seconds"])
+            iters.extend(r["coarse_gmres_iterations"])
+            step_s.append(time.perf_counter() - t0)
+    t_c = float(np.mean(coarse))
+    value = oracle_lcp_rate(first["fine_seconds"], t_c, REFERENCE_MVPS["hi"], REFERENCE_MVPS["lo"])
+    M = inst.n_bodies
+    N = inst.n_bodies * inst.n_theta * inst.n_phi
+    sample = (f"{args.steps} complete low-fidelity oracle mobility solves ({t_c:.3f} s each"
+              + (f", {np.mean(iters):.1f} GMRES iterations" if iters else "")
+              + f"), after one complete fine-grid slip solve in the warm-up ({first['fine_seconds']:.2f} s, "
+                f"{first['fine_gmres_iterations']} GMRES iterations to 1e-12); one LCP solve = "
+                f"(1 + {REFERENCE_MVPS['hi']}) fine + {REFERENCE_MVPS['lo']} low-fidelity solves "
+                f"({REFERENCE_MVPS['source']})")
+    anchor = c1_anchor()
     line = {"impl": "reference", "metric": "LCP solves/s", "value": value, "unit": "LCP solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "ms_per_step": 1e3 / value, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload},
-            "cpu_baseline": {"value": value, "unit": "LCP solves/s", "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
+            "ms_per_step": 1e3 * float(np.mean(step_s)), "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, M, N, lowfi_description(lowfi), world),
+            "cpu_baseline": {"value": value, "unit": "LCP solves/s", "cores": first["cores"], "kind": "oracle",
+                             "sample": sample, "fine_solve_seconds": first["fine_seconds"],
+                             "fine_gmres_iterations": first["fine_gmres_iterations"],
+                             "coarse_solve_seconds": t_c, "mvps_per_lcp": REFERENCE_MVPS,
+                             "c1_complete_solve": anchor},
+            "ms_per_step_note": "wall time of one sample step (one complete low-fidelity oracle solve)",
             "e2e": {"value": value, "unit": "LCP solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def main():
+    if "--c1-oracle" in sys.argv:
+        print(json.dumps(c1_oracle_solve()), flush=True)
+        return
     args = parse()
     rank, world, local = dist_info()
     if world > 1:
@@ -632,25 +730,29 @@ def main():
         s = r["summary"]
         cpu = None
         if args.cpu_baseline:
-            # mobility solves per LCP solve in fine-grid units: U_nc + high-fidelity MVPs, plus the
-            # coarse-grid low-fidelity solves at their pair-count ratio (GMRES to 1e-6: ~15 of the
-            # ~40 iterations of a 1e-12 solve)
-            per = 1.0 + float(np.mean(s["hi_mvps"]))
-            if r["lowfi_ns_ratio"]:
-                per += float(np.mean(s["lo_mvps"])) * r["lowfi_ns_ratio"] ** 2 * 15.0 / 40.0
-            cpu = cpu_oracle_rate(args.workload, 0, per)
+            # complete oracle mobility solves of this workload (one fine slip solve, two
+            # low-fidelity solves), combined with the MVP counts this run measured
+            hi, lo = float(np.mean(s["hi_mvps"])), float(np.mean(s["lo_mvps"]))
+            o = oracle_mobility_solves(args.workload, 0, r["lowfi_cfg"], coarse_solves=2)
+            t_c = float(np.mean(o["coarse_seconds"]))
+            cpu = {"value": oracle_lcp_rate(o["fine_seconds"], t_c, hi, lo), "unit": "LCP solves/s",
+                   "cores": o["cores"], "kind": "oracle",
+                   "sample": f"one complete fine-grid slip solve of a {args.workload} configuration "
+                             f"({o['fine_seconds']:.2f} s, {o['fine_gmres_iterations']} FP64 GMRES iterations to "
+                             f"1e-12) and {len(o['coarse_seconds'])} complete low-fidelity solves ({t_c:.3f} s each"
+                             + (f", {np.mean(o['coarse_gmres_iterations']):.1f} GMRES iterations"
+                                if o["coarse_gmres_iterations"] else "")
+                             + f"); one LCP solve = (1 + {hi:.2f}) fine + {lo:.2f} low-fidelity solves, the mean "
+                               f"MVP counts of this run's timed solves",
+                   "fine_solve_seconds": o["fine_seconds"], "fine_gmres_iterations": o["fine_gmres_iterations"],
+                   "coarse_solve_seconds": t_c, "mvps_per_lcp": {"hi": hi, "lo": lo},
+                   "c1_complete_solve": c1_anchor()}
         line = {
             "metric": "LCP solves/s", "value": value, "unit": "LCP solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["t_total"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {r['M']} Janus spheres, {r['N']} surface nodes, "
-                                   f"{3 * r['N']} unknowns",
-                       "method": f"{args.method}_pqn", "precision": args.precision, "tol": 1e-8,
-                       "low_fidelity": r["lowfi"],
-                       "gmres_tol": 1e-12, "step": "contacts + U_nc slip solve + b + LCP solve",
-                       "l2": "inputs larger than L2 (Krylov basis 76 MB + operator sweeps per apply)",
-                       "parallelism": f"instances x{world}"},
+            "config": config_dict(args, r["M"], r["N"], r["lowfi"], world),
             "latency_s": {"p50": pct(r["lat"], 50), "p99": pct(r["lat"], 99)},
             "matvecs_per_s": {
                 "high_fidelity_mvps": float(np.sum(s["hi_mvps"])) / r["t_total"],
