@@ -45,15 +45,18 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 # hash of the symmetric kernel's file was renewed when its unit bookkeeping moved
 # to a shared header, the kernel's code unchanged).
 PAIR32_TRAFFIC = {
-    "k_pair32_sym_a4": {"file": "stokes_sym.cu", "source_sha1": "4427e4d20dd6e9c5f57c04daec13adec0fb13d50",
-                        "bytes_per_launch": 691968},
+    "k_pair32_sym_p8rc": {"file": "stokes_sym.cu", "source_sha1": "ddfaf8c02312a9c9655a89936fe3f971cc5703c5",
+                          "bytes_per_launch": 1460480},
     "k_pair32": {"file": "stokes.cu", "source_sha1": "298b391165dc32f4d22c484bf6d970a4f86ee95e",
                  "bytes_per_launch": 665088},
 }
 # FP32 operations of the symmetric kernel per unordered node pair (both ordered
 # terms): r 3, |r|^2 6, |r|^-2 1, d 3, r.d 5, t 3, r.wn_q 5, r.wn_p 5, scales 2,
-# two accumulations 12 = 45 flops (FMA = 2), i.e. 22.5 per ordered pair.
+# two accumulations 12 = 45 flops (FMA = 2), i.e. 22.5 per ordered pair; the
+# variants that take |r|^-2 from a reciprocal (names ending in "rc") do one
+# multiply fewer: 44, i.e. 22 per ordered pair.
 SYM_FLOPS_PER_ORDERED_PAIR = 22.5
+SYM_RC_FLOPS_PER_ORDERED_PAIR = 22.0
 
 
 def parse():
@@ -341,8 +344,9 @@ def run_ours(args, rank, world, local):
                 "flops_note": "algorithmic work of the operator: 32 flops per ordered node pair, N(N-1) pairs",
                 "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (nominal max clock)"}
         if variant.startswith("sym"):
-            hw = pairs * SYM_FLOPS_PER_ORDERED_PAIR / avg32 / 1e12
-            roof["kernel_flops_per_pair"] = SYM_FLOPS_PER_ORDERED_PAIR
+            fpp = SYM_RC_FLOPS_PER_ORDERED_PAIR if variant.endswith("rc") else SYM_FLOPS_PER_ORDERED_PAIR
+            hw = pairs * fpp / avg32 / 1e12
+            roof["kernel_flops_per_pair"] = fpp
             roof["executed_tflops"] = hw
             roof["executed_frac"] = hw / FP32_PEAK_TFLOPS
             roof["symmetric_note"] = ("one evaluation serves both ordered terms of a node pair; "

@@ -22,6 +22,7 @@
 // (FP32) that the finish kernel adds in target-block order.  Forward sums are
 // FP64 per thread (shared memory) and go to partial[slot][p].  Everything is
 // deterministic.
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -29,12 +30,11 @@
 
 namespace {
 
-constexpr int SYM_THREADS = 128;
-constexpr int SYM_TPT = 4;                         // targets per thread (two FP32x2 packs)
-static_assert(SYM_TPT * SYM_THREADS == SYM_TB, "target block of the symmetric units");
-constexpr int SYM_WARPS = SYM_THREADS / 32;
 constexpr int SYM_CHUNK = 2;                       // source bodies staged per tile
 constexpr float SYM_EPS = 1e-20f;   // r = 0 only for q = p: keeps |r|^-3 = 1e30 finite, the term 0
+// With |r|^-2 from a reciprocal, |r|^-4 = eps^-2 must stay finite at r = 0:
+// 1e-12 perturbs |r|^2 >= 1e-2 (node spacing) by at most 1e-10 relative.
+constexpr float SYM_EPS_RC = 1e-12f;
 
 __device__ __forceinline__ float rsqrt_fast(float x) {
   float y;
@@ -43,26 +43,44 @@ __device__ __forceinline__ float rsqrt_fast(float x) {
 }
 
 
+__device__ __forceinline__ float rcp_fast(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Two targets (the lanes of e, nf, wp) against one source (duplicated in the
-// lanes of n*, w*, f*).  acc += forward terms, rv += reverse terms.
+// lanes of n*, w*, f*).  acc += forward terms, rv += reverse terms.  RC: take
+// |r|^-2 from a second special-function reciprocal instead of squaring |r|^-1,
+// one FP32x2 multiply fewer per pair (the special-function unit has room).
+template <bool RC>
 __device__ __forceinline__ void sym_pair(const float2 (&e)[3], const float2 (&nf)[3], const float2 (&wp)[3],
                                          float2 nx, float2 ny, float2 nz, float2 wx, float2 wy, float2 wz,
                                          float2 fx, float2 fy, float2 fz, float2 (&acc)[3], float2 (&rv)[3]) {
   const float2 rx = __fadd2_rn(e[0], nx);
   const float2 ry = __fadd2_rn(e[1], ny);
   const float2 rz = __fadd2_rn(e[2], nz);
-  float2 r2 = __ffma2_rn(rx, rx, make_float2(SYM_EPS, SYM_EPS));
+  constexpr float eps = RC ? SYM_EPS_RC : SYM_EPS;
+  float2 r2 = __ffma2_rn(rx, rx, make_float2(eps, eps));
   r2 = __ffma2_rn(ry, ry, r2);
   r2 = __ffma2_rn(rz, rz, r2);
   const float2 ir = make_float2(rsqrt_fast(r2.x), rsqrt_fast(r2.y));
-  const float2 i2 = __fmul2_rn(ir, ir);
   const float2 dx = __fadd2_rn(fx, nf[0]);
   const float2 dy = __fadd2_rn(fy, nf[1]);
   const float2 dz = __fadd2_rn(fz, nf[2]);
   float2 rd = __fmul2_rn(rx, dx);
   rd = __ffma2_rn(ry, dy, rd);
   rd = __ffma2_rn(rz, dz, rd);
-  const float2 t = __fmul2_rn(__fmul2_rn(rd, i2), __fmul2_rn(i2, ir));
+  float2 t;
+  if (RC) {
+    // at r = 0 (a node with itself) rd = 0 and |r|^-4 = SYM_EPS_RC^-2 stays
+    // finite, so t = 0
+    const float2 i2 = make_float2(rcp_fast(r2.x), rcp_fast(r2.y));
+    t = __fmul2_rn(__fmul2_rn(rd, ir), __fmul2_rn(i2, i2));
+  } else {
+    const float2 i2 = __fmul2_rn(ir, ir);
+    t = __fmul2_rn(__fmul2_rn(rd, i2), __fmul2_rn(i2, ir));
+  }
   float2 rq = __fmul2_rn(rx, wx);
   rq = __ffma2_rn(ry, wy, rq);
   rq = __ffma2_rn(rz, wz, rq);
@@ -77,6 +95,16 @@ __device__ __forceinline__ void sym_pair(const float2 (&e)[3], const float2 (&nf
   rv[0] = __ffma2_rn(sr, rx, rv[0]);
   rv[1] = __ffma2_rn(sr, ry, rv[1]);
   rv[2] = __ffma2_rn(sr, rz, rv[2]);
+}
+
+// Add a to the compensated sum (hi, lo) (Knuth's TwoSum: the rounding error of
+// hi + a is recovered exactly and collected in lo).
+__device__ __forceinline__ void two_sum_acc(float2& s, float a) {
+  const float h = __fadd_rn(s.x, a);
+  const float bp = __fsub_rn(h, s.x);
+  const float err = __fadd_rn(__fsub_rn(s.x, __fsub_rn(h, bp)), __fsub_rn(a, bp));
+  s.x = h;
+  s.y = __fadd_rn(s.y, err);
 }
 
 // Sum NV values (NV = 8 or 16) over the 32 lanes of a warp: at each of the
@@ -113,12 +141,23 @@ __device__ __forceinline__ float warp_transpose_sum(const float (&v)[NV], int la
 //   BATCH: sources per warp reduction (2 or 4);
 //   MINB:  CTAs per SM the registers are sized for (4: 128, 3: 168 registers);
 //   PIPE:  reduce the previous batch after computing the current one, so
-//          the shuffle latency overlaps the arithmetic.
-template <bool AOS, int BATCH, int MINB, bool PIPE>
+//          the shuffle latency overlaps the arithmetic;
+//   TPT, THR: targets per thread and CTA size (TPT x THR = SYM_TB);
+//   CT:    source template (duplicated (v, v) pairs, AOS order) read from the
+//          launch's parameter block `tpar` (constant bank: every lane reads the
+//          same source) instead of shared memory;
+//   RC:    |r|^-2 by a special-function reciprocal (see sym_pair);
+//   CF:    forward sums carried across source bodies as compensated FP32
+//          (hi, lo) pairs instead of FP64 adds (FP64 runs at 1/64 rate).
+template <bool AOS, int BATCH, int MINB, bool PIPE, int TPT, int THR, bool CT, bool RC, bool CF>
 __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUnits su,
                                                 const float* __restrict__ tmpl32, const float* __restrict__ c32,
                                                 const float* __restrict__ phi32, double* __restrict__ partial,
-                                                float* __restrict__ rev) {
+                                                float* __restrict__ rev, const float2* tpar) {
+  static_assert(!CT || AOS, "the parameter-block template is in record order");
+  static_assert(TPT * THR == SYM_TB && TPT % 2 == 0, "a thread's targets fill FP32x2 packs of the block");
+  constexpr int NPK = TPT / 2;       // FP32x2 packs of targets per thread
+  constexpr int WARPS = THR / 32;
   constexpr int NV = BATCH == 8 ? 32 : (BATCH == 4 ? 16 : 8);
   constexpr int LPV = 32 / NV;   // lanes holding each reduced value
   extern __shared__ float4 smem4[];
@@ -126,11 +165,12 @@ __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUn
   //      s_f [SYM_CHUNK][ns_pad][2] float4 = (fx,fx,fy,fy) (fz,fz,0,0)
   // SoA: s_t [6][ns_pad] float2; s_f [3][SYM_CHUNK][ns_pad] float2
   float2* s_t = reinterpret_cast<float2*>(smem4);
-  float2* s_f = s_t + 6 * ns_pad;
+  float2* s_f = s_t + (CT ? 0 : 6 * ns_pad);
   const int f_len = AOS ? 4 * SYM_CHUNK * ns_pad : 3 * SYM_CHUNK * ns_pad;   // float2 entries
-  float* s_rev = reinterpret_cast<float*>(s_f + f_len);                      // [SYM_WARPS][3][ns_pad]
-  double* s_fwd = reinterpret_cast<double*>(s_rev + SYM_WARPS * 3 * ns_pad);   // [SYM_TPT][3][SYM_THREADS]
-  for (int q = threadIdx.x; q < ns_pad; q += blockDim.x) {
+  float* s_rev = reinterpret_cast<float*>(s_f + f_len);                      // [WARPS][3][ns_pad]
+  double* s_fwd = reinterpret_cast<double*>(s_rev + WARPS * 3 * ns_pad);       // [TPT][3][THR]
+  float2* s_fwc = reinterpret_cast<float2*>(s_fwd);                              // CF: (hi, lo) in the same slots
+  for (int q = threadIdx.x; q < (CT ? 0 : ns_pad); q += blockDim.x) {
     const bool real = q < ns;
     for (int d = 0; d < 3; d++) {
       const float x = real ? -tmpl32[d * ns + q] : (d == 0 ? -1.0e3f : 0.f);
@@ -162,15 +202,18 @@ __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUn
     const int slot = c - su.cta_of(su.off[tb]);
     u = seg_end;
 
-    int pb[SYM_TPT], pq[SYM_TPT];   // body (INT_MAX past the end) and template node of each target
+    int pb[TPT], pq[TPT];   // body (INT_MAX past the end) and template node of each target
 #pragma unroll
-    for (int t = 0; t < SYM_TPT; t++) {
-      const int p = tb * SYM_TB + t * SYM_THREADS + threadIdx.x;
+    for (int t = 0; t < TPT; t++) {
+      const int p = tb * SYM_TB + t * THR + threadIdx.x;
       const int pc = p < N ? p : N - 1;
       const int bi = pc / ns;
       pb[t] = p < N ? bi : 0x7fffffff;
       pq[t] = pc - bi * ns;
-      for (int d = 0; d < 3; d++) s_fwd[(t * 3 + d) * SYM_THREADS + threadIdx.x] = 0.0;
+      for (int d = 0; d < 3; d++) {
+        if (CF) s_fwc[(t * 3 + d) * THR + threadIdx.x] = make_float2(0.f, 0.f);
+        else s_fwd[(t * 3 + d) * THR + threadIdx.x] = 0.0;
+      }
     }
     for (int jc = j0; jc < j1; jc += SYM_CHUNK) {
       const int nb = min(SYM_CHUNK, j1 - jc);
@@ -195,9 +238,9 @@ __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUn
         const float4 cjh = *reinterpret_cast<const float4*>(c32 + 8 * j);
         const float4 cjl = *reinterpret_cast<const float4*>(c32 + 8 * j + 4);
         // per pack k: targets 2k (lane x) and 2k+1 (lane y)
-        float2 e[2][3], nf[2][3], wp[2][3], acc[2][3];
+        float2 e[NPK][3], nf[NPK][3], wp[NPK][3], acc[NPK][3];
 #pragma unroll
-        for (int t = 0; t < SYM_TPT; t++) {
+        for (int t = 0; t < TPT; t++) {
           const int k = t >> 1;
           const int bi = pb[t] == 0x7fffffff ? (N - 1) / ns : pb[t];
           const float4 cih = *reinterpret_cast<const float4*>(c32 + 8 * bi);
@@ -236,7 +279,7 @@ __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUn
             float2 rv[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             float2 nx, ny, nz, wx, wy, wz, fx, fy, fz;
             if (AOS) {
-              const float4* t4 = reinterpret_cast<const float4*>(s_t) + 3 * qq;
+              const float4* t4 = reinterpret_cast<const float4*>(CT ? tpar : s_t) + 3 * qq;
               const float4 A = t4[0], B = t4[1], C = t4[2];
               nx = make_float2(A.x, A.y); ny = make_float2(A.z, A.w);
               nz = make_float2(B.x, B.y); wx = make_float2(B.z, B.w);
@@ -252,9 +295,9 @@ __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUn
               fz = s_f[(2 * SYM_CHUNK + b) * ns_pad + qq];
             }
 #pragma unroll
-            for (int k = 0; k < 2; k++) sym_pair(e[k], nf[k], wp[k], nx, ny, nz, wx, wy, wz, fx, fy, fz, acc[k], rv);
+            for (int k = 0; k < NPK; k++) sym_pair<RC>(e[k], nf[k], wp[k], nx, ny, nz, wx, wy, wz, fx, fy, fz, acc[k], rv);
 #pragma unroll
-            for (int d = 0; d < 3; d++) v[3 * h + d] = rv[d].x + rv[d].y;   // the thread's four targets
+            for (int d = 0; d < 3; d++) v[3 * h + d] = rv[d].x + rv[d].y;   // the thread's TPT targets
           }
 #pragma unroll
           for (int k = 3 * BATCH; k < NV; k++) v[k] = 0.f;
@@ -282,11 +325,12 @@ __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUn
           if (lane % LPV == 0 && k < 3 * BATCH) rout[(k % 3) * ns_pad + qp + k / 3] = tot;
         }
 #pragma unroll
-        for (int t = 0; t < SYM_TPT; t++)
+        for (int t = 0; t < TPT; t++)
           if (pb[t] <= j)
             for (int d = 0; d < 3; d++) {
               const float a = (t & 1) ? acc[t >> 1][d].y : acc[t >> 1][d].x;
-              s_fwd[(t * 3 + d) * SYM_THREADS + threadIdx.x] += (double)a;
+              if (CF) two_sum_acc(s_fwc[(t * 3 + d) * THR + threadIdx.x], a);
+              else s_fwd[(t * 3 + d) * THR + threadIdx.x] += (double)a;
             }
         if (any_rev) {
           __syncthreads();
@@ -296,7 +340,7 @@ __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUn
             const int q = k / 3, d = k - 3 * q;
             float s = 0.f;
 #pragma unroll
-            for (int w = 0; w < SYM_WARPS; w++) s += s_rev[(w * 3 + d) * ns_pad + q];
+            for (int w = 0; w < WARPS; w++) s += s_rev[(w * 3 + d) * ns_pad + q];
             dst[k] = s;
           }
           __syncthreads();
@@ -304,43 +348,83 @@ __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUn
       }
     }
 #pragma unroll
-    for (int t = 0; t < SYM_TPT; t++) {
-      const int p = tb * SYM_TB + t * SYM_THREADS + threadIdx.x;
+    for (int t = 0; t < TPT; t++) {
+      const int p = tb * SYM_TB + t * THR + threadIdx.x;
       if (p < N) {
         double* o = partial + ((size_t)slot * N + p) * 3;
-        for (int d = 0; d < 3; d++) o[d] = s_fwd[(t * 3 + d) * SYM_THREADS + threadIdx.x];
+        for (int d = 0; d < 3; d++) {
+          if (CF) {
+            const float2 h = s_fwc[(t * 3 + d) * THR + threadIdx.x];
+            o[d] = (double)h.x + (double)h.y;
+          } else {
+            o[d] = s_fwd[(t * 3 + d) * THR + threadIdx.x];
+          }
+        }
       }
     }
   }
 }
 
-#define PAIR32_SYM_VARIANT(NAME, AOS, BATCH, MINB, PIPE)                                                        \
-  __global__ void __launch_bounds__(SYM_THREADS, MINB)                                                          \
+#define PAIR32_SYM_VARIANT(NAME, AOS, BATCH, MINB, PIPE, TPT, THR)                                             \
+  __global__ void __launch_bounds__(THR, MINB)                                                                  \
       NAME(int N, int ns, int ns_pad, SymUnits su, const float* __restrict__ tmpl32, const float* __restrict__ c32, \
            const float* __restrict__ phi32, double* __restrict__ partial, float* __restrict__ rev) {               \
-    pair32_sym_body<AOS, BATCH, MINB, PIPE>(N, ns, ns_pad, su, tmpl32, c32, phi32, partial, rev);                 \
+    pair32_sym_body<AOS, BATCH, MINB, PIPE, TPT, THR, false, false, false>(N, ns, ns_pad, su, tmpl32, c32, phi32,  \
+                                                                           partial, rev, nullptr);                 \
+  }
+// variants that take the source template from their parameter block
+#define PAIR32_SYM_VARIANT_P(NAME, BATCH, MINB, TPT, THR, RC, CF)                                               \
+  __global__ void __launch_bounds__(THR, MINB)                                                                  \
+      NAME(int N, int ns, int ns_pad, SymUnits su, const float* __restrict__ tmpl32, const float* __restrict__ c32, \
+           const float* __restrict__ phi32, double* __restrict__ partial, float* __restrict__ rev,                 \
+           const __grid_constant__ SymTmplParam tp) {                                                              \
+    pair32_sym_body<true, BATCH, MINB, false, TPT, THR, true, RC, CF>(N, ns, ns_pad, su, tmpl32, c32, phi32,      \
+                                                                      partial, rev,                               \
+                                                                      reinterpret_cast<const float2*>(tp.v));     \
   }
 // Measured at 216 spheres x 242 nodes (ms per launch): sym_a4 1.69, sym_a4m4
 // 1.67, sym_a8m2 1.70, sym_a2 1.75, sym 1.86, pipelined variants 1.84-1.96;
 // the plain kernel 1.97.  At 64 spheres x 162 nodes: sym_a4 0.100, sym_a8m2
 // 0.103, sym_a4m4 0.114 (plain 0.100).
-PAIR32_SYM_VARIANT(k_pair32_sym_a4, true, 4, 3, false)
-PAIR32_SYM_VARIANT(k_pair32_sym_a4m4, true, 4, 4, false)
-PAIR32_SYM_VARIANT(k_pair32_sym_a8m2, true, 8, 2, false)
-PAIR32_SYM_VARIANT(k_pair32_sym_a2, true, 2, 4, false)
-PAIR32_SYM_VARIANT(k_pair32_sym, false, 2, 4, false)
+PAIR32_SYM_VARIANT(k_pair32_sym_a4, true, 4, 3, false, 4, 128)
+PAIR32_SYM_VARIANT(k_pair32_sym_a4m4, true, 4, 4, false, 4, 128)
+PAIR32_SYM_VARIANT(k_pair32_sym_a8m2, true, 8, 2, false, 4, 128)
+PAIR32_SYM_VARIANT(k_pair32_sym_a2, true, 2, 4, false, 4, 128)
+PAIR32_SYM_VARIANT(k_pair32_sym, false, 2, 4, false, 4, 128)
+// eight targets per thread (four FP32x2 packs) in CTAs of 64 threads: twice
+// the independent chains per warp and half the reduction work per pair
+// (216 spheres: t8b4 1.63, t8b2 1.65 ms)
+PAIR32_SYM_VARIANT(k_pair32_sym_t8b2, true, 2, 4, false, 8, 64)
+PAIR32_SYM_VARIANT(k_pair32_sym_t8b4, true, 4, 3, false, 8, 64)
+// Template in the parameter block, |r|^-2 by reciprocal, compensated forward
+// sums; measured at 216 spheres (ms): eight targets per thread 1.60 with the
+// template alone, 1.57 with the reciprocal, 1.54 with both and the compensated
+// sums (sym_p8rc, the default); four targets per thread 1.61 (sym_p4rc); two
+// sources per reduction 1.69.
+PAIR32_SYM_VARIANT_P(k_pair32_sym_p8rc, 4, 3, 8, 64, true, true)
+PAIR32_SYM_VARIANT_P(k_pair32_sym_p4rc, 4, 3, 4, 128, true, true)
 
 typedef void (*Pair32SymKernel)(int, int, int, SymUnits, const float*, const float*, const float*, double*, float*);
+typedef void (*Pair32SymKernelP)(int, int, int, SymUnits, const float*, const float*, const float*, double*, float*,
+                                 SymTmplParam);
 struct Pair32SymVariant {
-  Pair32SymKernel kernel;
+  Pair32SymKernel kernel;     // template from shared memory, or
+  Pair32SymKernelP kernel_p;  // template from the parameter block
   bool aos;
-  int batch;   // sources per warp reduction: node padding is a multiple of max(4, batch)
+  int batch;     // sources per warp reduction: node padding is a multiple of max(4, batch)
+  int threads;   // CTA size; targets per thread = SYM_TB / threads
   const char* name;
 };
 static const Pair32SymVariant kSymVariants[] = {
-    {k_pair32_sym_a4, true, 4, "sym_a4"},     {k_pair32_sym_a4m4, true, 4, "sym_a4m4"},
-    {k_pair32_sym_a8m2, true, 8, "sym_a8m2"}, {k_pair32_sym_a2, true, 2, "sym_a2"},
-    {k_pair32_sym, false, 2, "sym"}};
+    {k_pair32_sym_a4, nullptr, true, 4, 128, "sym_a4"},
+    {k_pair32_sym_a4m4, nullptr, true, 4, 128, "sym_a4m4"},
+    {k_pair32_sym_a8m2, nullptr, true, 8, 128, "sym_a8m2"},
+    {k_pair32_sym_a2, nullptr, true, 2, 128, "sym_a2"},
+    {k_pair32_sym, nullptr, false, 2, 128, "sym"},
+    {k_pair32_sym_t8b2, nullptr, true, 2, 64, "sym_t8b2"},
+    {k_pair32_sym_t8b4, nullptr, true, 4, 64, "sym_t8b4"},
+    {nullptr, k_pair32_sym_p8rc, true, 4, 64, "sym_p8rc"},
+    {nullptr, k_pair32_sym_p4rc, true, 4, 128, "sym_p4rc"}};
 constexpr int kNumSymVariants = sizeof(kSymVariants) / sizeof(kSymVariants[0]);
 
 // out_p = forward partials + reverse rows of the target blocks before body(p)
@@ -390,8 +474,9 @@ static int sym_ns_pad(int ns, int v) {
 static size_t sym_smem(int ns, int v) {
   const int ns_pad = sym_ns_pad(ns, v);
   const bool aos = kSymVariants[v].aos;
-  return sizeof(float2) * ((size_t)6 * ns_pad + (aos ? 4 : 3) * SYM_CHUNK * ns_pad) +
-         sizeof(float) * SYM_WARPS * 3 * ns_pad + sizeof(double) * SYM_TPT * 3 * SYM_THREADS;
+  const size_t t_len = kSymVariants[v].kernel_p ? 0 : (size_t)6 * ns_pad;   // template in the parameter block
+  return sizeof(float2) * (t_len + (aos ? 4 : 3) * SYM_CHUNK * ns_pad) +
+         sizeof(float) * (kSymVariants[v].threads / 32) * 3 * ns_pad + sizeof(double) * 3 * SYM_TB;
 }
 
 int stokes_sym_df_configure(lcp_ctx* ctx, const int* off, int ntb);
@@ -439,12 +524,38 @@ int stokes_sym_configure(lcp_ctx* ctx) {
     ctx->sym = false;
     return LCP_OK;
   }
-  for (int v = 0; v < kNumSymVariants && v < 8; v++) {
+  // the source template as a launch parameter block (duplicated pairs, record order)
+  const bool tparam_ok = ns <= SYM_TPARAM_NODES;
+  if (tparam_ok) {
+    std::vector<float> t32((size_t)6 * ns);
+    LCP_CUDA(cudaMemcpyAsync(t32.data(), ctx->tmpl32, sizeof(float) * 6 * ns, cudaMemcpyDeviceToHost, ctx->stream));
+    LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->sym_tparam.assign(sizeof(SymTmplParam) / sizeof(float4), make_float4(0.f, 0.f, 0.f, 0.f));
+    float2* tp = reinterpret_cast<float2*>(ctx->sym_tparam.data());
+    for (int q = 0; q < SYM_TPARAM_NODES; q++) {
+      const bool real = q < ns;
+      for (int d = 0; d < 3; d++) {
+        const float x = real ? -t32[(size_t)d * ns + q] : (d == 0 ? -1.0e3f : 0.f);
+        const float w = real ? t32[(size_t)(3 + d) * ns + q] : 0.f;
+        tp[6 * q + d] = make_float2(x, x);
+        tp[6 * q + 3 + d] = make_float2(w, w);
+      }
+    }
+  }
+  for (int v = 0; v < kNumSymVariants && v < 16; v++) {
+    const Pair32SymVariant& kv = kSymVariants[v];
+    if (kv.kernel_p && !tparam_ok) {   // parameter-block variants cover up to SYM_TPARAM_NODES nodes
+      ctx->symv_occ[v] = 0;
+      continue;
+    }
     const size_t smem = sym_smem(ns, v);
-    if (smem > 48 * 1024)
-      LCP_CUDA(raise_smem_limit((const void*)kSymVariants[v].kernel, smem));
+    const void* fn = kv.kernel_p ? (const void*)kv.kernel_p : (const void*)kv.kernel;
+    if (smem > 48 * 1024) LCP_CUDA(raise_smem_limit(fn, smem));
     int occ = 0;
-    LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kSymVariants[v].kernel, SYM_THREADS, smem));
+    if (kv.kernel_p)
+      LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kv.kernel_p, kv.threads, smem));
+    else
+      LCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kv.kernel, kv.threads, smem));
     int G = ctx->num_sms * (occ > 0 ? occ : 1);
     if (G > U) G = U;
     int slots = 1;
@@ -460,9 +571,12 @@ int stokes_sym_configure(lcp_ctx* ctx) {
   const int df_slots = stokes_sym_df_configure(ctx, off.data(), ntb);
   if (df_slots > ctx->sym_slots) ctx->sym_slots = df_slots;
   // default: the symmetric sum when every CTA gets several units (otherwise
-  // the one-wave balance of the plain kernel's finer units wins)
+  // the one-wave balance of the plain kernel's finer units wins), in its
+  // fastest measured form where that fits the size
   ctx->sym = U >= 4 * ctx->symv_grid[0];
   ctx->sym_v = 0;
+  for (int v = 0; v < kNumSymVariants && v < 16; v++)
+    if (std::strcmp(kSymVariants[v].name, "sym_p8rc") == 0 && ctx->symv_occ[v] > 0) ctx->sym_v = v;
   ctx->sym_off = (int*)ctx_alloc(ctx, sizeof(int) * (ntb + 1));
   ctx->sym_roff = (long long*)ctx_alloc(ctx, sizeof(long long) * (ntb + 1));
   // room for double-float (hi, lo) rows: the symmetric double-float kernel shares the buffer
@@ -475,7 +589,7 @@ int stokes_sym_configure(lcp_ctx* ctx) {
   return LCP_OK;
 }
 
-int stokes_sym_variant_count() { return kNumSymVariants < 8 ? kNumSymVariants : 8; }
+int stokes_sym_variant_count() { return kNumSymVariants < 16 ? kNumSymVariants : 16; }
 const char* stokes_sym_variant_name(int v) { return kSymVariants[v].name; }
 bool stokes_sym_variant_usable(const lcp_ctx* ctx, int v) {
   return ctx->symv_occ[v] > 0 && ctx->symv_slots[v] <= ctx->splits;
@@ -506,8 +620,14 @@ int stokes_sym_apply(lcp_ctx* ctx, double* out) {
   LCP_CUDA(cudaMemsetAsync(ctx->partial, 0, sizeof(double) * 3 * (size_t)N * slots, ctx->stream));
   SymUnits su{ctx->sym_units, G, ctx->sym_ntb, ns, ctx->sym_off, ctx->sym_roff};
   cudaEvent_t e0 = prof_begin(ctx);
-  ++ctx->nlaunch, kSymVariants[v].kernel<<<G, SYM_THREADS, sym_smem(ns, v), ctx->stream>>>(
-                      N, ns, ns_pad, su, ctx->tmpl32, ctx->centers32, ctx->phi32, ctx->partial, ctx->sym_rev);
+  const Pair32SymVariant& kv = kSymVariants[v];
+  if (kv.kernel_p)
+    ++ctx->nlaunch, kv.kernel_p<<<G, kv.threads, sym_smem(ns, v), ctx->stream>>>(
+                        N, ns, ns_pad, su, ctx->tmpl32, ctx->centers32, ctx->phi32, ctx->partial, ctx->sym_rev,
+                        *reinterpret_cast<const SymTmplParam*>(ctx->sym_tparam.data()));
+  else
+    ++ctx->nlaunch, kv.kernel<<<G, kv.threads, sym_smem(ns, v), ctx->stream>>>(
+                        N, ns, ns_pad, su, ctx->tmpl32, ctx->centers32, ctx->phi32, ctx->partial, ctx->sym_rev);
   prof_end(ctx, e0, 0);
   ++ctx->nlaunch, k_finish_sym<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(
                       N, ns, slots, ctx->partial, ctx->sym_rev, ctx->sym_roff, ctx->coef, ctx->tmpl64, out);

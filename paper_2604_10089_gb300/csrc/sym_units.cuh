@@ -18,3 +18,12 @@ struct SymUnits {
   }
   __device__ __forceinline__ int first_body(int tb) const { return (int)(((long long)tb * SYM_TB) / ns); }
 };
+
+// Source template of the symmetric FP32 pair sum as a launch parameter block
+// (it lands in the constant bank, which every lane of a warp reads at the same
+// address): per node q, float2 entries 6q + d = (-xi_d, -xi_d) and 6q + 3 + d =
+// (wn_d, wn_d); padding nodes sit far away with zero weight.
+constexpr int SYM_TPARAM_NODES = 512;
+struct __align__(16) SymTmplParam {
+  float4 v[SYM_TPARAM_NODES * 3];
+};

@@ -22,7 +22,8 @@ def small_batch():
     return insts
 
 
-VARIANTS = ("sym_a4", "sym_a4m4", "sym_a8m2", "sym_a2", "sym", "t2c8", "t1c8", "t2c16", "t2c4", "t1c16")
+VARIANTS = ("sym_a4", "sym_a4m4", "sym_a8m2", "sym_a2", "sym", "sym_t8b2", "sym_t8b4", "sym_p8rc", "sym_p4rc",
+            "t2c8", "t1c8", "t2c16", "t2c4", "t1c16")
 
 
 def make_ctxs(insts, **kw):

@@ -138,7 +138,7 @@ def test_coarse_child_keeps_parent_shared_memory_limits():
         ref = torch.empty_like(phi)
         L.lcp_stokes_apply_dev(ctx, phi, ref, L.LCP_FP64)
         out = torch.empty_like(phi)
-        for v in ("sym_a4", "t2c8"):
+        for v in ("sym_a4", "sym_p8rc", "t2c8"):
             L.lcp_select_kernel_variant(ctx, v)
             L.lcp_stokes_apply_dev(ctx, phi, out, L.LCP_DF64)
             assert rel(out.cpu().numpy(), ref.cpu().numpy()) <= 1e-12, v
