@@ -95,6 +95,12 @@ typedef struct {
   /* Bi-PQN's low-fidelity initialisation (Sec. 5.2, solved "approximately"):
    * stops at max(tol, init_forcing * its initial KKT error); 0 = to tol. */
   double init_forcing;
+  /* Warm start of the slip solve for U_nc along a trajectory (lcp_step): start
+   * GMRES from the previous step's density instead of zero.  Consecutive
+   * configurations differ by one time step, so the start is close and fewer
+   * iterations reach the same tolerance.  The paper names reuse across solves as
+   * future work ("Conclusions and Future Work"); 0 = always start from zero. */
+  int warm_start;
 } lcp_config;
 
 typedef struct {
@@ -122,6 +128,8 @@ typedef struct {
   int ssn_iterations;       /* semi-smooth Newton iterations of all prox evaluations */
   int ssn_fallbacks;        /* prox evaluations that needed the projected Gauss-Seidel fallback */
   double h0_delta;          /* scale delta of B_0 = delta I (1 when unscaled) */
+  int unc_gmres_iterations; /* GMRES iterations of the slip solve that produced this LCP's b */
+  int unc_warm_started;     /* 1 if that slip solve started from the previous step's density */
 } lcp_stats;
 
 typedef struct lcp_ctx lcp_ctx;   /* opaque, library-owned */

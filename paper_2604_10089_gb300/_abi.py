@@ -36,7 +36,7 @@ class lcp_config(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("own_stream", ctypes.c_int), ("h0_scaling", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("lowfi_n_theta", ctypes.c_int),
                 ("lowfi_n_phi", ctypes.c_int), ("lowfi_tol", ctypes.c_double),
-                ("init_forcing", ctypes.c_double)]
+                ("init_forcing", ctypes.c_double), ("warm_start", ctypes.c_int)]
 
 
 class lcp_contact(ctypes.Structure):
@@ -52,7 +52,8 @@ class lcp_stats(ctypes.Structure):
                 ("kkt_dot", ctypes.c_double), ("e_mvps", ctypes.c_double),
                 ("hi_mvp_seconds", ctypes.c_double), ("lo_mvp_seconds", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("df64_applies", ctypes.c_int), ("resets", ctypes.c_int),
-                ("ssn_iterations", ctypes.c_int), ("ssn_fallbacks", ctypes.c_int), ("h0_delta", ctypes.c_double)]
+                ("ssn_iterations", ctypes.c_int), ("ssn_fallbacks", ctypes.c_int), ("h0_delta", ctypes.c_double),
+                ("unc_gmres_iterations", ctypes.c_int), ("unc_warm_started", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -114,6 +114,9 @@ struct lcp_ctx {
   int *bc_ptr = nullptr, *bc_idx = nullptr;
   int *flags = nullptr, *csr_cnt = nullptr;
   double* U_nc = nullptr;     // [M][6]
+  double* phi_unc = nullptr;  // [3N]: density of the last slip solve (warm start along a trajectory)
+  bool phi_unc_valid = false;
+  int unc_its = 0, unc_warm = 0;   // GMRES iterations / warm start of the last slip solve
   double* MDx = nullptr;      // [M][6] collisional velocities M D x of the last solve
   double *cnext = nullptr, *anext = nullptr;   // [M][3] advanced centres / axes
   bool have_solution = false;
@@ -125,7 +128,8 @@ struct lcp_ctx {
   bool sym = true;            // FP32 sums by the symmetric kernel (stokes_sym.cu)
   int sym_v = 0;              // symmetric kernel variant in use
   int sym_ntb = 0, sym_units = 0, sym_slots = 0;   // sym_slots: largest over the variants
-  int symv_occ[8] = {0}, symv_grid[8] = {0}, symv_slots[8] = {0};
+  int symv_occ[16] = {0}, symv_grid[16] = {0}, symv_slots[16] = {0};
+  std::vector<float4> sym_tparam;  // launch-parameter copy of the source template (duplicated pairs)
   int symdf_grid = 0, symdf_slots = 0;   // the symmetric double-float kernel (stokes_sym_df.cu)
   int* sym_off = nullptr;          // [ntb + 1] first unit of each target block
   long long* sym_roff = nullptr;   // [ntb + 1] first float of each block's reverse rows
@@ -224,7 +228,7 @@ int contacts_csr(lcp_ctx* ctx);
 int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision);
 int stokes_rhs(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs);
 int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef);
-int mobility_solve(lcp_ctx* ctx, const double* FT, int include_slip, double* UO);
+int mobility_solve(lcp_ctx* ctx, const double* FT, int include_slip, double* UO, const double* phi0 = nullptr);
 int precond_build(lcp_ctx* ctx);
 int precond_apply(lcp_ctx* ctx, const double* v, double* z);
 int scatter_D(lcp_ctx* ctx, const double* x, double* FT);

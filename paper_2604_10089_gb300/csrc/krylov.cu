@@ -417,18 +417,27 @@ static int norm2(lcp_ctx* ctx, const double* v, int L, double* out) {
 // IR_UPDATE_MAX ||phi|| falls back to an FP64 residual.
 static constexpr double IR_UPDATE_MAX = 1e-5;
 
-int density_solve(lcp_ctx* ctx, const double* rhs, double* phi) {
+// phi0 (or NULL): initial guess.  With a guess the first residual is taken
+// with the high-accuracy operator, so the guess only has to be close, not exact.
+int density_solve(lcp_ctx* ctx, const double* rhs, double* phi, const double* phi0) {
   const int L = 3 * ctx->N;
   const int T = 256;
   double bn = 0.0;
   LCP_TRY(norm2(ctx, rhs, L, &bn));
-  LCP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * L, ctx->stream));
-  if (bn == 0.0) return LCP_OK;
+  if (phi0)
+    LCP_CUDA(cudaMemcpyAsync(phi, phi0, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+  else
+    LCP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * L, ctx->stream));
+  if (bn == 0.0) {
+    if (phi0) LCP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * L, ctx->stream));
+    return LCP_OK;
+  }
   const double tol = ctx->cfg.gmres_tol * bn;
+  const int zero_init = phi0 ? 0 : 1;
   int its = 0;
   double res = 0.0;
   if (ctx->cfg.precision == LCP_FP64) {
-    LCP_TRY(gmres(ctx, rhs, phi, 1, tol, LCP_FP64, ctx->cfg.gmres_maxit, &its, &res));
+    LCP_TRY(gmres(ctx, rhs, phi, zero_init, tol, LCP_FP64, ctx->cfg.gmres_maxit, &its, &res));
     ctx->c_gmres += its;
     if (res > tol) {
       ctx->err = "GMRES did not reach its tolerance";
@@ -437,7 +446,7 @@ int density_solve(lcp_ctx* ctx, const double* rhs, double* phi) {
     return LCP_OK;
   }
   if (ctx->fp32_only) {   // low-fidelity grid: FP32-operator GMRES to the tolerance, no refinement
-    LCP_TRY(gmres(ctx, rhs, phi, 1, tol, LCP_MIXED, ctx->cfg.gmres_maxit, &its, &res));
+    LCP_TRY(gmres(ctx, rhs, phi, zero_init, tol, LCP_MIXED, ctx->cfg.gmres_maxit, &its, &res));
     ctx->c_gmres += its;
     if (res > tol) {
       ctx->err = "GMRES did not reach its tolerance";
@@ -445,9 +454,18 @@ int density_solve(lcp_ctx* ctx, const double* rhs, double* phi) {
     }
     return LCP_OK;
   }
-  // mixed precision: phi = 0, r = rhs
-  LCP_CUDA(cudaMemcpyAsync(ctx->res, rhs, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+  // mixed precision: phi = 0, r = rhs; or phi = phi0, r = rhs - (K + P) phi0
+  // with the high-accuracy operator
   double rn = bn;
+  if (phi0) {
+    LCP_TRY(stokes_apply(ctx, phi, ctx->wv, ctx->cfg.residual_precision));
+    ++ctx->nlaunch, k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->wv, ctx->res);
+    LCP_TRY(norm2(ctx, ctx->res, L, &rn));
+    if (!(rn == rn)) { ctx->err = "refinement: NaN residual"; return LCP_ERR_NUMERICAL; }
+    if (rn <= tol) return LCP_OK;
+  } else {
+    LCP_CUDA(cudaMemcpyAsync(ctx->res, rhs, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
   for (int sweep = 0; sweep < ctx->cfg.ir_maxit; sweep++) {
     LCP_CUDA(cudaMemsetAsync(ctx->dphi, 0, sizeof(double) * L, ctx->stream));
     const double tin = std::max(ctx->cfg.inner_tol * rn, 0.5 * tol);
@@ -472,9 +490,9 @@ int density_solve(lcp_ctx* ctx, const double* rhs, double* phi) {
   return LCP_ERR_NOT_CONVERGED;
 }
 
-int mobility_solve(lcp_ctx* ctx, const double* FT, int include_slip, double* UO) {
+int mobility_solve(lcp_ctx* ctx, const double* FT, int include_slip, double* UO, const double* phi0) {
   LCP_TRY(stokes_rhs(ctx, FT, include_slip, ctx->rhs));
-  LCP_TRY(density_solve(ctx, ctx->rhs, ctx->phi));
+  LCP_TRY(density_solve(ctx, ctx->rhs, ctx->phi, phi0));
   return stokes_velocity(ctx, ctx->phi, UO);
 }
 

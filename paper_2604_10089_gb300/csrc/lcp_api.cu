@@ -61,6 +61,7 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->autotune = 0;
   c->own_stream = 0;
   c->h0_scaling = 1;
+  c->warm_start = 1;
   c->cuda_stream = nullptr;
 }
 
@@ -109,7 +110,9 @@ static int lowfi_create(lcp_ctx* ctx) {
   lo->cfg.own_stream = 0;
   lo->cfg.lowfi_n_theta = 0;
   lo->cfg.lowfi_n_phi = 0;
-  lo->cfg.autotune = 1;   // its pair kernel runs ~10x per high-fidelity MVP: pick the fastest variant once
+  // the kernel choice follows the parent's autotune setting; by default the
+  // size rule picks it, which keeps the choice independent of timing noise
+  // (and of a profiler's launch overhead)
   lo->stream = ctx->stream;
   lo->device = ctx->device;
   lo->M = ctx->M;
@@ -156,12 +159,13 @@ static int alloc_static(lcp_ctx* ctx) {
   ctx->FT = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->UO = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->U_nc = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
+  ctx->phi_unc = (double*)ctx_alloc(ctx, sizeof(double) * L);
   ctx->MDx = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->cnext = (double*)ctx_alloc(ctx, sizeof(double) * 3 * M);
   ctx->anext = (double*)ctx_alloc(ctx, sizeof(double) * 3 * M);
   if (!ctx->MDx || !ctx->cnext || !ctx->anext) return LCP_ERR_OOM;
   if (!ctx->V || !ctx->H || !ctx->phi || !ctx->rhs || !ctx->res || !ctx->wv || !ctx->dphi || !ctx->phi32 ||
-      !ctx->partial || !ctx->coef || !ctx->dotp || !ctx->FT || !ctx->UO || !ctx->U_nc || !ctx->phidf) {
+      !ctx->partial || !ctx->coef || !ctx->dotp || !ctx->FT || !ctx->UO || !ctx->U_nc || !ctx->phi_unc || !ctx->phidf) {
     ctx->err = "device allocation failed";
     return LCP_ERR_OOM;
   }
@@ -218,8 +222,9 @@ static int arena_ensure(lcp_ctx* ctx, int n) {
 
 // Everything that depends on the configuration: centres (and axes), the
 // collisional set and D, U_nc and b (Sec. 3, Eqs. collisional-set, defAandb).
+// warm: start the slip solve from the previous slip density (time stepping).
 static int configure(lcp_ctx* ctx, const double* centers, const double* axes, int n_contacts,
-                     const lcp_contact* contacts, bool device_inputs) {
+                     const lcp_contact* contacts, bool device_inputs, bool warm = false) {
   const int M = ctx->M;
   const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   LCP_CUDA(cudaMemcpyAsync(ctx->centers, centers, sizeof(double) * 3 * M, kind, ctx->stream));
@@ -248,10 +253,20 @@ static int configure(lcp_ctx* ctx, const double* centers, const double* axes, in
   LCP_TRY(contacts_csr(ctx));
   // U_nc: slip-driven velocities with F = T = 0
   LCP_CUDA(cudaMemsetAsync(ctx->FT, 0, sizeof(double) * 6 * M, ctx->stream));
+  ctx->unc_its = 0;
+  ctx->unc_warm = 0;
   if (ctx->has_axes) {
-    LCP_TRY(mobility_solve(ctx, ctx->FT, 1, ctx->U_nc));
+    const bool use_warm = warm && ctx->cfg.warm_start && ctx->phi_unc_valid;
+    const int g0 = ctx->c_gmres;
+    LCP_TRY(mobility_solve(ctx, ctx->FT, 1, ctx->U_nc, use_warm ? ctx->phi_unc : nullptr));
+    ctx->unc_its = ctx->c_gmres - g0;
+    ctx->unc_warm = use_warm ? 1 : 0;
+    LCP_CUDA(cudaMemcpyAsync(ctx->phi_unc, ctx->phi, sizeof(double) * 3 * ctx->N, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    ctx->phi_unc_valid = true;
   } else {
     LCP_CUDA(cudaMemsetAsync(ctx->U_nc, 0, sizeof(double) * 6 * M, ctx->stream));
+    ctx->phi_unc_valid = false;
   }
   if (n > 0) {
     LCP_TRY(gather_Dt(ctx, ctx->U_nc, ctx->tmp_n, nullptr));
@@ -325,7 +340,7 @@ extern "C" int lcp_step(lcp_ctx* ctx, double dt, double* centers_out, double* ax
   ++ctx->nlaunch, k_advance<<<(M + 127) / 128, 128, 0, ctx->stream>>>(M, dt, ctx->centers, ctx->axes, ctx->U_nc,
                                                                      ctx->MDx, ctx->has_axes, ctx->cnext, ctx->anext);
   LCP_CUDA(cudaGetLastError());
-  LCP_TRY(configure(ctx, ctx->cnext, ctx->has_axes ? ctx->anext : nullptr, 0, nullptr, true));
+  LCP_TRY(configure(ctx, ctx->cnext, ctx->has_axes ? ctx->anext : nullptr, 0, nullptr, true, true));
   ctx->have_solution = false;
   if (centers_out) LCP_TRY(copy_out(ctx, centers_out, ctx->centers, 3 * (size_t)M));
   if (axes_out && ctx->has_axes) LCP_TRY(copy_out(ctx, axes_out, ctx->axes, 3 * (size_t)M));
@@ -353,7 +368,7 @@ extern "C" int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n
   const size_t pairs = M * (M - 1) / 2 > 0 ? M * (M - 1) / 2 : 1;
   size_t b = 0;
   b += sizeof(double) * L * (m + 1) + (cfg->precondition ? sizeof(double) * L * m : 0);   // Krylov bases
-  b += sizeof(double) * L * 5 + sizeof(float) * L * 3;                                      // node vectors
+  b += sizeof(double) * L * 6 + sizeof(float) * L * 3;                                      // node vectors
   const size_t ntb = (N + 511) / 512, units = ntb * M / 2 + 1;                               // symmetric pair sum
   const size_t slots = std::min(units, 2 + M / std::max<size_t>(1, units / 304));
   b += sizeof(double) * L * std::max<size_t>(6, slots) + stokes_sym_bytes(n_bodies, (int)ns); // partial slots

@@ -1,13 +1,15 @@
 // Proximal quasi-Newton kernels (Sec. 4 and 5 of the paper).
 //
-//  * Algorithm 1 (Mono-PQN): x_tilde = x - H g by the two-loop recursion with
-//    H_0 = I, x_hat = prox^B(x_tilde) with B = I + U U^T - V V^T (BFGS
-//    unrolled, Appendix D.1), p = x_hat - x, one MVP A[p], the optimal
+//  * Algorithm 1 (Mono-PQN): x_tilde = x - H g, with H the inverse of the
+//    unrolled BFGS model B = delta I + U U^T - V V^T (Appendix D.1; B_0 =
+//    delta I scaled by the first secant pair, or I), applied by the Woodbury
+//    identity on [U V] (the same H as the two-loop recursion over the stored
+//    pairs), x_hat = prox^B(x_tilde), p = x_hat - x, one MVP A[p], the optimal
 //    over-relaxation of Algorithm 2, x += eta p, g += eta A[p] (MVP reuse),
 //    BFGS update with s = eta p, y = eta A[p].
 //  * Proposition 1 / Appendix A.2: the weighted prox by semi-smooth Newton on
 //    G(a, at) = [a + U^T(xt + C^-1 V at - z); at + V^T(xt - z)],
-//    z = (xt + C^-1 V at - U a)_+, C = I + U U^T, with the generalised
+//    z = (xt + C^-1 V at - U a / delta)_+, C = delta I + U U^T, with the generalised
 //    Jacobian J = I + [U^T L U, U^T (I - L) C^-1 V; V^T L U, -V^T L C^-1 V],
 //    L = diag(z > 0).  G and z are FP64; J is assembled and factorised in
 //    FP32 (an inexact Jacobian only changes the Newton path, not the root).
@@ -1162,6 +1164,8 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
   const double t_start = now_s();
   ctx->c_gmres = ctx->c_fp32 = ctx->c_fp64 = ctx->c_df64 = 0;
   lcp_stats s{};
+  s.unc_gmres_iterations = ctx->unc_its;
+  s.unc_warm_started = ctx->unc_warm;
   if (n == 0) {
     LCP_CUDA(cudaMemsetAsync(ctx->MDx, 0, sizeof(double) * 6 * ctx->M, ctx->stream));
     ctx->have_solution = true;

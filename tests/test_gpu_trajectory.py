@@ -1,0 +1,88 @@
+"""Warm start of the slip solve along a trajectory (lcp_step).
+
+The slip-driven density of the U_nc solve changes little over one time step,
+so starting GMRES from the previous step's density reaches the same tolerance
+in fewer iterations.  The next LCP's b must not change: it is compared with a
+cold-started run at every step and with the oracle after the first step.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2604_10089_gb300 as L  # noqa: E402
+from oracle.bie import DenseMobility  # noqa: E402
+from oracle.contacts import contact_matrix, detect_contacts  # noqa: E402
+from oracle.lcp import lcp_data  # noqa: E402
+from workloads import make_instance  # noqa: E402
+
+from .cases import dense_case  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def _rotate(e, w, dt):
+    th = np.linalg.norm(w) * dt
+    if th == 0.0:
+        return e
+    k = w / np.linalg.norm(w)
+    out = e * np.cos(th) + np.cross(k, e) * np.sin(th) + k * (k @ e) * (1 - np.cos(th))
+    return out / np.linalg.norm(out)
+
+
+@pytest.mark.parametrize("precision", [L.LCP_FP64, L.LCP_MIXED])
+def test_warm_started_slip_solve_same_b_fewer_iterations(precision):
+    inst = make_instance("spheres8_grid7x14", 2)
+    warm = L.lcp_setup(L.config_for(inst, precision, warm_start=1), inst.centers, inst.axes)
+    cold = L.lcp_setup(L.config_for(inst, precision, warm_start=0), inst.centers, inst.axes)
+    try:
+        its_w, its_c = [], []
+        for step in range(4):
+            xw, sw, _ = L.lcp_solve(warm, L.LCP_MONO_PQN, inst.tol)
+            xc, sc, _ = L.lcp_solve(cold, L.LCP_MONO_PQN, inst.tol)
+            assert sw["converged"] == 1 and sc["converged"] == 1
+            assert sw["unc_warm_started"] == (1 if step > 0 else 0) and sc["unc_warm_started"] == 0
+            if step > 0:
+                its_w.append(sw["unc_gmres_iterations"])
+                its_c.append(sc["unc_gmres_iterations"])
+            np.testing.assert_allclose(xw, xc, atol=1e-7 * max(1.0, np.abs(xc).max()))
+            L.lcp_step(warm, inst.dt)
+            L.lcp_step(cold, inst.dt)
+            assert rel(L.lcp_get_b(warm), L.lcp_get_b(cold)) <= 1e-10
+            assert rel(L.lcp_get_unc(warm), L.lcp_get_unc(cold)) <= 1e-10
+        _, sw, _ = L.lcp_solve(warm, L.LCP_MONO_PQN, inst.tol)
+        _, sc, _ = L.lcp_solve(cold, L.LCP_MONO_PQN, inst.tol)
+        its_w.append(sw["unc_gmres_iterations"])
+        its_c.append(sc["unc_gmres_iterations"])
+        assert all(w > 0 for w in its_w)
+        assert sum(its_w) < sum(its_c), (its_w, its_c)
+    finally:
+        L.lcp_destroy(warm)
+        L.lcp_destroy(cold)
+
+
+def test_warm_started_step_matches_oracle():
+    """Eq. (dvi) with the warm-started slip solve: the next b against the oracle."""
+    case = dense_case("spheres8_grid7x14", 4)
+    inst = case["inst"]
+    ctx = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, warm_start=1), inst.centers, inst.axes)
+    try:
+        x, _, _ = L.lcp_solve(ctx, L.LCP_MONO_PQN, inst.tol)
+        c_new, a_new = L.lcp_step(ctx, inst.dt)
+        U = (case["U_nc"] + case["Mob"] @ (case["D"] @ x)).reshape(-1, 6)
+        c_ref = inst.centers + inst.dt * U[:, :3]
+        a_ref = np.array([_rotate(inst.axes[i], U[i, 3:], inst.dt) for i in range(inst.n_bodies)])
+        mob = DenseMobility(c_ref, inst.n_theta, inst.n_phi, a=inst.radius)
+        pairs, normals, gaps = detect_contacts(c_ref, inst.contact_radius, inst.delta)
+        D = contact_matrix(inst.n_bodies, pairs, normals)
+        u_nc = mob.apply(np.zeros(6 * inst.n_bodies), axes=a_ref)
+        _, b_next = lcp_data(D, np.eye(6 * inst.n_bodies), u_nc, gaps, inst.dt)
+        _, st, _ = L.lcp_solve(ctx, L.LCP_MONO_PQN, inst.tol)
+        assert st["unc_warm_started"] == 1
+        assert rel(L.lcp_get_unc(ctx), u_nc) <= 1e-9
+        assert rel(L.lcp_get_b(ctx), b_next) <= 1e-9
+    finally:
+        L.lcp_destroy(ctx)
