@@ -87,8 +87,13 @@ def parse():
     p.add_argument("--sim-steps", type=int, default=3)
     p.add_argument("--arrival-rate", type=float, default=8.0, help="requests/s per simulation (Poisson)")
     p.add_argument("--budget-frac", type=float, default=0.5, help="HBM budget as a fraction of all contexts")
-    p.add_argument("--trajectory", type=int, default=0,
-                   help="also time this many forward-Euler steps (solve + lcp_step) of one configuration")
+    p.add_argument("--trajectory", type=int, default=100,
+                   help="also time this many forward-Euler steps (solve + lcp_step) of one configuration, with "
+                        "the warm-started slip solve, and the first --trajectory-cold of them cold-started")
+    p.add_argument("--trajectory-cold", type=int, default=10)
+    p.add_argument("--c2", type=int, default=1,
+                   help="64-sphere report: Mono vs Bi-PQN, FP64 vs mixed, high-fidelity MVPs and the error "
+                        "against the FP64 oracle")
     return p.parse_args()
 
 
@@ -309,24 +314,41 @@ def run_ours(args, rank, world, local):
     traj = None
     if args.trajectory and rank == 0:
         inst = insts[args.warmup]
-        L.lcp_update(ctx, inst.centers, inst.axes)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hi = lo = 0
-        kkts, ncs = [], []
-        for _ in range(args.trajectory):
-            _, st, _ = L.lcp_solve(ctx, method, tol)
-            hi += st["hi_mvps"]
-            lo += st["lo_mvps"]
-            kkts.append(st["kkt_abs"])
-            ncs.append(L.lcp_sizes(ctx)[2])
-            L.lcp_step(ctx, inst.dt)
-        torch.cuda.synchronize()
-        tt = time.perf_counter() - t0
-        traj = {"steps": args.trajectory, "dt": inst.dt, "seconds": tt, "steps_per_s": args.trajectory / tt,
-                "hi_mvps_per_step": hi / args.trajectory, "lo_mvps_per_step": lo / args.trajectory,
-                "max_kkt": max(kkts), "contacts_first_last": [ncs[0], ncs[-1]]}
+
+        def trajectory(c, steps):
+            L.lcp_update(c, inst.centers, inst.axes)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hi = lo = 0
+            kkts, ncs, unc, warm = [], [], [], []
+            for _ in range(steps):
+                _, st, _ = L.lcp_solve(c, method, tol)
+                hi += st["hi_mvps"]
+                lo += st["lo_mvps"]
+                kkts.append(st["kkt_abs"])
+                ncs.append(L.lcp_sizes(c)[2])
+                unc.append(st["unc_gmres_iterations"])
+                warm.append(st["unc_warm_started"])
+                L.lcp_step(c, inst.dt)
+            torch.cuda.synchronize()
+            tt = time.perf_counter() - t0
+            # the first slip solve of a trajectory comes from lcp_update (never warm-started)
+            later = unc[1:]
+            return {"steps": steps, "dt": inst.dt, "seconds": tt, "steps_per_s": steps / tt,
+                    "hi_mvps_per_step": hi / steps, "lo_mvps_per_step": lo / steps, "max_kkt": max(kkts),
+                    "contacts_first_last": [ncs[0], ncs[-1]],
+                    "slip_gmres_iterations_per_step": float(np.mean(later)) if later else None,
+                    "slip_warm_started_steps": int(sum(warm))}
+
+        traj = trajectory(ctx, args.trajectory)
+        traj["warm_start"] = True
+        if args.trajectory_cold:
+            cfg_cold = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream, warm_start=0, **lowfi)
+            ctx_cold = L.lcp_setup(cfg_cold, inst.centers, inst.axes)
+            traj["cold_start_first_steps"] = trajectory(ctx_cold, min(args.trajectory_cold, args.trajectory))
+            L.lcp_destroy(ctx_cold)
     L.lcp_destroy(ctx)
+    c2 = c2_report(stream) if (args.c2 and rank == 0) else None
 
     pairs = float(N) * (N - 1)
     avg32 = t32 / c32 / 1e3 if c32 else None
@@ -374,10 +396,43 @@ def run_ours(args, rank, world, local):
                                          + (", one evaluation per unordered pair (symmetric)" if sym_df else ""),
                "pairs_per_s": pairs / (tdf / cdf / 1e3), "share_of_timed_region": tdf / 1e3 / t_total}
     lowfi_desc = lowfi_description(lowfi)
-    return dict(t_total=t_total, lat=lat, clocks=clk, launches=launches, roof=roof, k64=k64, kdf=kdf, e2e=e2e, traj=traj,
+    return dict(t_total=t_total, lat=lat, clocks=clk, c2=c2, launches=launches, roof=roof, k64=k64, kdf=kdf, e2e=e2e, traj=traj,
                 lowfi=lowfi_desc, lowfi_cfg=lowfi,
                 comparison=comparison,
                 fp64=fp64, summary=summary, N=N, M=M)
+
+
+def c2_report(stream) -> dict:
+    """64 spheres (9 x 18 nodes, delta 0.05): Mono-PQN on the high-fidelity mobility and Bi-PQN
+    with the RPY low fidelity, each all-FP64 and mixed (FP32 sums + FP64 refinement): solve time,
+    high-/low-fidelity MVPs, and the distance to the plain FP64 Mono-PQN solution (the tests
+    check these solves against the FP64 oracle)."""
+    import paper_2604_10089_gb300 as L
+    from workloads import make_instance
+
+    inst = make_instance("spheres64_grid9x18", 0)
+    out = {"workload": "spheres64_grid9x18: 64 Janus spheres, 10368 nodes, 31104 unknowns, delta 0.05",
+           "tol": inst.tol}
+    ref = None
+    for name, meth, prec in (("mono_fp64", L.LCP_MONO_PQN, L.LCP_FP64), ("mono_mixed", L.LCP_MONO_PQN, L.LCP_MIXED),
+                             ("bi_rpy_fp64", L.LCP_BI_PQN, L.LCP_FP64), ("bi_rpy_mixed", L.LCP_BI_PQN, L.LCP_MIXED)):
+        ctx = L.lcp_setup(L.config_for(inst, prec, cuda_stream=stream.cuda_stream), inst.centers, inst.axes)
+        try:
+            L.lcp_solve(ctx, meth, inst.tol)   # warm-up (graph capture, first launches)
+            t0 = time.perf_counter()
+            x, st, _ = L.lcp_solve(ctx, meth, inst.tol)
+            dt = time.perf_counter() - t0
+        finally:
+            L.lcp_destroy(ctx)
+        if ref is None:
+            ref = x
+        thr = 1e-9 * max(1.0, float(np.abs(ref).max()))
+        out[name] = {"seconds": dt, "hi_mvps": st["hi_mvps"], "lo_mvps": st["lo_mvps"], "e_mvps": st["e_mvps"],
+                     "kkt": st["kkt_abs"], "converged": st["converged"] == 1,
+                     "max_abs_diff_vs_mono_fp64": float(np.abs(x - ref).max()),
+                     "same_active_set_as_mono_fp64": bool(np.array_equal(x > thr, ref > thr))}
+    out["contacts"] = int(ref.size)
+    return out
 
 
 def run_batched(args):
@@ -766,6 +821,7 @@ def main():
             "roofline": r["roof"], "fp64_kernel": r["k64"], "df64_kernel": r["kdf"], "clocks": r["clocks"],
             "e2e": r["e2e"], "gpu_launches": r["launches"], "cpu_baseline": cpu,
             "fp64_mono_pqn": r["fp64"], "method_comparison_mixed": r["comparison"], "trajectory": r["traj"],
+            "c2_spheres64": r["c2"],
             "solver": s,
         }
         print(json.dumps(line), flush=True)

@@ -61,3 +61,26 @@ def test_fullsize_slip_velocities_and_lcp_solution(big):
     assert mismatch <= MISMATCH_REL * max(1.0, np.linalg.norm(b)), (eps_op, mismatch)
     assert kkt_abs(x, Ax + b) <= inst.tol + eps_op
     assert np.count_nonzero(x) >= 0.1 * x.size     # a non-trivial LCP
+
+
+@pytest.mark.parametrize("method", [L.LCP_MONO_PQN, L.LCP_BI_PQN])
+@pytest.mark.parametrize("precision", [L.LCP_FP64, L.LCP_MIXED])
+def test_c2_solves_against_the_oracle(method, precision):
+    """64 spheres (the Mono vs Bi, FP64 vs mixed comparison): each solution's KKT error with
+    the matrix-free oracle's MVP and b stays within tol + eps_op."""
+    inst = make_instance("spheres64_grid9x18", 0)
+    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius)
+    pairs, normals, gaps = detect_contacts(inst.centers, inst.contact_radius, inst.delta)
+    D = contact_matrix(inst.n_bodies, pairs, normals)
+    b_or = gaps / inst.dt + D.T @ mf.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes)
+    ctx = L.lcp_setup(L.config_for(inst, precision), inst.centers, inst.axes)
+    try:
+        x, st, _ = L.lcp_solve(ctx, method, inst.tol)
+        assert st["converged"] == 1
+        g_gpu = L.lcp_apply_A(ctx, x, L.LCP_HIGH) + L.lcp_get_b(ctx)
+    finally:
+        L.lcp_destroy(ctx)
+    g = D.T @ mf.apply(D @ x) + b_or
+    eps_op, mismatch = kkt_bound(inst.tol, x, g, g_gpu, b_or, st["hi_mvps"])
+    assert mismatch <= MISMATCH_REL * max(1.0, np.linalg.norm(b_or)), mismatch
+    assert kkt_abs(x, g) <= inst.tol + eps_op
