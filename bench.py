@@ -87,6 +87,8 @@ def parse():
     p.add_argument("--sim-steps", type=int, default=3)
     p.add_argument("--arrival-rate", type=float, default=8.0, help="requests/s per simulation (Poisson)")
     p.add_argument("--budget-frac", type=float, default=0.5, help="HBM budget as a fraction of all contexts")
+    p.add_argument("--fp64-baseline", type=int, default=1,
+                   help="batched/serving modes: time plain FP64 Mono-PQN on every instance, one at a time")
     p.add_argument("--trajectory", type=int, default=100,
                    help="also time this many forward-Euler steps (solve + lcp_step) of one configuration, with "
                         "the warm-started slip solve, and the first --trajectory-cold of them cold-started")
@@ -472,18 +474,15 @@ def run_batched(args):
     for c in ctxs:
         L.lcp_solve(c, L.LCP_BI_PQN, 1e-8)
     t_seq = time.perf_counter() - t0
-    sample = sorted(range(len(insts)), key=lambda k: insts[k].n_bodies * insts[k].nodes_per_body)[:: max(1, len(insts) // 4)][:4]
-    t64 = []
-    for k in sample:
-        i = insts[k]
-        c64 = L.lcp_setup(L.config_for(i, L.LCP_FP64), i.centers, i.axes)
-        ts = time.perf_counter()
-        L.lcp_solve(c64, L.LCP_MONO_PQN, 1e-8, allow_not_converged=True)
-        t64.append((i.n_bodies * i.nodes_per_body, time.perf_counter() - ts))
-        L.lcp_destroy(c64)
-    # FP64 time model t ~ c N^2 fitted on the sample, summed over all instances
-    cfit = float(np.mean([t / (nn * nn) for nn, t in t64]))
-    t64_all = sum(cfit * (i.n_bodies * i.nodes_per_body) ** 2 for i in insts)
+    # plain FP64 Mono-PQN on the GPU, one instance at a time (every instance, timed)
+    t64_all = 0.0
+    if args.fp64_baseline:
+        for i in insts:
+            c64 = L.lcp_setup(L.config_for(i, L.LCP_FP64), i.centers, i.axes)
+            ts = time.perf_counter()
+            L.lcp_solve(c64, L.LCP_MONO_PQN, 1e-8, allow_not_converged=True)
+            t64_all += time.perf_counter() - ts
+            L.lcp_destroy(c64)
     variants = {}
     for c in ctxs:
         v = L.lcp_kernel_variant(c)
@@ -495,8 +494,8 @@ def run_batched(args):
             "seconds_per_batch": t_batch, "all_converged": all(s == 0 for s in statuses),
             "hi_mvps_mean": float(np.mean([s["hi_mvps"] for s in stats])),
             "sequential_mixed_solves_per_s": len(insts) / t_seq,
-            "sequential_fp64_mono_solves_per_s_model": len(insts) / t64_all,
-            "fp64_sample_seconds": t64, "setup_seconds_all": t_setup, "generation_seconds": t_gen,
+            "sequential_fp64_mono_solves_per_s": (len(insts) / t64_all) if args.fp64_baseline else None,
+            "setup_seconds_all": t_setup, "generation_seconds": t_gen,
             "kernel_variants": variants, "clocks": clk,
             "config": {"workload": "256 packings, 8-128 spheres, 98 or 162 nodes per sphere, phi 0.30-0.45",
                        "method": "bi_pqn", "precision": "mixed", "tol": 1e-8}}
@@ -504,7 +503,8 @@ def run_batched(args):
 
 
 def run_serving(args):
-    """Poisson requests from concurrent simulations (16-216 spheres, 162 nodes), HBM-budget admission."""
+    """Poisson requests from concurrent simulations (16-216 spheres, 162 nodes); the server holds
+    each simulation's first request until its estimated footprint fits the HBM budget."""
     import torch
 
     import paper_2604_10089_gb300 as L
@@ -512,93 +512,80 @@ def run_serving(args):
 
     sims = serving_simulations(args.sims)
     rng = np.random.default_rng(77)
-    cfgs = [L.config_for(i, L.LCP_MIXED, own_stream=1) for i in sims]
-    est = [L.lcp_footprint_estimate(c, i.n_bodies, 3 * i.n_bodies) for c, i in zip(cfgs, sims)]
+    cfgs = [L.config_for(i, L.LCP_MIXED) for i in sims]
+    est = [L.lcp_footprint_estimate(c, i.n_bodies, 6 * i.n_bodies) for c, i in zip(cfgs, sims)]
     budget = int(args.budget_frac * sum(est))
     srv = L.lcp_server_create(args.workers, budget)
+    ids = [L.lcp_server_open(srv, c, i.centers, i.axes) for c, i in zip(cfgs, sims)]
     steps_left = [args.sim_steps] * len(sims)
-    ctx = [None] * len(sims)
     arrival = list(rng.exponential(1.0 / args.arrival_rate, len(sims)))
+    ncon = [None] * len(sims)
     ticket = {}
-    lat, sizes, solves_stats = [], [], []
-    reserved = 0
+    lat, solves_stats = [], []
     t0 = time.perf_counter()
     clocks = ClockSampler(0)
     clocks.start()
     done = 0
     total = args.sim_steps * len(sims)
-    max_resident = 0
+    max_resident = max_waiting = 0
     while done < total and time.perf_counter() - t0 < 1800:
         now = time.perf_counter() - t0
         for k in range(len(sims)):
             if steps_left[k] == 0 or k in ticket or arrival[k] > now:
                 continue
-            if ctx[k] is None:                     # admission: create only when the budget allows
-                if reserved + est[k] > budget:
-                    continue
-                ctx[k] = L.lcp_setup(cfgs[k], sims[k].centers, sims[k].axes)
-                if L.lcp_server_admit(srv, ctx[k]) != L.LCP_OK:
-                    L.lcp_destroy(ctx[k])
-                    ctx[k] = None
-                    continue
-                reserved += est[k]
-            ticket[k] = (L.lcp_server_submit(srv, ctx[k], L.LCP_BI_PQN, 1e-8), arrival[k])
+            dt = sims[k].dt if steps_left[k] > 1 else 0.0     # the simulation advances after each solve
+            ticket[k] = (L.lcp_server_request(srv, ids[k], L.LCP_BI_PQN, 1e-8, dt), arrival[k])
         for k, (t, arr) in list(ticket.items()):
-            status, x, st = L.lcp_server_poll(srv, t, L.lcp_sizes(ctx[k])[2], 200)
+            status, x, st = L.lcp_server_poll(srv, t, 6 * sims[k].n_bodies, 200)
             if status == L.LCP_ERR_TIMEOUT:
                 continue
             fin = time.perf_counter() - t0
             lat.append(fin - arr)
-            sizes.append(sims[k].n_bodies)
             solves_stats.append(st)
             del ticket[k]
             done += 1
             steps_left[k] -= 1
             if steps_left[k] > 0:
-                L.lcp_step(ctx[k], sims[k].dt)         # the simulation advances, then asks again
                 arrival[k] = fin + rng.exponential(1.0 / args.arrival_rate)
             else:
-                L.lcp_server_release(srv, ctx[k])
-                L.lcp_destroy(ctx[k])
-                ctx[k] = None
-                reserved -= est[k]
-        max_resident = max(max_resident, L.lcp_server_stats(srv)[0])
+                L.lcp_server_close(srv, ids[k])
+        resident, waiting, _ = L.lcp_server_stats(srv)
+        max_resident = max(max_resident, resident)
+        max_waiting = max(max_waiting, waiting)
         time.sleep(0.0005)
     makespan = time.perf_counter() - t0
     clk = clocks.stop()
     L.lcp_server_destroy(srv)
-    # sequential baseline: the same first-step requests one at a time (mixed Bi-PQN), and plain
-    # FP64 Mono-PQN on a sample of sizes
-    t_seq = 0.0
+    # sequential baselines: the same first-step requests one at a time, mixed Bi-PQN, and plain
+    # FP64 Mono-PQN on the GPU (every simulation, timed)
+    t_seq = t64 = 0.0
     for i in sims:
         c = L.lcp_setup(L.config_for(i, L.LCP_MIXED), i.centers, i.axes)
         ts = time.perf_counter()
         L.lcp_solve(c, L.LCP_BI_PQN, 1e-8)
         t_seq += time.perf_counter() - ts
         L.lcp_destroy(c)
-    order = sorted(range(len(sims)), key=lambda k: sims[k].n_bodies)
-    t64 = []
-    for k in (order[0], order[len(order) // 4]):
-        i = sims[k]
-        c = L.lcp_setup(L.config_for(i, L.LCP_FP64), i.centers, i.axes)
-        ts = time.perf_counter()
-        L.lcp_solve(c, L.LCP_MONO_PQN, 1e-8, allow_not_converged=True)
-        t64.append((i.n_bodies, time.perf_counter() - ts))
-        L.lcp_destroy(c)
-    cfit = float(np.mean([t / (m * m) for m, t in t64]))
-    t64_all = sum(cfit * i.n_bodies ** 2 for i in sims)
+        if args.fp64_baseline:
+            c = L.lcp_setup(L.config_for(i, L.LCP_FP64), i.centers, i.axes)
+            ts = time.perf_counter()
+            L.lcp_solve(c, L.LCP_MONO_PQN, 1e-8, allow_not_converged=True)
+            t64 += time.perf_counter() - ts
+            L.lcp_destroy(c)
     line = {"metric": "served LCP solves/s", "value": done / makespan, "unit": "LCP solves/s", "n_gpus": 1,
             "mode": "serving", "requests": done, "simulations": len(sims), "workers": args.workers,
             "latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": max(lat) if lat else None},
             "arrival_rate_per_sim": args.arrival_rate, "hbm_budget_bytes": budget,
-            "max_resident_bytes": max_resident, "sum_of_footprints": int(sum(est)),
+            "max_resident_bytes": max_resident, "max_requests_waiting": max_waiting,
+            "sum_of_footprint_estimates": int(sum(est)),
             "all_converged": all(s["converged"] == 1 for s in solves_stats),
-            "sequential_mixed_solves_per_s": len(sims) / t_seq,
-            "sequential_fp64_mono_solves_per_s_model": len(sims) / t64_all, "fp64_sample_seconds": t64,
+            "sequential_mixed_bi_solves_per_s": len(sims) / t_seq,
+            "sequential_fp64_mono_solves_per_s": (len(sims) / t64) if args.fp64_baseline else None,
             "clocks": clk,
             "config": {"workload": f"{len(sims)} simulations, 16-216 spheres, 162 nodes per sphere, "
                                    f"phi 0.35-0.45, {args.sim_steps} steps each",
-                       "method": "bi_pqn", "precision": "mixed", "tol": 1e-8}}
+                       "method": "bi_pqn", "precision": "mixed", "tol": 1e-8,
+                       "admission": "server-held: a simulation's context is created once its estimated "
+                                    "footprint fits the budget"}}
     print(json.dumps(line), flush=True)
 
 

@@ -202,13 +202,37 @@ LCP_API int lcp_select_kernel_variant(lcp_ctx* ctx, const char* name);
 LCP_API int lcp_batch_solve(lcp_ctx** ctxs, int count, int method, double tol, double* const* x_dev, lcp_stats* stats,
                     int* statuses, int workers);
 
-/* Continuous-batching solve server: `workers` host threads take requests as
- * they arrive and run them concurrently (each context on its own stream).
- * Contexts must be admitted first; admission counts lcp_footprint against
- * hbm_budget_bytes and returns LCP_ERR_REJECTED when it would be exceeded.
- * A context has at most one request in flight.  lcp_server_poll waits at most
- * timeout_us for the ticket (LCP_ERR_TIMEOUT otherwise), copies x (host, at
- * least n doubles) and the stats, and returns the solve's status. */
+/* Continuous-batching solve server (the paper describes no serving layer; it
+ * serves many simulations at once): `workers` host threads take requests as they arrive and
+ * run them concurrently (each context on its own stream), while later
+ * requests keep arriving.
+ *
+ * Simulations owned by the server (the request carries the problem):
+ *   lcp_server_open registers a simulation (configuration, bodies, centres,
+ *   optional Janus axes; copied) and allocates nothing on the device.
+ *   lcp_server_request asks for a solve of its current LCP; with step_dt > 0
+ *   the simulation then advances one time step (lcp_step), so the next
+ *   request solves the next configuration.  The server creates the
+ *   simulation's context on its first request, but only once the context's
+ *   estimated device footprint (lcp_footprint_estimate with six contacts per
+ *   body) fits hbm_budget_bytes next to everything resident; until then the
+ *   request is held, first come first admitted.  The context then stays
+ *   resident (geometry, Krylov and quasi-Newton state) for the simulation's
+ *   later requests.  A simulation whose estimate alone exceeds the budget is
+ *   rejected (LCP_ERR_REJECTED).  lcp_server_close (after its last request has
+ *   been polled) destroys the context, returns its budget and admits held
+ *   requests.  One request per simulation at a time (LCP_ERR_INVALID_ARG).
+ *
+ * Caller-owned contexts: lcp_server_admit counts lcp_footprint against the
+ * budget (LCP_ERR_REJECTED when it would be exceeded), lcp_server_submit
+ * queues a solve of an admitted context, lcp_server_release returns the budget
+ * (and admits held simulation requests).
+ *
+ * lcp_server_poll waits at most timeout_us for the ticket (LCP_ERR_TIMEOUT
+ * otherwise), copies x (host, at least n doubles) and the stats, and returns
+ * the solve's (or, after a solve, the time step's) status.  lcp_server_stats:
+ * bytes counted against the budget, requests waiting (held or queued), and
+ * requests running. */
 typedef struct lcp_server lcp_server;
 LCP_API int lcp_server_create(int workers, size_t hbm_budget_bytes, lcp_server** out);
 LCP_API void lcp_server_destroy(lcp_server* srv);
@@ -217,6 +241,11 @@ LCP_API int lcp_server_release(lcp_server* srv, lcp_ctx* ctx);
 LCP_API int lcp_server_submit(lcp_server* srv, lcp_ctx* ctx, int method, double tol, uint64_t* ticket);
 LCP_API int lcp_server_poll(lcp_server* srv, uint64_t ticket, double* x, int x_len, lcp_stats* st, int timeout_us);
 LCP_API int lcp_server_stats(lcp_server* srv, size_t* resident_bytes, int* queued, int* in_flight);
+LCP_API int lcp_server_open(lcp_server* srv, const lcp_config* cfg, int n_bodies, const double* centers,
+                            const double* axes, uint64_t* sim);
+LCP_API int lcp_server_request(lcp_server* srv, uint64_t sim, int method, double tol, double step_dt,
+                               uint64_t* ticket);
+LCP_API int lcp_server_close(lcp_server* srv, uint64_t sim);
 
 /* Kernel timing.  lcp_profile(ctx, 1) clears the record and starts timing
  * every stresslet-sum launch with CUDA events on the context's stream;

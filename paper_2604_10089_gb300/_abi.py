@@ -101,6 +101,10 @@ PROTOTYPES = {
     "lcp_server_submit": (_I, [_P, _P, _I, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]),
     "lcp_server_poll": (_I, [_P, ctypes.c_uint64, _D, _I, ctypes.POINTER(lcp_stats), _I]),
     "lcp_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "lcp_server_open": (_I, [_P, ctypes.POINTER(lcp_config), _I, _D, _D, ctypes.POINTER(ctypes.c_uint64)]),
+    "lcp_server_request": (_I, [_P, ctypes.c_uint64, _I, ctypes.c_double, ctypes.c_double,
+                                ctypes.POINTER(ctypes.c_uint64)]),
+    "lcp_server_close": (_I, [_P, ctypes.c_uint64]),
 }
 
 _lib = None

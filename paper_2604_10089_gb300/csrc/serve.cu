@@ -56,9 +56,23 @@ extern "C" int lcp_batch_solve(lcp_ctx** ctxs, int count, int method, double tol
 namespace {
 struct Request {
   uint64_t ticket;
-  lcp_ctx* ctx;
+  lcp_ctx* ctx;      // caller-owned context, or NULL for a server-owned simulation
+  uint64_t sim;      // simulation id when ctx is NULL
   int method;
   double tol;
+  double step_dt;    // > 0: advance the simulation by one time step after the solve
+};
+// A simulation whose context the server owns: created when its estimated
+// device footprint fits the budget, kept resident across requests, destroyed
+// on close.
+struct Sim {
+  lcp_config cfg{};
+  int M = 0;
+  std::vector<double> centers, axes;
+  lcp_ctx* ctx = nullptr;
+  size_t est = 0;          // estimated device footprint (lcp_footprint_estimate)
+  size_t reserved = 0;     // bytes counted against the budget (0: not admitted)
+  bool busy = false;       // a request is pending, queued or running
 };
 struct Result {
   int status = LCP_OK;
@@ -70,7 +84,10 @@ struct Result {
 struct lcp_server {
   std::mutex mu;
   std::condition_variable cv_q, cv_done;
-  std::deque<Request> queue;
+  std::deque<Request> queue;                       // admitted, waiting for a worker
+  std::deque<Request> held;                        // simulations waiting for budget (FIFO)
+  std::unordered_map<uint64_t, Sim> sims;
+  uint64_t next_sim = 1;
   std::unordered_map<uint64_t, Result> done;
   std::unordered_map<lcp_ctx*, size_t> admitted;   // context -> bytes counted against the budget
   std::unordered_set<lcp_ctx*> busy;               // queued or running
@@ -81,31 +98,76 @@ struct lcp_server {
   std::vector<std::thread> threads;
 };
 
+// Moves held simulation requests to the run queue, first come first served,
+// while their estimated footprints fit the budget (caller holds the lock).
+static void admit_held(lcp_server* s) {
+  while (!s->held.empty()) {
+    const Request& h = s->held.front();
+    Sim& x = s->sims[h.sim];
+    const size_t need = x.reserved ? 0 : x.est;
+    if (s->resident + need > s->budget) break;
+    x.reserved += need;
+    s->resident += need;
+    s->queue.push_back(h);
+    s->held.pop_front();
+  }
+}
+
 static void server_worker(lcp_server* s) {
   cudaSetDevice(s->device);
   for (;;) {
     Request r;
+    Sim* sim = nullptr;
+    lcp_ctx* c = nullptr;
     {
       std::unique_lock<std::mutex> lock(s->mu);
       s->cv_q.wait(lock, [&] { return s->stop || !s->queue.empty(); });
       if (s->stop && s->queue.empty()) return;
       r = s->queue.front();
       s->queue.pop_front();
+      if (r.ctx) {
+        c = r.ctx;
+      } else {
+        sim = &s->sims[r.sim];   // stays valid: a busy simulation is never erased
+        c = sim->ctx;
+      }
     }
     Result res;
-    lcp_ctx* c = r.ctx;
-    res.status = lcp_solve_device(c, r.method, r.tol, nullptr, c->tmp_n3, &res.st);
-    res.x.resize(c->n);
-    if (c->n > 0 && (res.status == LCP_OK || res.status == LCP_ERR_NOT_CONVERGED)) {
-      if (cudaMemcpyAsync(res.x.data(), c->tmp_n3, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream) !=
-              cudaSuccess ||
-          cudaStreamSynchronize(c->stream) != cudaSuccess)
-        res.status = LCP_ERR_CUDA;
+    if (!c) {   // first request of an admitted simulation: create its context
+      lcp_ctx* nc = nullptr;
+      res.status = lcp_setup(&sim->cfg, sim->M, sim->centers.data(), sim->axes.empty() ? nullptr : sim->axes.data(),
+                             0, nullptr, &nc);
+      if (res.status == LCP_OK) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        sim->ctx = nc;
+        c = nc;
+      }
+    }
+    if (c) {
+      res.status = lcp_solve_device(c, r.method, r.tol, nullptr, c->tmp_n3, &res.st);
+      res.x.resize(c->n);
+      if (c->n > 0 && (res.status == LCP_OK || res.status == LCP_ERR_NOT_CONVERGED)) {
+        if (cudaMemcpyAsync(res.x.data(), c->tmp_n3, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+          res.status = LCP_ERR_CUDA;
+      }
+      if (sim && r.step_dt > 0.0 && res.status == LCP_OK) res.status = lcp_step(c, r.step_dt, nullptr, nullptr);
     }
     {
       std::lock_guard<std::mutex> lock(s->mu);
+      if (sim) {
+        // a context can outgrow its estimate (more contacts than estimated):
+        // the excess is counted from now on
+        if (c && c->bytes > sim->reserved) {
+          s->resident += c->bytes - sim->reserved;
+          sim->reserved = c->bytes;
+        }
+        sim->busy = false;
+      } else {
+        s->busy.erase(c);
+      }
       s->done[r.ticket] = std::move(res);
-      s->busy.erase(c);
     }
     s->cv_done.notify_all();
   }
@@ -130,6 +192,9 @@ extern "C" void lcp_server_destroy(lcp_server* s) {
   }
   s->cv_q.notify_all();
   for (auto& th : s->threads) th.join();
+  cudaSetDevice(s->device);
+  for (auto& kv : s->sims)
+    if (kv.second.ctx) lcp_destroy(kv.second.ctx);
   delete s;
 }
 
@@ -152,6 +217,8 @@ extern "C" int lcp_server_release(lcp_server* s, lcp_ctx* ctx) {
   if (s->busy.count(ctx)) return LCP_ERR_INVALID_ARG;
   s->resident -= it->second;
   s->admitted.erase(it);
+  admit_held(s);
+  s->cv_q.notify_all();
   return LCP_OK;
 }
 
@@ -164,7 +231,7 @@ extern "C" int lcp_server_submit(lcp_server* s, lcp_ctx* ctx, int method, double
     if (s->busy.count(ctx)) return LCP_ERR_INVALID_ARG;
     *ticket = s->next_ticket++;
     s->busy.insert(ctx);
-    s->queue.push_back(Request{*ticket, ctx, method, tol});
+    s->queue.push_back(Request{*ticket, ctx, 0, method, tol, 0.0});
   }
   s->cv_q.notify_one();
   return LCP_OK;
@@ -192,7 +259,80 @@ extern "C" int lcp_server_stats(lcp_server* s, size_t* resident_bytes, int* queu
   if (!s) return LCP_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(s->mu);
   if (resident_bytes) *resident_bytes = s->resident;
-  if (queued) *queued = (int)s->queue.size();
-  if (in_flight) *in_flight = (int)s->busy.size() - (int)s->queue.size();
+  int busy = (int)s->busy.size();
+  for (const auto& kv : s->sims) busy += kv.second.busy ? 1 : 0;
+  const int waiting = (int)(s->queue.size() + s->held.size());
+  if (queued) *queued = waiting;
+  if (in_flight) *in_flight = busy - waiting;
+  return LCP_OK;
+}
+
+// ---------------------------------------------------------------- simulations
+extern "C" int lcp_server_open(lcp_server* s, const lcp_config* cfg, int n_bodies, const double* centers,
+                               const double* axes, uint64_t* sim) {
+  if (!s || !cfg || n_bodies < 1 || !centers || !sim) return LCP_ERR_INVALID_ARG;
+  Sim x;
+  x.cfg = *cfg;
+  x.cfg.own_stream = 1;        // every simulation runs on its own stream
+  x.cfg.cuda_stream = nullptr;
+  x.M = n_bodies;
+  x.centers.assign(centers, centers + 3 * (size_t)n_bodies);
+  if (axes) x.axes.assign(axes, axes + 3 * (size_t)n_bodies);
+  // contacts are not known before the context exists: six per body bounds the
+  // packings of the workloads (contacts grow the estimate only slightly)
+  const int st = lcp_footprint_estimate(&x.cfg, n_bodies, 6 * n_bodies, &x.est);
+  if (st != LCP_OK) return st;
+  std::lock_guard<std::mutex> lock(s->mu);
+  *sim = s->next_sim++;
+  s->sims.emplace(*sim, std::move(x));
+  return LCP_OK;
+}
+
+extern "C" int lcp_server_request(lcp_server* s, uint64_t sim, int method, double tol, double step_dt,
+                                  uint64_t* ticket) {
+  if (!s || !ticket || !(tol >= 0.0) || !(step_dt >= 0.0)) return LCP_ERR_INVALID_ARG;
+  if (method != LCP_MONO_PQN && method != LCP_BI_PQN && method != LCP_BB_PGD) return LCP_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->sims.find(sim);
+    if (it == s->sims.end() || it->second.busy) return LCP_ERR_INVALID_ARG;
+    Sim& x = it->second;
+    if (!x.reserved && x.est > s->budget) return LCP_ERR_REJECTED;   // can never fit
+    *ticket = s->next_ticket++;
+    x.busy = true;
+    const Request r{*ticket, nullptr, sim, method, tol, step_dt};
+    if (x.reserved) {
+      s->queue.push_back(r);
+    } else {
+      s->held.push_back(r);   // behind earlier held requests: first come, first admitted
+      admit_held(s);
+    }
+  }
+  s->cv_q.notify_all();
+  return LCP_OK;
+}
+
+extern "C" int lcp_server_close(lcp_server* s, uint64_t sim) {
+  if (!s) return LCP_ERR_INVALID_ARG;
+  lcp_ctx* ctx = nullptr;
+  size_t reserved = 0;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->sims.find(sim);
+    if (it == s->sims.end() || it->second.busy) return LCP_ERR_INVALID_ARG;
+    ctx = it->second.ctx;
+    reserved = it->second.reserved;
+    s->sims.erase(it);
+  }
+  if (ctx) {
+    cudaSetDevice(s->device);
+    lcp_destroy(ctx);   // the memory is free before its budget is handed on
+  }
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->resident -= reserved;
+    admit_held(s);
+  }
+  s->cv_q.notify_all();
   return LCP_OK;
 }

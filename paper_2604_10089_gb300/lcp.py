@@ -300,6 +300,28 @@ def lcp_server_poll(srv, ticket: int, n: int, timeout_us: int):
     return status, x[:n], st.as_dict()
 
 
+def lcp_server_open(srv, cfg: _abi.lcp_config, centers, axes=None) -> int:
+    """Registers a server-owned simulation; returns its id."""
+    c = _f64(centers).reshape(-1, 3)
+    a = None if axes is None else _f64(axes, c.shape)
+    sim = ctypes.c_uint64()
+    _check(_lib().lcp_server_open(srv, ctypes.byref(cfg), c.shape[0], _dptr(c), None if a is None else _dptr(a),
+                                  ctypes.byref(sim)), None)
+    return sim.value
+
+
+def lcp_server_request(srv, sim: int, method: int, tol: float, step_dt: float = 0.0) -> int:
+    """Queues (or holds until the budget admits it) a solve of the simulation; returns the ticket."""
+    t = ctypes.c_uint64()
+    _check(_lib().lcp_server_request(srv, ctypes.c_uint64(sim), int(method), float(tol), float(step_dt),
+                                     ctypes.byref(t)), None)
+    return t.value
+
+
+def lcp_server_close(srv, sim: int) -> None:
+    _check(_lib().lcp_server_close(srv, ctypes.c_uint64(sim)), None)
+
+
 def lcp_server_stats(srv):
     b, q, f = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
     _check(_lib().lcp_server_stats(srv, ctypes.byref(b), ctypes.byref(q), ctypes.byref(f)), None)

@@ -12,7 +12,24 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2604_10089_gb300 as L  # noqa: E402
+from oracle.contacts import contact_matrix, detect_contacts  # noqa: E402
+from oracle.lcp import kkt_abs  # noqa: E402
+from oracle.mf import MatrixFreeMobility  # noqa: E402
 from workloads import batched_instances  # noqa: E402
+
+from .cases import MISMATCH_REL, kkt_bound  # noqa: E402
+
+
+def check_against_oracle(inst, x, g_gpu, hi_mvps):
+    """KKT error of x with the matrix-free FP64 oracle's MVP and b: <= tol + eps_op."""
+    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, mu=inst.viscosity)
+    pairs, normals, gaps = detect_contacts(inst.centers, inst.contact_radius, inst.delta)
+    D = contact_matrix(inst.n_bodies, pairs, normals)
+    b = gaps / inst.dt + D.T @ mf.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes)
+    g = D.T @ mf.apply(D @ x) + b
+    eps_op, mismatch = kkt_bound(inst.tol, x, g, g_gpu, b, hi_mvps)
+    assert mismatch <= MISMATCH_REL * max(1.0, np.linalg.norm(b)), mismatch
+    assert kkt_abs(x, g) <= inst.tol + eps_op
 
 
 @pytest.fixture(scope="module")
@@ -49,6 +66,10 @@ def test_batch_equals_alone(small_batch):
         assert all(s == L.LCP_OK for s in statuses)
         for a, x in zip(alone, xs):
             assert np.array_equal(a, x.cpu().numpy())
+        # and every batched result against the oracle
+        for c, i, x, st in zip(ctxs, small_batch, xs, stats):
+            xh = x.cpu().numpy()
+            check_against_oracle(i, xh, L.lcp_apply_A(c, xh, L.LCP_HIGH) + L.lcp_get_b(c), st["hi_mvps"])
     finally:
         for c in ctxs:
             L.lcp_destroy(c)
@@ -95,6 +116,75 @@ def test_server_continuous_batching_and_admission(small_batch):
     finally:
         for c in ctxs:
             L.lcp_destroy(c)
+
+
+def test_server_simulations_held_admission(small_batch):
+    """Server-owned simulations: each request carries its problem, the server creates the
+    context only when its estimated footprint fits the budget (holding the request until
+    then), keeps it resident across time steps and frees it on close.  Results equal solving
+    alone (two steps each), the first solves are checked against the oracle, and the budget
+    is never exceeded."""
+    insts = small_batch[:6]
+    cfgs = [L.config_for(i, L.LCP_MIXED) for i in insts]
+    est = [L.lcp_footprint_estimate(c, i.n_bodies, 6 * i.n_bodies) for c, i in zip(cfgs, insts)]
+    budget = sum(sorted(est)[:2]) + max(est)          # at most three at once, often two
+    # alone: solve, step, solve on a context of its own
+    alone = []
+    for c, i in zip(cfgs, insts):
+        ctx = L.lcp_setup(c, i.centers, i.axes)
+        try:
+            x1, _, _ = L.lcp_solve(ctx, L.LCP_BI_PQN, i.tol)
+            L.lcp_step(ctx, i.dt)
+            x2, _, _ = L.lcp_solve(ctx, L.LCP_BI_PQN, i.tol)
+            alone.append((x1, x2, L.lcp_sizes(ctx)[2]))
+        finally:
+            L.lcp_destroy(ctx)
+    srv = L.lcp_server_create(3, budget)
+    try:
+        sims = [L.lcp_server_open(srv, c, i.centers, i.axes) for c, i in zip(cfgs, insts)]
+        tickets = {k: L.lcp_server_request(srv, sims[k], L.LCP_BI_PQN, insts[k].tol, insts[k].dt)
+                   for k in range(len(sims))}
+        results = {k: [] for k in range(len(sims))}
+        saw_held = False
+        t_end = time.time() + 180
+        while tickets and time.time() < t_end:
+            resident, queued, _ = L.lcp_server_stats(srv)
+            assert resident <= budget
+            saw_held = saw_held or queued > 0
+            for k, t in list(tickets.items()):
+                n = alone[k][0].size if not results[k] else alone[k][2]
+                status, x, st = L.lcp_server_poll(srv, t, n, 1000)
+                if status == L.LCP_ERR_TIMEOUT:
+                    continue
+                assert status == L.LCP_OK and st["converged"] == 1
+                results[k].append((x, st))
+                if len(results[k]) == 1:        # next step: solve only
+                    tickets[k] = L.lcp_server_request(srv, sims[k], L.LCP_BI_PQN, insts[k].tol, 0.0)
+                else:
+                    del tickets[k]
+                    L.lcp_server_close(srv, sims[k])
+        assert not tickets and saw_held
+        for k in range(len(sims)):
+            assert np.array_equal(results[k][0][0], alone[k][0])
+            assert np.array_equal(results[k][1][0], alone[k][1])
+        # the first solves against the oracle (the GPU gradient from a context of its own)
+        for k, i in enumerate(insts[:3]):
+            ctx = L.lcp_setup(cfgs[k], i.centers, i.axes)
+            try:
+                x = results[k][0][0]
+                g_gpu = L.lcp_apply_A(ctx, x, L.LCP_HIGH) + L.lcp_get_b(ctx)
+            finally:
+                L.lcp_destroy(ctx)
+            check_against_oracle(i, x, g_gpu, results[k][0][1]["hi_mvps"])
+        assert L.lcp_server_stats(srv)[0] == 0
+        # a simulation that can never fit is rejected at once
+        big = L.lcp_server_open(srv, cfgs[0], np.arange(3 * 2000, dtype=float).reshape(-1, 3) * 3.0)
+        with pytest.raises(L.LcpError) as err:
+            L.lcp_server_request(srv, big, L.LCP_BI_PQN, 1e-8)
+        assert err.value.status == L.LCP_ERR_REJECTED
+        L.lcp_server_close(srv, big)
+    finally:
+        L.lcp_server_destroy(srv)
 
 
 def test_autotuned_kernel_gives_the_same_solution(small_batch):
