@@ -45,15 +45,15 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 # hash of the symmetric kernel's file was renewed when its unit bookkeeping moved
 # to a shared header, the kernel's code unchanged).
 PAIR32_TRAFFIC = {
-    "k_pair32_sym_p8rc": {"file": "stokes_sym.cu", "source_sha1": "ddfaf8c02312a9c9655a89936fe3f971cc5703c5",
-                          "bytes_per_launch": 1460480},
+    "k_pair32_sym_p8rc5": {"file": "stokes_sym.cu", "source_sha1": "d92242286d69cd8195fb9e173b2684de897e684d",
+                           "bytes_per_launch": 1042432},
     "k_pair32": {"file": "stokes.cu", "source_sha1": "298b391165dc32f4d22c484bf6d970a4f86ee95e",
                  "bytes_per_launch": 665088},
 }
 # FP32 operations of the symmetric kernel per unordered node pair (both ordered
 # terms): r 3, |r|^2 6, |r|^-2 1, d 3, r.d 5, t 3, r.wn_q 5, r.wn_p 5, scales 2,
 # two accumulations 12 = 45 flops (FMA = 2), i.e. 22.5 per ordered pair; the
-# variants that take |r|^-2 from a reciprocal (names ending in "rc") do one
+# variants that take |r|^-2 from a reciprocal ("rc" in the name) do one
 # multiply fewer: 44, i.e. 22 per ordered pair.
 SYM_FLOPS_PER_ORDERED_PAIR = 22.5
 SYM_RC_FLOPS_PER_ORDERED_PAIR = 22.0
@@ -368,7 +368,7 @@ def run_ours(args, rank, world, local):
                 "flops_note": "algorithmic work of the operator: 32 flops per ordered node pair, N(N-1) pairs",
                 "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (nominal max clock)"}
         if variant.startswith("sym"):
-            fpp = SYM_RC_FLOPS_PER_ORDERED_PAIR if variant.endswith("rc") else SYM_FLOPS_PER_ORDERED_PAIR
+            fpp = SYM_RC_FLOPS_PER_ORDERED_PAIR if "rc" in variant[len("sym_"):] else SYM_FLOPS_PER_ORDERED_PAIR
             hw = pairs * fpp / avg32 / 1e12
             roof["kernel_flops_per_pair"] = fpp
             roof["executed_tflops"] = hw

@@ -527,6 +527,114 @@ __global__ void k_rhs(int N, int ns, int M, double a, double mu, const double* _
   rhs[3 * p + 2] = s2 - u2;
 }
 
+// The same right-hand side in double-FP32 arithmetic (mixed-precision mode):
+// two targets per thread in the lanes of packed double-float values; every
+// sum and product is an error-free transformation (TwoSum, TwoProd by FMA),
+// |r|^-1 is the special-function seed refined by one Newton step in
+// double-float, so each term carries ~2^-44 relative error, on the FP32 pipe
+// (64x the FP64 rate).  Stokeslet and rotlet strengths are pre-scaled by
+// 1/(8 pi mu) in FP64 before the split.
+constexpr int RHS_THREADS = 128;
+__device__ __forceinline__ float rsqrt_seed(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ D2 dneg(D2 a) { return {neg2(a.hi), neg2(a.lo)}; }
+__device__ __forceinline__ D2 ddup(float2 v) { return {f2(v.x), f2(v.y)}; }
+
+__global__ void __launch_bounds__(RHS_THREADS) k_rhs_df(int N, int ns, int M, double a, double mu,
+                                                        const double* __restrict__ tmpl64,
+                                                        const double* __restrict__ centers,
+                                                        const double* __restrict__ FT,
+                                                        const double* __restrict__ axes, double* __restrict__ rhs) {
+  __shared__ float2 s_c[RHS_THREADS * 3];    // (hi, lo) of every centre component
+  __shared__ float2 s_ft[RHS_THREADS * 6];   // (hi, lo) of F / (8 pi mu), T / (8 pi mu)
+  const int t0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  int pc[2], bi[2], qi[2];
+#pragma unroll
+  for (int u = 0; u < 2; u++) {
+    pc[u] = min(t0 + u, N - 1);
+    bi[u] = pc[u] / ns;
+    qi[u] = pc[u] - bi[u] * ns;
+  }
+  // target positions x_p = c_i + xi_q in double-float, the two targets in the lanes
+  D2 X[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const dfl c0 = df_split(centers[3 * bi[0] + d]), c1 = df_split(centers[3 * bi[1] + d]);
+    const dfl x0 = df_split(tmpl64[8 * qi[0] + d]), x1 = df_split(tmpl64[8 * qi[1] + d]);
+    X[d] = dadd_n({make_float2(c0.hi, c1.hi), make_float2(c0.lo, c1.lo)},
+                  {make_float2(x0.hi, x1.hi), make_float2(x0.lo, x1.lo)});
+  }
+  const double k = 1.0 / (8.0 * LCP_PI * mu);
+  D2 U[3] = {{f2(0.f), f2(0.f)}, {f2(0.f), f2(0.f)}, {f2(0.f), f2(0.f)}};
+  for (int j0 = 0; j0 < M; j0 += RHS_THREADS) {
+    const int nb = min(RHS_THREADS, M - j0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
+      const dfl v = df_split(centers[3 * j0 + t]);
+      s_c[t] = make_float2(v.hi, v.lo);
+    }
+    for (int t = threadIdx.x; t < 6 * nb; t += blockDim.x) {
+      const dfl v = df_split(k * FT[6 * j0 + t]);
+      s_ft[t] = make_float2(v.hi, v.lo);
+    }
+    __syncthreads();
+    for (int b = 0; b < nb; b++) {
+      D2 R[3], F[3], T[3];
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        R[d] = dadd_n(X[d], dneg(ddup(s_c[3 * b + d])));
+        F[d] = ddup(s_ft[6 * b + d]);
+        T[d] = ddup(s_ft[6 * b + 3 + d]);
+      }
+      const D2 r2 = dadd_u(dadd_u(dsq_u(R[0]), dsq_u(R[1])), dsq_u(R[2]));
+      // |r|^-1: seed, then one Newton step y = y0 + y0 (1 - r2 y0^2) / 2 in double-float
+      const float2 y0 = make_float2(rsqrt_seed(r2.hi.x), rsqrt_seed(r2.hi.y));
+      const float2 yy = mul2(y0, y0);
+      const D2 tt = dmul_u(r2, {yy, fma2(y0, y0, neg2(yy))});
+      const float2 hh = sub2(sub2(f2(1.f), tt.hi), tt.lo);
+      const D2 ir = fast2sum2(y0, mul2(mul2(f2(0.5f), y0), hh));
+      const D2 ir3 = dmul_u(dsq_u(ir), ir);
+      const D2 rF = dadd_n(dadd_u(dmul_u(R[0], F[0]), dmul_u(R[1], F[1])), dmul_u(R[2], F[2]));
+      const D2 s = dmul_u(rF, ir3);
+      const D2 cx[3] = {dadd_u(dmul_u(T[1], R[2]), dneg(dmul_u(T[2], R[1]))),
+                        dadd_u(dmul_u(T[2], R[0]), dneg(dmul_u(T[0], R[2]))),
+                        dadd_u(dmul_u(T[0], R[1]), dneg(dmul_u(T[1], R[0])))};
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        const D2 term = dadd_u(dadd_u(dmul_u(F[d], ir), dmul_u(R[d], s)), dmul_u(cx[d], ir3));
+        U[d] = dadd_n(U[d], term);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; u++) {
+    const int p = t0 + u;
+    if (p >= N) continue;
+    const double* xi = tmpl64 + 8 * qi[u];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    if (axes) {
+      const int i = bi[u];
+      const double nx = xi[0] / a, ny = xi[1] / a, nz = xi[2] / a;
+      const double ex = axes[3 * i], ey = axes[3 * i + 1], ez = axes[3 * i + 2];
+      const double ne = nx * ex + ny * ey + nz * ez;
+      if (ne >= 0.0) {
+        s0 = -(ex - ne * nx);
+        s1 = -(ey - ne * ny);
+        s2 = -(ez - ne * nz);
+      }
+    }
+    const double u0 = u ? (double)U[0].hi.y + (double)U[0].lo.y : (double)U[0].hi.x + (double)U[0].lo.x;
+    const double u1 = u ? (double)U[1].hi.y + (double)U[1].lo.y : (double)U[1].hi.x + (double)U[1].lo.x;
+    const double u2 = u ? (double)U[2].hi.y + (double)U[2].lo.y : (double)U[2].hi.x + (double)U[2].lo.x;
+    rhs[3 * p] = s0 - u0;
+    rhs[3 * p + 1] = s1 - u1;
+    rhs[3 * p + 2] = s2 - u2;
+  }
+}
+
 __global__ void k_neg(int L, const double* __restrict__ x, double* __restrict__ y) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < L) y[t] = -x[t];
@@ -639,11 +747,19 @@ int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
   return LCP_OK;
 }
 
+// FP64 mode: the FP64 kernel; mixed mode: the double-float kernel (same
+// accuracy class, ~2^-44 per operation, on the FP32 pipe).
 int stokes_rhs(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs) {
   const int N = ctx->N;
-  ++ctx->nlaunch, k_rhs<<<(N + 127) / 128, 128, 0, ctx->stream>>>(N, ctx->ns, ctx->M, ctx->cfg.radius, ctx->cfg.viscosity,
-                                                  ctx->tmpl64, ctx->centers, FT,
-                                                  include_slip && ctx->has_axes ? ctx->axes : nullptr, rhs);
+  const double* ax = include_slip && ctx->has_axes ? ctx->axes : nullptr;
+  if (ctx->cfg.precision == LCP_FP64)
+    ++ctx->nlaunch, k_rhs<<<(N + 127) / 128, 128, 0, ctx->stream>>>(N, ctx->ns, ctx->M, ctx->cfg.radius,
+                                                                    ctx->cfg.viscosity, ctx->tmpl64, ctx->centers,
+                                                                    FT, ax, rhs);
+  else
+    ++ctx->nlaunch, k_rhs_df<<<(N + 2 * RHS_THREADS - 1) / (2 * RHS_THREADS), RHS_THREADS, 0, ctx->stream>>>(
+                        N, ctx->ns, ctx->M, ctx->cfg.radius, ctx->cfg.viscosity, ctx->tmpl64, ctx->centers, FT, ax,
+                        rhs);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }

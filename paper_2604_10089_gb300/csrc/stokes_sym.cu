@@ -158,7 +158,9 @@ __device__ __forceinline__ void pair32_sym_body(int N, int ns, int ns_pad, SymUn
   static_assert(TPT * THR == SYM_TB && TPT % 2 == 0, "a thread's targets fill FP32x2 packs of the block");
   constexpr int NPK = TPT / 2;       // FP32x2 packs of targets per thread
   constexpr int WARPS = THR / 32;
-  constexpr int NV = BATCH == 8 ? 32 : (BATCH == 4 ? 16 : 8);
+  // values per batch (3 per source) padded to a power of two for the transposing reduction
+  constexpr int NV = 3 * BATCH <= 8 ? 8 : (3 * BATCH <= 16 ? 16 : 32);
+  static_assert(3 * BATCH <= 32, "at most 32 values per warp reduction");
   constexpr int LPV = 32 / NV;   // lanes holding each reduced value
   extern __shared__ float4 smem4[];
   // AOS: s_t [ns_pad][3] float4 = (nx,nx,ny,ny) (nz,nz,wx,wx) (wy,wy,wz,wz);
@@ -403,6 +405,8 @@ PAIR32_SYM_VARIANT(k_pair32_sym_t8b4, true, 4, 3, false, 8, 64)
 // sources per reduction 1.69.
 PAIR32_SYM_VARIANT_P(k_pair32_sym_p8rc, 4, 3, 8, 64, true, true)
 PAIR32_SYM_VARIANT_P(k_pair32_sym_p4rc, 4, 3, 4, 128, true, true)
+// five sources per reduction: 15 of the 16 reduced values are used (12 of 16 with four)
+PAIR32_SYM_VARIANT_P(k_pair32_sym_p8rc5, 5, 3, 8, 64, true, true)
 
 typedef void (*Pair32SymKernel)(int, int, int, SymUnits, const float*, const float*, const float*, double*, float*);
 typedef void (*Pair32SymKernelP)(int, int, int, SymUnits, const float*, const float*, const float*, double*, float*,
@@ -424,7 +428,8 @@ static const Pair32SymVariant kSymVariants[] = {
     {k_pair32_sym_t8b2, nullptr, true, 2, 64, "sym_t8b2"},
     {k_pair32_sym_t8b4, nullptr, true, 4, 64, "sym_t8b4"},
     {nullptr, k_pair32_sym_p8rc, true, 4, 64, "sym_p8rc"},
-    {nullptr, k_pair32_sym_p4rc, true, 4, 128, "sym_p4rc"}};
+    {nullptr, k_pair32_sym_p4rc, true, 4, 128, "sym_p4rc"},
+    {nullptr, k_pair32_sym_p8rc5, true, 5, 64, "sym_p8rc5"}};
 constexpr int kNumSymVariants = sizeof(kSymVariants) / sizeof(kSymVariants[0]);
 
 // out_p = forward partials + reverse rows of the target blocks before body(p)
@@ -575,8 +580,16 @@ int stokes_sym_configure(lcp_ctx* ctx) {
   // fastest measured form where that fits the size
   ctx->sym = U >= 4 * ctx->symv_grid[0];
   ctx->sym_v = 0;
-  for (int v = 0; v < kNumSymVariants && v < 16; v++)
-    if (std::strcmp(kSymVariants[v].name, "sym_p8rc") == 0 && ctx->symv_occ[v] > 0) ctx->sym_v = v;
+  int v8 = -1, v85 = -1;
+  for (int v = 0; v < kNumSymVariants && v < 16; v++) {
+    if (std::strcmp(kSymVariants[v].name, "sym_p8rc") == 0 && ctx->symv_occ[v] > 0) v8 = v;
+    if (std::strcmp(kSymVariants[v].name, "sym_p8rc5") == 0 && ctx->symv_occ[v] > 0) v85 = v;
+  }
+  // five sources per reduction save reduction work unless the padding of the
+  // nodes to a multiple of five costs a CTA per SM (216 spheres x 242 nodes:
+  // 1.518 vs 1.536 ms; 512 nodes per sphere: 1.93 vs 1.52 ms)
+  if (v8 >= 0) ctx->sym_v = v8;
+  if (v85 >= 0 && (v8 < 0 || ctx->symv_occ[v85] >= ctx->symv_occ[v8])) ctx->sym_v = v85;
   ctx->sym_off = (int*)ctx_alloc(ctx, sizeof(int) * (ntb + 1));
   ctx->sym_roff = (long long*)ctx_alloc(ctx, sizeof(long long) * (ntb + 1));
   // room for double-float (hi, lo) rows: the symmetric double-float kernel shares the buffer

@@ -23,7 +23,7 @@ struct SymUnits {
 // (it lands in the constant bank, which every lane of a warp reads at the same
 // address): per node q, float2 entries 6q + d = (-xi_d, -xi_d) and 6q + 3 + d =
 // (wn_d, wn_d); padding nodes sit far away with zero weight.
-constexpr int SYM_TPARAM_NODES = 512;
+constexpr int SYM_TPARAM_NODES = 520;   // 512 nodes per sphere, padded to a multiple of 5 (or 8)
 struct __align__(16) SymTmplParam {
   float4 v[SYM_TPARAM_NODES * 3];
 };

@@ -39,7 +39,7 @@ def small_batch():
     return insts
 
 
-VARIANTS = ("sym_a4", "sym_a4m4", "sym_a8m2", "sym_a2", "sym", "sym_t8b2", "sym_t8b4", "sym_p8rc", "sym_p4rc",
+VARIANTS = ("sym_a4", "sym_a4m4", "sym_a8m2", "sym_a2", "sym", "sym_t8b2", "sym_t8b4", "sym_p8rc", "sym_p4rc", "sym_p8rc5",
             "t2c8", "t1c8", "t2c16", "t2c4", "t1c16")
 
 

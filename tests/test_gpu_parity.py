@@ -83,14 +83,25 @@ def test_stresslet_apply_many_tiles(name, index, precision, tol):
         L.lcp_destroy(ctx)
 
 
-def test_rhs_and_rigid_velocity(c1):
-    case, ctx = c1
+@pytest.mark.parametrize("precision", [L.LCP_FP64, L.LCP_MIXED])
+def test_rhs_and_rigid_velocity(c1, precision):
+    """The GMRES right-hand side: FP64 kernel in FP64 mode, double-FP32 kernel in mixed mode."""
+    case, ctx64 = c1
     mob, inst = case["mob"], case["inst"]
-    FT = np.random.default_rng(4).standard_normal(6 * inst.n_bodies)
-    dFT = torch.tensor(FT, device=DEV)
-    rhs = torch.empty(mob.x.shape[0] * 3, dtype=torch.float64, device=DEV)
-    L.lcp_stokes_rhs_dev(ctx, dFT, True, rhs)
-    assert rel(rhs.cpu().numpy(), rhs_oracle(mob, FT, inst.axes)) <= 1e-13
+    ctx = ctx64 if precision == L.LCP_FP64 else L.lcp_setup(L.config_for(inst, precision), inst.centers,
+                                                              inst.axes)
+    try:
+        FT = np.random.default_rng(4).standard_normal(6 * inst.n_bodies)
+        dFT = torch.tensor(FT, device=DEV)
+        rhs = torch.empty(mob.x.shape[0] * 3, dtype=torch.float64, device=DEV)
+        L.lcp_stokes_rhs_dev(ctx, dFT, True, rhs)
+        assert rel(rhs.cpu().numpy(), rhs_oracle(mob, FT, inst.axes)) <= 1e-13
+        L.lcp_stokes_rhs_dev(ctx, dFT, False, rhs)
+        assert rel(rhs.cpu().numpy(), rhs_oracle(mob, FT)) <= 1e-13
+    finally:
+        if ctx is not ctx64:
+            L.lcp_destroy(ctx)
+    ctx = ctx64
     phi = np.random.default_rng(6).standard_normal(mob.x.shape[0] * 3)
     UO = torch.empty(6 * inst.n_bodies, dtype=torch.float64, device=DEV)
     L.lcp_rigid_velocity_dev(ctx, torch.tensor(phi, device=DEV), UO)
