@@ -84,7 +84,7 @@ def parse():
     p.add_argument("--batch-count", type=int, default=256)
     p.add_argument("--workers", type=int, default=12)
     p.add_argument("--sims", type=int, default=32)
-    p.add_argument("--sim-steps", type=int, default=3)
+    p.add_argument("--sim-steps", type=int, default=10)
     p.add_argument("--arrival-rate", type=float, default=8.0, help="requests/s per simulation (Poisson)")
     p.add_argument("--budget-frac", type=float, default=0.5, help="HBM budget as a fraction of all contexts")
     p.add_argument("--fp64-baseline", type=int, default=1,
@@ -593,7 +593,7 @@ def run_serving(args):
 # Bi-PQN, 8 x 16 coarse-grid low fidelity): the mean over the 20 timed solves of a GPU
 # bench run.  The reference arm has no GPU, so it takes its solve count from here; the
 # main arm uses the counts it measures itself.
-REFERENCE_MVPS = {"hi": 3.2, "lo": 18.3,
+REFERENCE_MVPS = {"hi": 3.15, "lo": 18.40,
                   "source": "mean over the 20 timed solves of a GB300 bench run at spheres216_grid11x22 "
                             "(mixed Bi-PQN, 8 x 16 low fidelity)"}
 
