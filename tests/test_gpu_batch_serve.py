@@ -216,12 +216,19 @@ def test_footprint_estimate_covers_context(small_batch):
             L.lcp_destroy(ctx)
 
 
-@pytest.mark.parametrize("name,index", [("spheres8_grid7x14", 2), ("spheres64_grid9x18", 1)])
+@pytest.mark.parametrize("name,index", [("spheres8_grid7x14", 2), ("spheres64_grid9x18", 1), ("grid16x32", 0)])
 def test_every_kernel_variant_applies_the_same_operator(name, index):
-    """Each FP32 variant (symmetric or plain, any tile shape) against the double-FP32 apply."""
+    """Each FP32 variant (symmetric or plain, any tile shape) against the double-FP32 apply;
+    grid16x32 is the largest sphere grid (512 nodes, padded to 515 for five-source batches)."""
     from workloads import make_instance
-    inst = make_instance(name, index)
-    ctx = L.lcp_setup(L.config_for(inst, L.LCP_MIXED), inst.centers, inst.axes)
+    if name == "grid16x32":
+        idx = np.stack(np.meshgrid(*[np.arange(k) for k in (4, 4, 2)], indexing="ij"), -1).reshape(-1, 3)
+        centers = idx * 2.7 + np.random.default_rng(3).uniform(-0.05, 0.05, (32, 3))
+        cfg = L.lcp_default_config(n_theta=16, n_phi=32, precision=L.LCP_MIXED)
+        ctx = L.lcp_setup(cfg, centers)
+    else:
+        inst = make_instance(name, index)
+        ctx = L.lcp_setup(L.config_for(inst, L.LCP_MIXED), inst.centers, inst.axes)
     try:
         n = 3 * L.lcp_sizes(ctx)[1]
         phi = torch.tensor(np.random.default_rng(9).standard_normal(n), device="cuda")
@@ -231,7 +238,11 @@ def test_every_kernel_variant_applies_the_same_operator(name, index):
         ref64 = torch.empty_like(phi)
         L.lcp_stokes_apply_dev(ctx, phi, ref64, L.LCP_FP64)
         for v in VARIANTS:
-            L.lcp_select_kernel_variant(ctx, v)
+            try:
+                L.lcp_select_kernel_variant(ctx, v)
+            except L.LcpError:
+                assert name == "grid16x32" and not v.startswith("sym_p")   # may not fit the largest grid
+                continue
             assert L.lcp_kernel_variant(ctx) == v
             L.lcp_stokes_apply_dev(ctx, phi, out, L.LCP_MIXED)
             err = float((out - ref).abs().max() / ref.abs().max())
