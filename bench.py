@@ -93,6 +93,9 @@ def parse():
                    help="also time this many forward-Euler steps (solve + lcp_step) of one configuration, with "
                         "the warm-started slip solve, and the first --trajectory-cold of them cold-started")
     p.add_argument("--trajectory-cold", type=int, default=10)
+    p.add_argument("--c4c5", type=int, default=1,
+                   help="also run the batched (256 instances) and serving (32 simulations) configurations "
+                        "once and add their results to the line")
     p.add_argument("--c2", type=int, default=1,
                    help="64-sphere report: Mono vs Bi-PQN, FP64 vs mixed, high-fidelity MVPs and the error "
                         "against the FP64 oracle")
@@ -351,6 +354,17 @@ def run_ours(args, rank, world, local):
             L.lcp_destroy(ctx_cold)
     L.lcp_destroy(ctx)
     c2 = c2_report(stream) if (args.c2 and rank == 0) else None
+    c4 = c5 = None
+    if args.c4c5 and rank == 0:
+        # the batched and serving configurations at their sizes (256 instances; 32 simulations,
+        # 3 steps each), two timed batches, without the minutes-long plain-FP64 baselines
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup, sub.fp64_baseline, sub.sim_steps = 6, 3, 0, 3
+        c4 = run_batched(sub)
+        c5 = run_serving(sub)
+        for d in (c4, c5):
+            d["fp64_baseline_note"] = ("plain FP64 one at a time is timed over every instance by "
+                                       "bench.py --mode batched / --mode serving")
 
     pairs = float(N) * (N - 1)
     avg32 = t32 / c32 / 1e3 if c32 else None
@@ -398,7 +412,7 @@ def run_ours(args, rank, world, local):
                                          + (", one evaluation per unordered pair (symmetric)" if sym_df else ""),
                "pairs_per_s": pairs / (tdf / cdf / 1e3), "share_of_timed_region": tdf / 1e3 / t_total}
     lowfi_desc = lowfi_description(lowfi)
-    return dict(t_total=t_total, lat=lat, clocks=clk, c2=c2, launches=launches, roof=roof, k64=k64, kdf=kdf, e2e=e2e, traj=traj,
+    return dict(t_total=t_total, lat=lat, clocks=clk, c2=c2, c4=c4, c5=c5, launches=launches, roof=roof, k64=k64, kdf=kdf, e2e=e2e, traj=traj,
                 lowfi=lowfi_desc, lowfi_cfg=lowfi,
                 comparison=comparison,
                 fp64=fp64, summary=summary, N=N, M=M)
@@ -499,7 +513,7 @@ def run_batched(args):
             "kernel_variants": variants, "clocks": clk,
             "config": {"workload": "256 packings, 8-128 spheres, 98 or 162 nodes per sphere, phi 0.30-0.45",
                        "method": "bi_pqn", "precision": "mixed", "tol": 1e-8}}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_serving(args):
@@ -586,7 +600,7 @@ def run_serving(args):
                        "method": "bi_pqn", "precision": "mixed", "tol": 1e-8,
                        "admission": "server-held: a simulation's context is created once its estimated "
                                     "footprint fits the budget"}}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # Mean high- and low-fidelity MVPs per LCP solve of the GPU path on this workload (mixed
@@ -759,7 +773,8 @@ def main():
         torch.distributed.init_process_group(backend=backend)
     if args.impl == "ours" and args.mode != "solve":
         if rank == 0:
-            run_batched(args) if args.mode == "batched" else run_serving(args)
+            line = run_batched(args) if args.mode == "batched" else run_serving(args)
+            print(json.dumps(line), flush=True)
         if world > 1:
             import torch
             torch.distributed.destroy_process_group()
@@ -808,7 +823,7 @@ def main():
             "roofline": r["roof"], "fp64_kernel": r["k64"], "df64_kernel": r["kdf"], "clocks": r["clocks"],
             "e2e": r["e2e"], "gpu_launches": r["launches"], "cpu_baseline": cpu,
             "fp64_mono_pqn": r["fp64"], "method_comparison_mixed": r["comparison"], "trajectory": r["traj"],
-            "c2_spheres64": r["c2"],
+            "c2_spheres64": r["c2"], "c4_batched": r["c4"], "c5_serving": r["c5"],
             "solver": s,
         }
         print(json.dumps(line), flush=True)
