@@ -41,11 +41,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # FP32 pair kernel at 216 spheres x 242 nodes, from an ncu capture, with the SHA-1 of
-# the device code it was taken on (reported as null once that code changes; the
-# hash of the symmetric kernel's file was renewed when its unit bookkeeping moved
-# to a shared header, the kernel's code unchanged).
+# the device code it was taken on (reported as null once that code changes; for the
+# symmetric kernels the hashed code is the pair kernels' part of their file, before the
+# finish kernel).
 PAIR32_TRAFFIC = {
-    "k_pair32_sym_p8rc5": {"file": "stokes_sym.cu", "source_sha1": "d92242286d69cd8195fb9e173b2684de897e684d",
+    "k_pair32_sym_p8rc5": {"file": "stokes_sym.cu", "source_sha1": "7c3da54fa3fcd6dd382fc924582e9560bd3f70e5",
                            "bytes_per_launch": 1042432},
     "k_pair32": {"file": "stokes.cu", "source_sha1": "298b391165dc32f4d22c484bf6d970a4f86ee95e",
                  "bytes_per_launch": 665088},
@@ -160,8 +160,8 @@ def source_sha1(kernel: str) -> str:
     if info["file"] == "stokes.cu":   # pair2 .. the plain variant table
         a = text.find(b"__device__ __forceinline__ void pair2(")
         b = text.find(b"constexpr int kNumPair32Variants")
-    else:                              # everything before the host code
-        a, b = 0, text.find(b"// ------------------------------------------------------------------ host side")
+    else:                              # the pair kernels: everything before the finish kernel
+        a, b = 0, text.find(b"// out_p = forward partials")
     return hashlib.sha1(text[a:b] if 0 <= a < b else text).hexdigest()
 
 

@@ -133,6 +133,7 @@ struct lcp_ctx {
   int symdf_grid = 0, symdf_slots = 0;   // the symmetric double-float kernel (stokes_sym_df.cu)
   int* sym_off = nullptr;          // [ntb + 1] first unit of each target block
   long long* sym_roff = nullptr;   // [ntb + 1] first float of each block's reverse rows
+  long long* sym_rbase = nullptr;  // [ntb + 1] roff[tb] - (first body + 1) * 3 ns: row of body i at + i * 3 ns
   float* sym_rev = nullptr;        // reverse partial sums, one row per unit (FP32, or (hi, lo) pairs)
   double *V = nullptr, *H = nullptr;  // Krylov basis [(m+1)][3N], Hessenberg etc.
   double* Z = nullptr;                 // preconditioned basis [m][3N] (flexible GMRES)

@@ -435,8 +435,10 @@ constexpr int kNumSymVariants = sizeof(kSymVariants) / sizeof(kSymVariants[0]);
 // out_p = forward partials + reverse rows of the target blocks before body(p)
 // (in block order) + (P phi)_p.  One thread per node component; the reverse
 // rows are read four blocks at a time (independent loads in flight).
+// rbase[tb] = roff[tb] - (first body of tb + 1) * 3 ns, so that the row of
+// (tb, body i) starts at rbase[tb] + i * 3 ns (no division per row).
 __global__ void k_finish_sym(int N, int ns, int splits, const double* __restrict__ partial,
-                             const float* __restrict__ rev, const long long* __restrict__ roff,
+                             const float* __restrict__ rev, const long long* __restrict__ rbase,
                              const double* __restrict__ coef, const double* __restrict__ tmpl64,
                              double* __restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -446,22 +448,20 @@ __global__ void k_finish_sym(int N, int ns, int splits, const double* __restrict
   for (int s = 0; s < splits; s++) a += partial[(size_t)s * 3 * N + t];
   const int i = p / ns, q = p - i * ns;
   const int nbefore = (i * ns + SYM_TB - 1) / SYM_TB;   // blocks whose first body is before i
-  const long long within = 3LL * q + d;
+  const long long within = (long long)i * 3 * ns + 3LL * q + d;
+  // the FP32 reverse rows are summed as a compensated FP32 pair (TwoSum) and
+  // converted once: FP64 adds run at 1/64 rate and dominated this kernel
+  float2 rs = make_float2(0.f, 0.f);
   float r4[4];
   int tb = 0;
   for (; tb + 4 <= nbefore; tb += 4) {
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const int fb = ((tb + u) * SYM_TB) / ns;
-      r4[u] = rev[roff[tb + u] + (long long)(i - fb - 1) * 3 * ns + within];
-    }
+    for (int u = 0; u < 4; u++) r4[u] = rev[rbase[tb + u] + within];
 #pragma unroll
-    for (int u = 0; u < 4; u++) a += (double)r4[u];
+    for (int u = 0; u < 4; u++) two_sum_acc(rs, r4[u]);
   }
-  for (; tb < nbefore; tb++) {
-    const int fb = (tb * SYM_TB) / ns;
-    a += (double)rev[roff[tb] + (long long)(i - fb - 1) * 3 * ns + within];
-  }
+  for (; tb < nbefore; tb++) two_sum_acc(rs, rev[rbase[tb] + within]);
+  a += (double)rs.x + (double)rs.y;
   const double* c = coef + 6 * i;
   const double* xi = tmpl64 + 8 * q;
   if (d == 0) a += c[0] + (c[4] * xi[2] - c[5] * xi[1]);
@@ -592,11 +592,17 @@ int stokes_sym_configure(lcp_ctx* ctx) {
   if (v85 >= 0 && (v8 < 0 || ctx->symv_occ[v85] >= ctx->symv_occ[v8])) ctx->sym_v = v85;
   ctx->sym_off = (int*)ctx_alloc(ctx, sizeof(int) * (ntb + 1));
   ctx->sym_roff = (long long*)ctx_alloc(ctx, sizeof(long long) * (ntb + 1));
+  ctx->sym_rbase = (long long*)ctx_alloc(ctx, sizeof(long long) * (ntb + 1));
   // room for double-float (hi, lo) rows: the symmetric double-float kernel shares the buffer
   ctx->sym_rev = (float*)ctx_alloc(ctx, 2 * sizeof(float) * (size_t)(roff[ntb] > 0 ? roff[ntb] : 1));
-  if (!ctx->sym_off || !ctx->sym_roff || !ctx->sym_rev) return LCP_ERR_OOM;
+  if (!ctx->sym_off || !ctx->sym_roff || !ctx->sym_rbase || !ctx->sym_rev) return LCP_ERR_OOM;
+  std::vector<long long> rbase(ntb + 1, 0);
+  for (int tb = 0; tb < ntb; tb++)
+    rbase[tb] = roff[tb] - (long long)((((long long)tb * SYM_TB) / ns) + 1) * 3 * ns;
   LCP_CUDA(cudaMemcpyAsync(ctx->sym_off, off.data(), sizeof(int) * (ntb + 1), cudaMemcpyHostToDevice, ctx->stream));
   LCP_CUDA(cudaMemcpyAsync(ctx->sym_roff, roff.data(), sizeof(long long) * (ntb + 1), cudaMemcpyHostToDevice,
+                           ctx->stream));
+  LCP_CUDA(cudaMemcpyAsync(ctx->sym_rbase, rbase.data(), sizeof(long long) * (ntb + 1), cudaMemcpyHostToDevice,
                            ctx->stream));
   LCP_CUDA(cudaStreamSynchronize(ctx->stream));
   return LCP_OK;
@@ -616,7 +622,8 @@ size_t stokes_sym_bytes(int M, int ns) {
   long long total = 0;
   for (long long tb = 0; tb < ntb; tb++) total += (long long)(M - 1 - (tb * SYM_TB) / ns) * 3 * ns;
   if (2 * sizeof(float) * (size_t)total > sym_rev_cap()) return 0;
-  return 2 * sizeof(float) * (size_t)(total > 0 ? total : 1) + (sizeof(int) + sizeof(long long)) * (size_t)(ntb + 1);
+  return 2 * sizeof(float) * (size_t)(total > 0 ? total : 1) +
+         (sizeof(int) + 2 * sizeof(long long)) * (size_t)(ntb + 1);
 }
 
 // (K + P) phi with the symmetric FP32 pair sum (variant ctx->sym_v); phi32
@@ -643,7 +650,7 @@ int stokes_sym_apply(lcp_ctx* ctx, double* out) {
                         N, ns, ns_pad, su, ctx->tmpl32, ctx->centers32, ctx->phi32, ctx->partial, ctx->sym_rev);
   prof_end(ctx, e0, 0);
   ++ctx->nlaunch, k_finish_sym<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(
-                      N, ns, slots, ctx->partial, ctx->sym_rev, ctx->sym_roff, ctx->coef, ctx->tmpl64, out);
+                      N, ns, slots, ctx->partial, ctx->sym_rev, ctx->sym_rbase, ctx->coef, ctx->tmpl64, out);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }

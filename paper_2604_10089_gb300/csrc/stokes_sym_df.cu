@@ -257,7 +257,7 @@ k_pair_df_sym(int N, int ns, int ns_pad, SymUnits su, const double* __restrict__
 // out_p = forward partials + the double-float reverse rows of the target
 // blocks before body(p) (in block order) + (P phi)_p; one thread per component.
 __global__ void k_finish_sym_df(int N, int ns, int splits, const double* __restrict__ partial,
-                                const float2* __restrict__ rev, const long long* __restrict__ roff,
+                                const float2* __restrict__ rev, const long long* __restrict__ rbase,
                                 const double* __restrict__ coef, const double* __restrict__ tmpl64,
                                 double* __restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -267,10 +267,9 @@ __global__ void k_finish_sym_df(int N, int ns, int splits, const double* __restr
   for (int s = 0; s < splits; s++) a += partial[(size_t)s * 3 * N + t];
   const int i = p / ns, q = p - i * ns;
   const int nbefore = (i * ns + SYM_TB - 1) / SYM_TB;
-  const long long within = 3LL * q + d;
-  for (int tb = 0; tb < nbefore; tb++) {
-    const int fb = (tb * SYM_TB) / ns;
-    const float2 r = rev[roff[tb] + (long long)(i - fb - 1) * 3 * ns + within];
+  const long long within = (long long)i * 3 * ns + 3LL * q + d;
+  for (int tb = 0; tb < nbefore; tb++) {   // rows at rbase[tb] + i * 3 ns (see k_finish_sym)
+    const float2 r = rev[rbase[tb] + within];
     a += (double)r.x + (double)r.y;
   }
   const double* c = coef + 6 * i;
@@ -337,7 +336,7 @@ int stokes_sym_df_apply(lcp_ctx* ctx, double* out) {
                       N, ns, sdf_ns_pad(ns), su, ctx->tmpl64, ctx->centers, ctx->phidf, ctx->partial, rev);
   prof_end(ctx, e0, 2);
   ++ctx->nlaunch, k_finish_sym_df<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(
-                      N, ns, slots, ctx->partial, rev, ctx->sym_roff, ctx->coef, ctx->tmpl64, out);
+                      N, ns, slots, ctx->partial, rev, ctx->sym_rbase, ctx->coef, ctx->tmpl64, out);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }
