@@ -340,3 +340,51 @@ def test_bb_step_is_the_inverse_rayleigh_quotient_on_a_quadratic():
     tau = (s @ s) / (s @ A @ s)
     x2, *_ = bb_pgd(lambda v: A @ v, b, x0, tau0=0.1, tol=0.0, kmax=2)
     np.testing.assert_allclose(x2, x1 - tau * (A @ x1 + b), rtol=1e-12)
+
+
+def test_contact_matrix_gives_the_rate_of_change_of_the_gaps():
+    """(D^T U)_l is the time derivative of gap l when the bodies move with U (Sec. 3:
+    D^T = grad Phi G): checked by finite differences of the gaps under random body
+    velocities (a swapped normal or body index flips the sign)."""
+    inst = make_instance("spheres8_grid7x14", 1)
+    a = inst.contact_radius
+    pairs, normals, gaps = detect_contacts(inst.centers, a, inst.delta)
+    D = contact_matrix(inst.n_bodies, pairs, normals)
+    U = np.random.default_rng(5).standard_normal((inst.n_bodies, 6))
+    eps = 1e-6
+    moved = inst.centers + eps * U[:, :3]
+    gaps_eps = np.array([np.linalg.norm(moved[j] - moved[i]) - 2 * a for i, j in pairs])
+    np.testing.assert_allclose((gaps_eps - gaps) / eps, D.T @ U.reshape(-1), atol=1e-5)
+
+
+def test_contact_forces_conserve_momentum_and_angular_momentum():
+    """A unit contact force is a pair of equal and opposite forces along the line of
+    centres: the total force and the total torque about the origin vanish."""
+    inst = make_instance("spheres8_grid7x14", 2)
+    pairs, normals, _ = detect_contacts(inst.centers, inst.contact_radius, inst.delta)
+    D = contact_matrix(inst.n_bodies, pairs, normals)
+    FT = (D @ np.random.default_rng(6).uniform(0, 1, len(pairs))).reshape(-1, 6)
+    np.testing.assert_allclose(FT[:, :3].sum(0), 0.0, atol=1e-12)
+    np.testing.assert_allclose(np.cross(inst.centers, FT[:, :3]).sum(0), 0.0, atol=1e-11)
+    np.testing.assert_array_equal(FT[:, 3:], 0.0)
+
+
+def test_collisional_set_threshold():
+    """Eq. (collisional-set): a pair enters when its gap is at most delta."""
+    a, delta = 1.25, 0.05
+    c = np.array([[0.0, 0.0, 0.0], [2 * a + 0.03, 0.0, 0.0], [0.0, 2 * a + delta + 1e-9, 0.0],
+                  [0.0, 0.0, 2 * a + delta]])
+    pairs, normals, gaps = detect_contacts(c, a, delta)
+    assert [tuple(p) for p in pairs] == [(0, 1), (0, 3)]
+    np.testing.assert_allclose(gaps, [0.03, delta], atol=1e-14)
+    np.testing.assert_allclose(normals, [[1.0, 0, 0], [0, 0, 1.0]], atol=1e-15)
+
+
+def test_rpy_mobility_is_symmetric_positive_definite():
+    """The RPY tensor of non-overlapping equal spheres is a symmetric positive definite
+    mobility (a property of the Rotne-Prager-Yamakawa construction for r >= 2a)."""
+    for k in range(3):
+        inst = make_instance("spheres64_grid9x18", k)
+        R = rpy_matrix(inst.centers, a=inst.radius)
+        np.testing.assert_allclose(R, R.T, atol=1e-15)
+        assert np.linalg.eigvalsh(R).min() > 0.0
