@@ -14,7 +14,9 @@ of the same workload on the host cores (cpu_baseline).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 run under torch.distributed.run: every rank solves its own
-configurations (weak scaling, no collective on the data path).
+configurations (weak scaling, no collective on the data path); the extra
+reports (plain-FP64 comparison, method comparison, trajectory, 64-sphere,
+batched and serving runs, CPU baseline) run at N = 1 only.
 """
 from __future__ import annotations
 
@@ -283,7 +285,7 @@ def run_ours(args, rank, world, local):
 
     # plain FP64 Mono-PQN on the first timed configuration, and agreement with it
     fp64 = None
-    if args.fp64_compare and rank == 0:
+    if args.fp64_compare and rank == 0 and world == 1:
         cfg64 = L.config_for(insts[0], L.LCP_FP64)
         ctx64 = L.lcp_setup(cfg64, insts[args.warmup].centers, insts[args.warmup].axes)
         t0 = time.perf_counter()
@@ -300,7 +302,7 @@ def run_ours(args, rank, world, local):
                 "kkt_fp64": st64["kkt_abs"], "kkt_ours": stm["kkt_abs"]}
     # the paper's comparison on this workload: high-fidelity MVPs and time per solve
     comparison = None
-    if args.compare_methods and rank == 0:
+    if args.compare_methods and rank == 0 and world == 1:
         comparison = {}
         inst = insts[args.warmup]
         runs = [("bb_pgd", L.LCP_BB_PGD, ctx), ("mono_pqn", L.LCP_MONO_PQN, ctx), ("bi_pqn", L.LCP_BI_PQN, ctx)]
@@ -317,7 +319,7 @@ def run_ours(args, rank, world, local):
                                 "converged": st["converged"] == 1}
         L.lcp_destroy(ctx_o)
     traj = None
-    if args.trajectory and rank == 0:
+    if args.trajectory and rank == 0 and world == 1:
         inst = insts[args.warmup]
 
         def trajectory(c, steps):
@@ -353,9 +355,9 @@ def run_ours(args, rank, world, local):
             traj["cold_start_first_steps"] = trajectory(ctx_cold, min(args.trajectory_cold, args.trajectory))
             L.lcp_destroy(ctx_cold)
     L.lcp_destroy(ctx)
-    c2 = c2_report(stream) if (args.c2 and rank == 0) else None
+    c2 = c2_report(stream) if (args.c2 and rank == 0 and world == 1) else None
     c4 = c5 = None
-    if args.c4c5 and rank == 0:
+    if args.c4c5 and rank == 0 and world == 1:
         # the batched and serving configurations at their sizes (256 instances; 32 simulations,
         # 3 steps each), two timed batches, without the minutes-long plain-FP64 baselines
         sub = argparse.Namespace(**vars(args))
@@ -790,7 +792,7 @@ def main():
         value = args.steps * world / r["t_total"]
         s = r["summary"]
         cpu = None
-        if args.cpu_baseline:
+        if args.cpu_baseline and world == 1:
             # complete oracle mobility solves of this workload (one fine slip solve, two
             # low-fidelity solves), combined with the MVP counts this run measured
             hi, lo = float(np.mean(s["hi_mvps"])), float(np.mean(s["lo_mvps"]))
