@@ -38,34 +38,45 @@ __device__ __forceinline__ D2 ddot3(const D2 (&a)[3], const D2 (&b)[3]) {
   return dadd_n(dadd_u(dmul_u(a[0], b[0]), dmul_u(a[1], b[1])), dmul_u(a[2], b[2]));
 }
 
-// Sum 8 double-float values over the warp (transposing: 3 halving levels,
-// then 2 butterflies); lane l ends with the total of value l / 4.
-__device__ __forceinline__ dfl warp_transpose_sum8_df(const dfl (&v)[8], int lane) {
-  dfl a[8];
+__device__ __forceinline__ D2 shfl_xor_d2(D2 v, int o) {
+  D2 r;
+  r.hi.x = __shfl_xor_sync(0xffffffffu, v.hi.x, o);
+  r.hi.y = __shfl_xor_sync(0xffffffffu, v.hi.y, o);
+  r.lo.x = __shfl_xor_sync(0xffffffffu, v.lo.x, o);
+  r.lo.y = __shfl_xor_sync(0xffffffffu, v.lo.y, o);
+  return r;
+}
+
+// Sum 8 double-float values over the warp; value k sits in pack k / 2, lane
+// (x, y) = k % 2.  Transposing: the first two halving levels add whole packs
+// (two independent double-float sums per FP32x2 instruction), the third splits
+// the last pack, two butterflies finish; sums stay unnormalised until the end
+// (lo grows by a few ulps of hi at most).  Lane l ends with value l / 4.
+__device__ __forceinline__ dfl warp_transpose_sum8_packed(D2 (&P)[4], int lane) {
+  {
+    const bool up = lane & 16;   // keep values 4..7 (packs 2, 3), send 0..3
 #pragma unroll
-  for (int i = 0; i < 8; i++) a[i] = v[i];
-#pragma unroll
-  for (int L = 0; L < 3; L++) {
-    const int n = 8 >> (L + 1), o = 16 >> L;
-    const bool hi = lane & o;
-#pragma unroll
-    for (int i = 0; i < n; i++) {
-      const dfl send = hi ? a[i] : a[i + n];
-      const dfl keep = hi ? a[i + n] : a[i];
-      dfl recv;
-      recv.hi = __shfl_xor_sync(0xffffffffu, send.hi, o);
-      recv.lo = __shfl_xor_sync(0xffffffffu, send.lo, o);
-      a[i] = df_add(keep, recv);
+    for (int i = 0; i < 2; i++) {
+      const D2 send = up ? P[i] : P[i + 2];
+      const D2 keep = up ? P[i + 2] : P[i];
+      P[i] = dadd_u(keep, shfl_xor_d2(send, 16));
     }
   }
-#pragma unroll
-  for (int o = 2; o >= 1; o >>= 1) {
-    dfl recv;
-    recv.hi = __shfl_xor_sync(0xffffffffu, a[0].hi, o);
-    recv.lo = __shfl_xor_sync(0xffffffffu, a[0].lo, o);
-    a[0] = df_add(a[0], recv);
+  {
+    const bool up = lane & 8;    // keep the second of the two remaining packs
+    const D2 send = up ? P[0] : P[1];
+    const D2 keep = up ? P[1] : P[0];
+    P[0] = dadd_u(keep, shfl_xor_d2(send, 8));
   }
-  return a[0];
+  const bool up = lane & 4;      // keep the odd value of the pack, send the even one
+  const float sh = up ? P[0].hi.x : P[0].hi.y, sl = up ? P[0].lo.x : P[0].lo.y;
+  const float kh = up ? P[0].hi.y : P[0].hi.x, kl = up ? P[0].lo.y : P[0].lo.x;
+  D2 t = dadd_u({f2(kh), f2(kl)}, {f2(__shfl_xor_sync(0xffffffffu, sh, 4)), f2(__shfl_xor_sync(0xffffffffu, sl, 4))});
+#pragma unroll
+  for (int o = 2; o >= 1; o >>= 1)
+    t = dadd_u(t, {f2(__shfl_xor_sync(0xffffffffu, t.hi.x, o)), f2(__shfl_xor_sync(0xffffffffu, t.lo.x, o))});
+  t = fast2sum2(t.hi, t.lo);
+  return {t.hi.x, t.lo.x};
 }
 
 }  // namespace
@@ -166,7 +177,7 @@ k_pair_df_sym(int N, int ns, int ns_pad, SymUnits su, const double* __restrict__
         float2* rout = s_rev + (size_t)warp * 3 * ns_pad;
 #pragma unroll 1
         for (int q = 0; q < ns_pad; q += 2) {
-          dfl v[8];
+          D2 RV[2][3];   // reverse terms of the two sources; lanes: the thread's two targets
 #pragma unroll
           for (int h = 0; h < 2; h++) {
             const int qq = q + h;
@@ -208,16 +219,21 @@ k_pair_df_sym(int N, int ns, int ns_pad, SymUnits su, const double* __restrict__
 #pragma unroll
             for (int d = 0; d < 3; d++) {
               ACC[d] = dadd_n(ACC[d], dmul_u(sf, R[d]));
-              const D2 rv = dmul_u(sr, R[d]);
-              v[3 * h + d] = df_add(dfl{rv.hi.x, rv.lo.x}, dfl{rv.hi.y, rv.lo.y});   // the thread's two targets
+              RV[h][d] = dmul_u(sr, R[d]);
             }
           }
           if (any_rev) {
-            v[6] = dfl{0.f, 0.f};
-            v[7] = dfl{0.f, 0.f};
-            const dfl tot = warp_transpose_sum8_df(v, lane);
+            // fold the thread's two targets, both sources at once: pack d = component d of
+            // (source q, source q + 1), i.e. value k = 2 d + h
+            D2 P[4];
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+              P[d] = dadd_u({make_float2(RV[0][d].hi.x, RV[1][d].hi.x), make_float2(RV[0][d].lo.x, RV[1][d].lo.x)},
+                            {make_float2(RV[0][d].hi.y, RV[1][d].hi.y), make_float2(RV[0][d].lo.y, RV[1][d].lo.y)});
+            P[3] = {f2(0.f), f2(0.f)};
+            const dfl tot = warp_transpose_sum8_packed(P, lane);
             const int k = lane >> 2;
-            if (!(lane & 3) && k < 6) rout[(k % 3) * ns_pad + q + k / 3] = make_float2(tot.hi, tot.lo);
+            if (!(lane & 3) && k < 6) rout[(k >> 1) * ns_pad + q + (k & 1)] = make_float2(tot.hi, tot.lo);
           }
         }
 #pragma unroll
