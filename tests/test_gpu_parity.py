@@ -305,3 +305,52 @@ def test_bb_pgd_baseline_matches_oracle(index):
         assert ok and abs(st["hi_mvps"] - mvps) <= 1
     finally:
         L.lcp_destroy(ctx)
+
+
+@pytest.mark.parametrize("method", [L.LCP_MONO_PQN, L.LCP_BI_PQN, L.LCP_BB_PGD])
+def test_duplicated_contact_degenerate_lcp(method):
+    """A contact listed twice gives A two equal columns (semidefinite, not definite): the
+    split of the force between the two copies is not unique, their sum is.  The solvers
+    must still converge, the KKT error with the oracle's A stays within tol + eps_op, and
+    the pair's total force equals the single-contact solution's."""
+    case = dense_case("spheres8_grid7x14", 1)
+    inst, A, b, xs = case["inst"], case["A"], case["b"], case["x"]
+    l0 = int(np.argmax(xs))                       # an active contact
+    order = list(range(xs.size)) + [l0]
+    contacts = [(case["pairs"][l][0], case["pairs"][l][1], case["normals"][l], case["gaps"][l]) for l in order]
+    ctx = L.lcp_setup(L.config_for(inst), inst.centers, inst.axes, contacts=contacts)
+    try:
+        x, st, status = L.lcp_solve(ctx, method, inst.tol)
+        assert status == L.LCP_OK and st["converged"] == 1
+        g_gpu = L.lcp_apply_A(ctx, x, L.LCP_HIGH) + L.lcp_get_b(ctx)
+    finally:
+        L.lcp_destroy(ctx)
+    idx = np.array(order)
+    A2, b2 = A[np.ix_(idx, idx)], b[idx]
+    g = A2 @ x + b2
+    eps_op, mismatch = kkt_bound(inst.tol, x, g, g_gpu, b2, st["hi_mvps"])
+    assert mismatch <= MISMATCH_REL * max(1.0, np.linalg.norm(b2)), mismatch
+    assert kkt_abs(x, g) <= inst.tol + eps_op
+    merged = x[:xs.size].copy()
+    merged[l0] += x[-1]
+    assert np.abs(merged - xs).max() <= 1e-5 * max(1.0, np.abs(xs).max())
+    assert x.min() >= 0.0
+
+
+def test_update_grows_the_contact_buffers():
+    """A context set up with two caller contacts, then updated to the full collisional set
+    (more contacts than its first allocation): the solve still matches the oracle."""
+    case = dense_case("spheres8_grid7x14", 3)
+    inst = case["inst"]
+    few = [(case["pairs"][l][0], case["pairs"][l][1], case["normals"][l], case["gaps"][l]) for l in range(2)]
+    ctx = L.lcp_setup(L.config_for(inst), inst.centers, inst.axes, contacts=few)
+    try:
+        assert L.lcp_sizes(ctx)[2] == 2
+        L.lcp_solve(ctx, L.LCP_MONO_PQN, inst.tol)
+        L.lcp_update(ctx, inst.centers, inst.axes)          # detect: the full set
+        assert L.lcp_sizes(ctx)[2] == case["b"].size > 2
+        assert rel(L.lcp_get_b(ctx), case["b"]) <= 1e-9
+        x, st, _ = L.lcp_solve(ctx, L.LCP_BI_PQN, inst.tol)
+        check_solution(case, x, inst.tol, ctx, st["hi_mvps"])
+    finally:
+        L.lcp_destroy(ctx)
