@@ -75,6 +75,8 @@ def parse():
                         "or auto = (n_theta - 3) x 2(n_theta - 3) of the workload's grid")
     p.add_argument("--lowfi-min-bodies", type=int, default=10 ** 9,
                    help="batched/serving modes: use --lowfi only for instances with at least this many spheres")
+    p.add_argument("--recycle", type=int, default=0,
+                   help="solve pairs kept for projected starts of the mobility solves (0 = off)")
     p.add_argument("--fp64-compare", type=int, default=1)
     p.add_argument("--cpu-baseline", type=int, default=1)
     p.add_argument("--compare-methods", type=int, default=1,
@@ -218,7 +220,7 @@ def run_ours(args, rank, world, local):
     prec = L.LCP_MIXED if args.precision == "mixed" else L.LCP_FP64
     method = L.LCP_BI_PQN if args.method == "bi" else L.LCP_MONO_PQN
     lowfi = lowfi_overrides(args.lowfi, insts[0].n_theta)
-    cfg = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream, **lowfi)
+    cfg = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream, recycle=args.recycle, **lowfi)
     tol = insts[0].tol
     with torch.cuda.stream(stream):
         cen = [torch.tensor(i.centers, dtype=torch.float64, device=dev) for i in insts]
@@ -286,7 +288,7 @@ def run_ours(args, rank, world, local):
     # plain FP64 Mono-PQN on the first timed configuration, and agreement with it
     fp64 = None
     if args.fp64_compare and rank == 0 and world == 1:
-        cfg64 = L.config_for(insts[0], L.LCP_FP64)
+        cfg64 = L.config_for(insts[0], L.LCP_FP64, recycle=0)   # the paper's method as printed
         ctx64 = L.lcp_setup(cfg64, insts[args.warmup].centers, insts[args.warmup].axes)
         t0 = time.perf_counter()
         x64, st64, _ = L.lcp_solve(ctx64, L.LCP_MONO_PQN, tol)
@@ -401,6 +403,8 @@ def run_ours(args, rank, world, local):
         "hi_mvps": [s["hi_mvps"] for s in stats], "lo_mvps": [s["lo_mvps"] for s in stats],
         "e_mvps": [round(s["e_mvps"], 3) for s in stats], "iterations": [s["iterations"] for s in stats],
         "gmres_iterations": [s["gmres_iterations"] for s in stats],
+        "lo_gmres_iterations": [s["lo_gmres_iterations"] for s in stats],
+        "recycled_solves": [s["recycled_solves"] for s in stats],
         "fp32_applies": [s["fp32_applies"] for s in stats], "fp64_applies": [s["fp64_applies"] for s in stats],
         "df64_applies": [s["df64_applies"] for s in stats],
         "kkt_abs": [s["kkt_abs"] for s in stats], "contacts": ncon,
@@ -494,7 +498,7 @@ def run_batched(args):
     t64_all = 0.0
     if args.fp64_baseline:
         for i in insts:
-            c64 = L.lcp_setup(L.config_for(i, L.LCP_FP64), i.centers, i.axes)
+            c64 = L.lcp_setup(L.config_for(i, L.LCP_FP64, recycle=0), i.centers, i.axes)
             ts = time.perf_counter()
             L.lcp_solve(c64, L.LCP_MONO_PQN, 1e-8, allow_not_converged=True)
             t64_all += time.perf_counter() - ts
@@ -582,7 +586,7 @@ def run_serving(args):
         t_seq += time.perf_counter() - ts
         L.lcp_destroy(c)
         if args.fp64_baseline:
-            c = L.lcp_setup(L.config_for(i, L.LCP_FP64), i.centers, i.axes)
+            c = L.lcp_setup(L.config_for(i, L.LCP_FP64, recycle=0), i.centers, i.axes)
             ts = time.perf_counter()
             L.lcp_solve(c, L.LCP_MONO_PQN, 1e-8, allow_not_converged=True)
             t64 += time.perf_counter() - ts
@@ -702,7 +706,7 @@ def config_dict(args, M: int, N: int, lowfi_desc: str, world: int) -> dict:
             "low_fidelity": lowfi_desc,
             "gmres_tol": 1e-12, "step": "contacts + U_nc slip solve + b + LCP solve",
             "l2": "inputs larger than L2 (Krylov basis 76 MB + operator sweeps per apply)",
-            "parallelism": f"instances x{world}"}
+            "recycle": args.recycle, "parallelism": f"instances x{world}"}
 
 
 def lowfi_description(lowfi: dict) -> str:

@@ -101,6 +101,20 @@ typedef struct {
    * iterations reach the same tolerance.  The paper names reuse across solves as
    * future work ("Conclusions and Future Work"); 0 = always start from zero. */
   int warm_start;
+  /* Reuse across the mobility solves of one configuration (the MVPs of one LCP
+   * share K + P and their right-hand sides differ little): the context keeps
+   * up to `recycle` pairs (psi_k, w_k = (K + P) psi_k, w orthonormal) from its
+   * earlier solves and starts each solve from the Galerkin projection
+   * phi0 = Psi W^T rhs when that predicts at least a tenfold smaller residual
+   * (Fischer's projection method for successive right-hand sides); when all
+   * pairs are in use the set restarts from the newest solve.  Cleared when the
+   * configuration changes and at the start of every LCP solve, so a solve's
+   * result depends only on its configuration.  It pays where successive
+   * right-hand sides are close (repeated or combined forces in mobility_apply);
+   * the MVPs of a PQN solve multiply new search directions, which the kept
+   * pairs do not predict.  The paper names reuse across solves as future work.
+   * 0 = off (default); at most gmres_restart. */
+  int recycle;
 } lcp_config;
 
 typedef struct {
@@ -130,6 +144,8 @@ typedef struct {
   double h0_delta;          /* scale delta of B_0 = delta I (1 when unscaled) */
   int unc_gmres_iterations; /* GMRES iterations of the slip solve that produced this LCP's b */
   int unc_warm_started;     /* 1 if that slip solve started from the previous step's density */
+  int lo_gmres_iterations;  /* GMRES iterations of the coarse-grid low-fidelity solves, summed */
+  int recycled_solves;      /* mobility solves (both grids) started from the projection (cfg.recycle) */
 } lcp_stats;
 
 typedef struct lcp_ctx lcp_ctx;   /* opaque, library-owned */
@@ -258,6 +274,15 @@ LCP_API int lcp_profile_read(lcp_ctx* ctx, int kind, int* count, double* total_m
 
 /* Number of kernels this context has launched since lcp_setup. */
 LCP_API int lcp_launch_count(const lcp_ctx* ctx, unsigned long long* count);
+
+/* Mobility solves of one grid since lcp_setup (fidelity LCP_HIGH, or
+ * LCP_LOW_BIE for the coarse low-fidelity grid): *solves solves (slip solves,
+ * MVPs and direct mobility calls), *gmres_iterations their GMRES iterations,
+ * *recycled those started from the projection on earlier solves
+ * (cfg.recycle).  Host counters; no device work.  LCP_ERR_INVALID_ARG for
+ * another fidelity or a missing coarse grid. */
+LCP_API int lcp_solve_counters(const lcp_ctx* ctx, int fidelity, long long* solves, long long* gmres_iterations,
+                               long long* recycled);
 
 /* Frees every device buffer of the context.  NULL is ignored. */
 LCP_API void lcp_destroy(lcp_ctx* ctx);

@@ -36,7 +36,8 @@ class lcp_config(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("own_stream", ctypes.c_int), ("h0_scaling", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("lowfi_n_theta", ctypes.c_int),
                 ("lowfi_n_phi", ctypes.c_int), ("lowfi_tol", ctypes.c_double),
-                ("init_forcing", ctypes.c_double), ("warm_start", ctypes.c_int)]
+                ("init_forcing", ctypes.c_double), ("warm_start", ctypes.c_int),
+                ("recycle", ctypes.c_int)]
 
 
 class lcp_contact(ctypes.Structure):
@@ -53,7 +54,8 @@ class lcp_stats(ctypes.Structure):
                 ("hi_mvp_seconds", ctypes.c_double), ("lo_mvp_seconds", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("df64_applies", ctypes.c_int), ("resets", ctypes.c_int),
                 ("ssn_iterations", ctypes.c_int), ("ssn_fallbacks", ctypes.c_int), ("h0_delta", ctypes.c_double),
-                ("unc_gmres_iterations", ctypes.c_int), ("unc_warm_started", ctypes.c_int)]
+                ("unc_gmres_iterations", ctypes.c_int), ("unc_warm_started", ctypes.c_int),
+                ("lo_gmres_iterations", ctypes.c_int), ("recycled_solves", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -73,6 +75,8 @@ PROTOTYPES = {
     "lcp_step": (_I, [_P, ctypes.c_double, _D, _D]),
     "lcp_profile": (_I, [_P, _I]),
     "lcp_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "lcp_solve_counters": (_I, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "lcp_profile_read": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "lcp_last_error": (ctypes.c_char_p, [_P]),
     "lcp_sizes": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),

@@ -183,8 +183,19 @@ struct lcp_ctx {
   // bodies and stream, no contacts; its mobility solves run FP32 GMRES only
   lcp_ctx* lo = nullptr;
   bool fp32_only = false;
+  // reuse across the mobility solves of one configuration: up to rc_max pairs
+  // (psi_k, w_k), w_k ~= (K + P) psi_k, the w_k orthonormal, in slots [0, rc_count)
+  double* rc_psi = nullptr;   // [rc_max][3N]
+  double* rc_w = nullptr;     // [rc_max][3N]
+  double* rc_h = nullptr;     // [3 rc_max] projection / Gram-Schmidt coefficients
+  double* rc_phi0 = nullptr;  // [3N] start of the current solve, then its direction
+  double* rc_r0 = nullptr;    // [3N] start residual of the current solve, then its image
+  int rc_max = 0, rc_count = 0;
   // counters of the current solve
   int c_gmres = 0, c_fp64 = 0, c_fp32 = 0, c_df64 = 0;
+  int c_recycled = 0;         // solves started from the projection
+  // since set-up (never reset): mobility solves, their GMRES iterations, projected starts
+  long long tot_solves = 0, tot_gmres = 0, tot_recycled = 0;
 };
 
 #define LCP_CUDA(call)                                                            \
@@ -230,6 +241,7 @@ int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision);
 int stokes_rhs(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs);
 int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef);
 int mobility_solve(lcp_ctx* ctx, const double* FT, int include_slip, double* UO, const double* phi0 = nullptr);
+void recycle_reset(lcp_ctx* ctx);   // forget the kept solve pairs (this context and its coarse grid)
 int precond_build(lcp_ctx* ctx);
 int precond_apply(lcp_ctx* ctx, const double* v, double* z);
 int scatter_D(lcp_ctx* ctx, const double* x, double* FT);

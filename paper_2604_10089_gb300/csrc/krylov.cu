@@ -77,6 +77,11 @@ __global__ void k_add(int L, const double* __restrict__ a, double* __restrict__ 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < L) c[i] += a[i];
 }
+// y = s x
+__global__ void k_scale_into(int L, double s, const double* __restrict__ x, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L) y[i] = s * x[i];
+}
 
 // GMRES bookkeeping on the device (one thread).  Work layout (doubles):
 // H[(m+1) * m] column j at H + j * (m+1); cs[m]; sn[m]; g[m+1]; y[m];
@@ -407,64 +412,182 @@ static int norm2(lcp_ctx* ctx, const double* v, int L, double* out) {
   return LCP_OK;
 }
 
+// --------------------------------------------------- reuse across solves
+// The mobility solves of one configuration share the operator K + P, and the
+// right-hand sides of the successive MVPs of one LCP differ little.  The
+// context keeps up to rc_max pairs (psi_k, w_k) from its earlier solves, with
+// w_k ~= (K + P) psi_k and the w_k orthonormal.  A solve may start from the
+// Galerkin projection phi0 = Psi c, c = W^T rhs, whose residual is predicted
+// as rhs - W c (Fischer's projection method for successive right-hand
+// sides).  After each solve its pair enters: the direction the solve moved
+// (phi - phi_start) and its image (start residual - final residual),
+// orthogonalised against the kept w_k by classical Gram-Schmidt applied twice
+// (the same coefficients applied to the psi_k) and normalised.  Once every
+// slot is in use the set restarts from the newest solve alone: its whole
+// solution and right-hand side (less the final residual) as the one pair.
+// The w_k only choose the start: each solve's accepted residual is computed
+// from its own iterate, so an inexact image costs iterations, not accuracy.
+
+// A projected start is taken when it predicts a residual below
+// RC_USE ||rhs||: at least one decade, worth more than the one operator
+// application that the FP64 and FP32-only solves spend on its exact residual.
+static constexpr double RC_USE = 0.1;
+
+// c = a - c
+__global__ void k_from_sub(int L, const double* __restrict__ a, double* __restrict__ c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L) c[i] = a[i] - c[i];
+}
+// c = c - b
+__global__ void k_sub_from(int L, const double* __restrict__ b, double* __restrict__ c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L) c[i] -= b[i];
+}
+
+void recycle_reset(lcp_ctx* ctx) {
+  ctx->rc_count = 0;
+  if (ctx->lo) recycle_reset(ctx->lo);
+}
+
+// c = W^T rhs (into rc_h), phi = Psi c, r = rhs - W c; *rn = ||r||.
+static int recycle_project(lcp_ctx* ctx, const double* rhs, double* phi, double* r, double* rn) {
+  const int L = 3 * ctx->N, m = ctx->rc_count, T = 256;
+  const size_t ld = (size_t)L;
+  double* c = ctx->rc_h;
+  LCP_TRY(dots(ctx, L, m, ctx->rc_w, ld, rhs, c));
+  LCP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * L, ctx->stream));
+  ++ctx->nlaunch, k_gmres_update<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, m, ctx->rc_psi, ld, c, phi);
+  LCP_CUDA(cudaGetLastError());
+  LCP_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+  LCP_TRY(update_dots(ctx, L, m, ctx->rc_w, ld, c, r, 1, r, ld, ctx->dscal + 8));   // r -= W c; ||r||^2
+  LCP_CUDA(cudaMemcpyAsync(ctx->hscal + 8, ctx->dscal + 8, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+  *rn = std::sqrt(ctx->hscal[8]);
+  return LCP_OK;
+}
+
+// Enters the pair (rc_phi0, rc_r0) = (direction, image) of the solve just
+// finished into the free slot rc_count (< rc_max); skipped when its
+// orthogonalised image is not above wmin (no new direction).
+static int recycle_add(lcp_ctx* ctx, double wmin) {
+  const int L = 3 * ctx->N, m = ctx->rc_count, T = 256;
+  const size_t ld = (size_t)L;
+  double* p = ctx->rc_phi0;
+  double* w = ctx->rc_r0;
+  double* h1 = ctx->rc_h + ctx->rc_max;
+  double* h2 = ctx->rc_h + 2 * ctx->rc_max;
+  if (m > 0) {
+    LCP_TRY(dots(ctx, L, m, ctx->rc_w, ld, w, h1));
+    LCP_TRY(update_dots(ctx, L, m, ctx->rc_w, ld, h1, w, m, ctx->rc_w, ld, h2));
+    LCP_TRY(update_dots(ctx, L, m, ctx->rc_w, ld, h2, w, 0, nullptr, 0, nullptr));
+    LCP_TRY(update_dots(ctx, L, m, ctx->rc_psi, ld, h1, p, 0, nullptr, 0, nullptr));
+    LCP_TRY(update_dots(ctx, L, m, ctx->rc_psi, ld, h2, p, 0, nullptr, 0, nullptr));
+  }
+  double wn = 0.0;
+  LCP_TRY(norm2(ctx, w, L, &wn));
+  if (!(wn > wmin) || !std::isfinite(wn)) return LCP_OK;
+  ++ctx->nlaunch, k_scale_into<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, 1.0 / wn, w, ctx->rc_w + m * ld);
+  ++ctx->nlaunch, k_scale_into<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, 1.0 / wn, p, ctx->rc_psi + m * ld);
+  LCP_CUDA(cudaGetLastError());
+  ctx->rc_count++;
+  return LCP_OK;
+}
+
 // Solve (K + P) phi = rhs to ||rhs - (K + P) phi|| <= gmres_tol ||rhs||.
 // FP64: GMRES on the FP64 operator.  MIXED: iterative refinement.  Each sweep
 // solves for a correction d with GMRES on the FP32 operator (FP64 Arnoldi) to
 // inner_tol relative.  The residual after the first sweep is recomputed with
-// the high-accuracy operator (FP64 or double-FP32 sums, residual_precision); later residuals are updated, r <- r - (K + P)_32 d, which
-// is accurate to ~eps32 ||K|| ||d|| because those corrections are small (the
-// FP32 operator's relative error eps32 is ~4e-7).  A correction larger than
-// IR_UPDATE_MAX ||phi|| falls back to an FP64 residual.
+// the high-accuracy operator (FP64 or double-FP32 sums, residual_precision);
+// later residuals are updated, r <- r - (K + P)_32 d, which is accurate to
+// ~eps32 ||K|| ||d|| because those corrections are small (the FP32
+// operator's relative error eps32 is ~4e-7).  A correction larger than
+// IR_UPDATE_MAX ||phi|| falls back to a high-accuracy residual.  The
+// low-fidelity grid (fp32_only) runs GMRES on the FP32 operator alone.
 static constexpr double IR_UPDATE_MAX = 1e-5;
 
-// phi0 (or NULL): initial guess.  With a guess the first residual is taken
-// with the high-accuracy operator, so the guess only has to be close, not exact.
+// phi0 (or NULL): initial guess (the previous slip density along a
+// trajectory); its residual is taken with the solve's accurate operator, so
+// the guess only has to be close, not exact.  Without phi0 the start is the
+// projection on the kept pairs when it predicts a residual below
+// RC_USE ||rhs||, else zero.
 int density_solve(lcp_ctx* ctx, const double* rhs, double* phi, const double* phi0) {
   const int L = 3 * ctx->N;
   const int T = 256;
   double bn = 0.0;
   LCP_TRY(norm2(ctx, rhs, L, &bn));
-  if (phi0)
-    LCP_CUDA(cudaMemcpyAsync(phi, phi0, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
-  else
-    LCP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * L, ctx->stream));
   if (bn == 0.0) {
-    if (phi0) LCP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * L, ctx->stream));
+    LCP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * L, ctx->stream));
     return LCP_OK;
   }
   const double tol = ctx->cfg.gmres_tol * bn;
-  const int zero_init = phi0 ? 0 : 1;
-  int its = 0;
-  double res = 0.0;
-  if (ctx->cfg.precision == LCP_FP64) {
-    LCP_TRY(gmres(ctx, rhs, phi, zero_init, tol, LCP_FP64, ctx->cfg.gmres_maxit, &its, &res));
-    ctx->c_gmres += its;
-    if (res > tol) {
-      ctx->err = "GMRES did not reach its tolerance";
-      return LCP_ERR_NOT_CONVERGED;
-    }
-    return LCP_OK;
-  }
-  if (ctx->fp32_only) {   // low-fidelity grid: FP32-operator GMRES to the tolerance, no refinement
-    LCP_TRY(gmres(ctx, rhs, phi, zero_init, tol, LCP_MIXED, ctx->cfg.gmres_maxit, &its, &res));
-    ctx->c_gmres += its;
-    if (res > tol) {
-      ctx->err = "GMRES did not reach its tolerance";
-      return LCP_ERR_NOT_CONVERGED;
-    }
-    return LCP_OK;
-  }
-  // mixed precision: phi = 0, r = rhs; or phi = phi0, r = rhs - (K + P) phi0
-  // with the high-accuracy operator
+  const bool keep = ctx->rc_max > 0;
+  const bool refine = ctx->cfg.precision != LCP_FP64 && !ctx->fp32_only;
+  // start: 0 zero, 1 phi0, 2 projection (predicted residual in ctx->res, norm rn)
+  int start = 0;
   double rn = bn;
   if (phi0) {
+    LCP_CUDA(cudaMemcpyAsync(phi, phi0, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+    start = 1;
+  } else if (keep && ctx->rc_count > 0) {
+    double rp = 0.0;
+    LCP_TRY(recycle_project(ctx, rhs, phi, ctx->res, &rp));
+    if (rp <= RC_USE * bn) {
+      start = 2;
+      rn = rp;
+      ctx->c_recycled++;
+    }
+  }
+  if (start == 0) LCP_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * L, ctx->stream));
+  int its = 0;
+  double res = 0.0;
+  if (!refine) {
+    const int prec = ctx->cfg.precision == LCP_FP64 ? LCP_FP64 : LCP_MIXED;
+    double* r0 = keep ? ctx->rc_r0 : ctx->res;
+    double* d = keep ? ctx->rc_phi0 : ctx->dphi;
+    if (start == 0) {
+      LCP_TRY(gmres(ctx, rhs, phi, 1, tol, prec, ctx->cfg.gmres_maxit, &its, &res));
+      if (keep && its > 0) {
+        LCP_CUDA(cudaMemcpyAsync(d, phi, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+        LCP_CUDA(cudaMemcpyAsync(r0, rhs, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+    } else {
+      // exact start residual with the solve's operator, then the correction
+      LCP_TRY(stokes_apply(ctx, phi, ctx->wv, prec));
+      ++ctx->nlaunch, k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->wv, r0);
+      LCP_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * L, ctx->stream));
+      LCP_TRY(gmres(ctx, r0, d, 1, tol, prec, ctx->cfg.gmres_maxit, &its, &res));
+      ++ctx->nlaunch, k_add<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, d, phi);
+      LCP_CUDA(cudaGetLastError());
+    }
+    ctx->c_gmres += its;
+    if (res > tol) {
+      ctx->err = "GMRES did not reach its tolerance";
+      return LCP_ERR_NOT_CONVERGED;
+    }
+    // the image of the direction is r0 up to the final residual (<= tol)
+    if (keep && its > 0) {
+      if (ctx->rc_count == ctx->rc_max) {   // full: restart from this solve
+        ctx->rc_count = 0;
+        LCP_CUDA(cudaMemcpyAsync(d, phi, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+        LCP_CUDA(cudaMemcpyAsync(r0, rhs, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+      LCP_TRY(recycle_add(ctx, tol));
+    }
+    return LCP_OK;
+  }
+  // mixed precision: refinement from the start's residual
+  if (start == 1) {
     LCP_TRY(stokes_apply(ctx, phi, ctx->wv, ctx->cfg.residual_precision));
     ++ctx->nlaunch, k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->wv, ctx->res);
     LCP_TRY(norm2(ctx, ctx->res, L, &rn));
     if (!(rn == rn)) { ctx->err = "refinement: NaN residual"; return LCP_ERR_NUMERICAL; }
     if (rn <= tol) return LCP_OK;
-  } else {
+  } else if (start == 0) {
     LCP_CUDA(cudaMemcpyAsync(ctx->res, rhs, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  if (keep) {
+    LCP_CUDA(cudaMemcpyAsync(ctx->rc_phi0, phi, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+    LCP_CUDA(cudaMemcpyAsync(ctx->rc_r0, ctx->res, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
   }
   for (int sweep = 0; sweep < ctx->cfg.ir_maxit; sweep++) {
     LCP_CUDA(cudaMemsetAsync(ctx->dphi, 0, sizeof(double) * L, ctx->stream));
@@ -475,6 +598,8 @@ int density_solve(lcp_ctx* ctx, const double* rhs, double* phi, const double* ph
     double dn = 0.0, pn = 0.0;
     LCP_TRY(norm2(ctx, ctx->dphi, L, &dn));
     LCP_TRY(norm2(ctx, phi, L, &pn));
+    // the first sweep always ends with an accurate residual: after a
+    // projected start it replaces the predicted one
     if (sweep == 0 || dn > IR_UPDATE_MAX * pn) {
       LCP_TRY(stokes_apply(ctx, phi, ctx->wv, ctx->cfg.residual_precision));
       ++ctx->nlaunch, k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->wv, ctx->res);
@@ -484,7 +609,21 @@ int density_solve(lcp_ctx* ctx, const double* rhs, double* phi, const double* ph
     }
     LCP_TRY(norm2(ctx, ctx->res, L, &rn));
     if (!(rn == rn)) { ctx->err = "refinement: NaN residual"; return LCP_ERR_NUMERICAL; }
-    if (rn <= tol) return LCP_OK;
+    if (rn <= tol) {
+      if (keep) {
+        if (ctx->rc_count == ctx->rc_max) {   // full: restart from phi, image rhs - r_final
+          ctx->rc_count = 0;
+          LCP_CUDA(cudaMemcpyAsync(ctx->rc_phi0, phi, sizeof(double) * L, cudaMemcpyDeviceToDevice, ctx->stream));
+          ++ctx->nlaunch, k_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, rhs, ctx->res, ctx->rc_r0);
+        } else {   // direction phi - phi_start, image r_start - r_final
+          ++ctx->nlaunch, k_from_sub<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, phi, ctx->rc_phi0);
+          ++ctx->nlaunch, k_sub_from<<<blocks_for(L, T), T, 0, ctx->stream>>>(L, ctx->res, ctx->rc_r0);
+        }
+        LCP_CUDA(cudaGetLastError());
+        LCP_TRY(recycle_add(ctx, tol));
+      }
+      return LCP_OK;
+    }
   }
   ctx->err = "iterative refinement did not reach the GMRES tolerance";
   return LCP_ERR_NOT_CONVERGED;
@@ -492,7 +631,12 @@ int density_solve(lcp_ctx* ctx, const double* rhs, double* phi, const double* ph
 
 int mobility_solve(lcp_ctx* ctx, const double* FT, int include_slip, double* UO, const double* phi0) {
   LCP_TRY(stokes_rhs(ctx, FT, include_slip, ctx->rhs));
-  LCP_TRY(density_solve(ctx, ctx->rhs, ctx->phi, phi0));
+  const int g0 = ctx->c_gmres, r0 = ctx->c_recycled;
+  const int st = density_solve(ctx, ctx->rhs, ctx->phi, phi0);
+  ctx->tot_solves++;
+  ctx->tot_gmres += ctx->c_gmres - g0;
+  ctx->tot_recycled += ctx->c_recycled - r0;
+  LCP_TRY(st);
   return stokes_velocity(ctx, ctx->phi, UO);
 }
 

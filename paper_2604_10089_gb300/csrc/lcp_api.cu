@@ -62,6 +62,7 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->own_stream = 0;
   c->h0_scaling = 1;
   c->warm_start = 1;
+  c->recycle = 0;
   c->cuda_stream = nullptr;
 }
 
@@ -83,6 +84,7 @@ static int validate(const lcp_config* c, int M, const double* centers, std::stri
     *err = "low-fidelity grid: lowfi_n_theta >= 2, even lowfi_n_phi >= 4, at most 512 nodes, lowfi_tol in (0, 0.1]";
     return LCP_ERR_INVALID_ARG;
   }
+  if (c->recycle < 0 || c->recycle > c->gmres_restart) { *err = "recycle in [0, gmres_restart]"; return LCP_ERR_INVALID_ARG; }
   if (!(c->init_forcing >= 0.0) || c->init_forcing >= 1.0) { *err = "init_forcing in [0, 1)"; return LCP_ERR_INVALID_ARG; }
   // the direction kernel keeps its r x r systems in shared memory (<= 227 KB: r <= 48)
   if (c->memory < 1 || c->memory > 48) { *err = "memory in [1, 48]"; return LCP_ERR_INVALID_ARG; }
@@ -160,6 +162,15 @@ static int alloc_static(lcp_ctx* ctx) {
   ctx->UO = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->U_nc = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->phi_unc = (double*)ctx_alloc(ctx, sizeof(double) * L);
+  ctx->rc_max = ctx->cfg.recycle;
+  if (ctx->rc_max > 0) {
+    ctx->rc_psi = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)L * ctx->rc_max);
+    ctx->rc_w = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)L * ctx->rc_max);
+    ctx->rc_h = (double*)ctx_alloc(ctx, sizeof(double) * 3 * ctx->rc_max);
+    ctx->rc_phi0 = (double*)ctx_alloc(ctx, sizeof(double) * L);
+    ctx->rc_r0 = (double*)ctx_alloc(ctx, sizeof(double) * L);
+    if (!ctx->rc_psi || !ctx->rc_w || !ctx->rc_h || !ctx->rc_phi0 || !ctx->rc_r0) return LCP_ERR_OOM;
+  }
   ctx->MDx = (double*)ctx_alloc(ctx, sizeof(double) * 6 * M);
   ctx->cnext = (double*)ctx_alloc(ctx, sizeof(double) * 3 * M);
   ctx->anext = (double*)ctx_alloc(ctx, sizeof(double) * 3 * M);
@@ -227,6 +238,7 @@ static int configure(lcp_ctx* ctx, const double* centers, const double* axes, in
                      const lcp_contact* contacts, bool device_inputs, bool warm = false) {
   const int M = ctx->M;
   const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  recycle_reset(ctx);   // K + P changes with the configuration
   LCP_CUDA(cudaMemcpyAsync(ctx->centers, centers, sizeof(double) * 3 * M, kind, ctx->stream));
   ctx->has_axes = axes != nullptr;
   if (axes) LCP_CUDA(cudaMemcpyAsync(ctx->axes, axes, sizeof(double) * 3 * M, kind, ctx->stream));
@@ -369,6 +381,8 @@ extern "C" int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n
   size_t b = 0;
   b += sizeof(double) * L * (m + 1) + (cfg->precondition ? sizeof(double) * L * m : 0);   // Krylov bases
   b += sizeof(double) * L * 6 + sizeof(float) * L * 3;                                      // node vectors
+  if (cfg->recycle > 0)                                                                      // reuse pairs
+    b += sizeof(double) * (L * (2 * (size_t)cfg->recycle + 2) + 3 * (size_t)cfg->recycle);
   const size_t ntb = (N + 511) / 512, units = ntb * M / 2 + 1;                               // symmetric pair sum
   const size_t slots = std::min(units, 2 + M / std::max<size_t>(1, units / 304));
   b += sizeof(double) * L * std::max<size_t>(6, slots) + stokes_sym_bytes(n_bodies, (int)ns); // partial slots
@@ -409,6 +423,22 @@ extern "C" int lcp_select_kernel_variant(lcp_ctx* ctx, const char* name) {
 extern "C" int lcp_launch_count(const lcp_ctx* ctx, unsigned long long* count) {
   if (!ctx || !count) return LCP_ERR_INVALID_ARG;
   *count = ctx->nlaunch;
+  return LCP_OK;
+}
+
+extern "C" int lcp_solve_counters(const lcp_ctx* ctx, int fidelity, long long* solves, long long* gmres_iterations,
+                                   long long* recycled) {
+  if (!ctx || !solves || !gmres_iterations || !recycled) return LCP_ERR_INVALID_ARG;
+  const lcp_ctx* c = ctx;
+  if (fidelity == LCP_LOW_BIE) {
+    if (!ctx->lo) return LCP_ERR_INVALID_ARG;
+    c = ctx->lo;
+  } else if (fidelity != LCP_HIGH) {
+    return LCP_ERR_INVALID_ARG;
+  }
+  *solves = c->tot_solves;
+  *gmres_iterations = c->tot_gmres;
+  *recycled = c->tot_recycled;
   return LCP_OK;
 }
 

@@ -1163,6 +1163,9 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
   const int n = ctx->n;
   const double t_start = now_s();
   ctx->c_gmres = ctx->c_fp32 = ctx->c_fp64 = ctx->c_df64 = 0;
+  ctx->c_recycled = 0;
+  if (ctx->lo) ctx->lo->c_gmres = ctx->lo->c_recycled = 0;
+  recycle_reset(ctx);   // each LCP solve depends only on its configuration
   lcp_stats s{};
   s.unc_gmres_iterations = ctx->unc_its;
   s.unc_warm_started = ctx->unc_warm;
@@ -1325,6 +1328,8 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
                                       : (a[S_DSET] != 0.0 ? a[S_DELTA] : 1.0);
   }
   s.gmres_iterations = ctx->c_gmres;
+  s.lo_gmres_iterations = ctx->lo ? ctx->lo->c_gmres : 0;
+  s.recycled_solves = ctx->c_recycled + (ctx->lo ? ctx->lo->c_recycled : 0);
   s.fp32_applies = ctx->c_fp32;
   s.fp64_applies = ctx->c_fp64;
   s.df64_applies = ctx->c_df64;

@@ -121,6 +121,13 @@ def lcp_launch_count(ctx) -> int:
     return c.value
 
 
+def lcp_solve_counters(ctx, fidelity: int = 0):
+    """(mobility solves, their GMRES iterations, projected starts) of one grid since set-up."""
+    a, b, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(_lib().lcp_solve_counters(ctx, fidelity, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), ctx)
+    return a.value, b.value, c.value
+
+
 def lcp_profile_read(ctx, kind: int):
     """(launch count, total milliseconds) of kind 0 = FP32 pair sum, 1 = FP64 pair sum."""
     c, t = ctypes.c_int(), ctypes.c_double()

@@ -1,6 +1,7 @@
 """The C ABI: every function declared in include/*.h is exported by the library
 (and nothing else of the library's internals leaks); the library loads and its
 defaults are readable without a GPU."""
+import ctypes
 import glob
 import os
 import re
@@ -51,3 +52,29 @@ def test_library_loads_and_binding_matches(built):
     cfg = L.lcp_default_config()
     assert cfg.n_theta == 9 and cfg.n_phi == 18 and cfg.gmres_tol == 1e-12
     assert cfg.residual_precision == L.LCP_DF64 and cfg.precondition == 1
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs: same fields, offsets and sizes
+    as the C compiler lays them out (a C program built against include/*.h)."""
+    from paper_2604_10089_gb300 import _abi
+    structs = [("lcp_config", _abi.lcp_config), ("lcp_stats", _abi.lcp_stats), ("lcp_contact", _abi.lcp_contact)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lcp_gb300.h"', "int main(void) {"]
+    for cname, py in structs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    c_layout = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, field, value = line.split()
+        c_layout[(name, field)] = int(value)
+    for cname, py in structs:
+        assert c_layout[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert c_layout[(cname, field)] == getattr(py, field).offset, (cname, field)
+    # equal sizes and offsets: no header field is missing from the mirror, at the end or between
