@@ -75,6 +75,8 @@ def parse():
                         "or auto = (n_theta - 3) x 2(n_theta - 3) of the workload's grid")
     p.add_argument("--lowfi-min-bodies", type=int, default=10 ** 9,
                    help="batched/serving modes: use --lowfi only for instances with at least this many spheres")
+    p.add_argument("--inner-tol", type=float, default=1e-6,
+                   help="relative tolerance of each FP32-operator refinement sweep (mixed precision)")
     p.add_argument("--recycle", type=int, default=0,
                    help="solve pairs kept for projected starts of the mobility solves (0 = off)")
     p.add_argument("--fp64-compare", type=int, default=1)
@@ -220,7 +222,8 @@ def run_ours(args, rank, world, local):
     prec = L.LCP_MIXED if args.precision == "mixed" else L.LCP_FP64
     method = L.LCP_BI_PQN if args.method == "bi" else L.LCP_MONO_PQN
     lowfi = lowfi_overrides(args.lowfi, insts[0].n_theta)
-    cfg = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream, recycle=args.recycle, **lowfi)
+    cfg = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream, recycle=args.recycle,
+                       inner_tol=args.inner_tol, **lowfi)
     tol = insts[0].tol
     with torch.cuda.stream(stream):
         cen = [torch.tensor(i.centers, dtype=torch.float64, device=dev) for i in insts]
@@ -706,7 +709,7 @@ def config_dict(args, M: int, N: int, lowfi_desc: str, world: int) -> dict:
             "low_fidelity": lowfi_desc,
             "gmres_tol": 1e-12, "step": "contacts + U_nc slip solve + b + LCP solve",
             "l2": "inputs larger than L2 (Krylov basis 76 MB + operator sweeps per apply)",
-            "recycle": args.recycle, "parallelism": f"instances x{world}"}
+            "inner_tol": args.inner_tol, "recycle": args.recycle, "parallelism": f"instances x{world}"}
 
 
 def lowfi_description(lowfi: dict) -> str:
