@@ -264,7 +264,9 @@ LCP_API int lcp_server_request(lcp_server* srv, uint64_t sim, int method, double
 LCP_API int lcp_server_close(lcp_server* srv, uint64_t sim);
 
 /* Kernel timing.  lcp_profile(ctx, 1) clears the record and starts timing
- * every stresslet-sum launch with CUDA events on the context's stream;
+ * every stresslet-sum launch with CUDA events on the context's stream (inside
+ * the captured GMRES steps too: those graphs then record their own events,
+ * read after each replay, and replay as usual);
  * lcp_profile(ctx, 0) stops and clears.  lcp_profile_read returns the number
  * of launches of a kind (0 = FP32, 1 = FP64, 2 = double-FP32 pair sum; 3 = PQN direction,
  * 4 = PQN step, 5 = quasi-Newton rebuild, 6 = low-fidelity MVP) and their

@@ -177,8 +177,19 @@ struct lcp_ctx {
     int stamp = -1;
     unsigned long long kernels = 0;
     int c32 = 0, c64 = 0, cdf = 0;
+    std::vector<cudaEvent_t> ev;   // timed graphs: event pairs recorded by the graph's own nodes
+    std::vector<int> ev_kind;
   };
   std::vector<ArnoldiGraph> agraphs;
+  // kernel timing inside graphs: while a timed graph is captured, prof_begin /
+  // prof_end record external events into it (cap_ev, cap_kind); after each
+  // replay and the host's synchronisation the pairs are read into prof_ms /
+  // prof_n (per kind) before the same graph can run again
+  std::vector<cudaEvent_t>* cap_ev = nullptr;
+  std::vector<int>* cap_kind = nullptr;
+  int timed_key = -1;                 // graph replayed last with events to read
+  double prof_ms[8] = {0};
+  int prof_n[8] = {0};
   // low-fidelity coarse-grid context (Bi-PQN, cfg.lowfi_n_theta > 0): same
   // bodies and stream, no contacts; its mobility solves run FP32 GMRES only
   lcp_ctx* lo = nullptr;
@@ -214,17 +225,29 @@ struct lcp_ctx {
   } while (0)
 
 // Event timing of a launch (lcp_profile): returns the start event or null.
+// Inside a graph capture the events are external (recorded by graph nodes at
+// every replay) and belong to the graph.
 inline cudaEvent_t prof_begin(lcp_ctx* ctx) {
   if (!ctx->prof) return nullptr;
   cudaEvent_t e;
   if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-  cudaEventRecord(e, ctx->stream);
+  if (ctx->cap_ev)
+    cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, ctx->stream);
   return e;
 }
 inline void prof_end(lcp_ctx* ctx, cudaEvent_t start, int kind) {
   if (!start) return;
   cudaEvent_t e;
   if (cudaEventCreate(&e) != cudaSuccess) return;
+  if (ctx->cap_ev) {
+    cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal);
+    ctx->cap_ev->push_back(start);
+    ctx->cap_ev->push_back(e);
+    ctx->cap_kind->push_back(kind);
+    return;
+  }
   cudaEventRecord(e, ctx->stream);
   ctx->ev_pool.push_back(start);
   ctx->ev_pool.push_back(e);

@@ -290,25 +290,37 @@ static int arnoldi_step(lcp_ctx* ctx, int j, int prec) {
   return LCP_OK;
 }
 
-// Launches Arnoldi step j as a captured CUDA graph (one per column and
-// operator precision, captured on first use and replayed by every later
-// solve of the context), or directly when the context runs on the legacy
-// default stream (not capturable) or kernel profiling is on.
+// Launches Arnoldi step j as a captured CUDA graph (one per column, operator
+// precision and kernel timing on or off, captured on first use and replayed
+// by every later solve of the context), or directly when the context runs on
+// the legacy default stream (not capturable).  With kernel timing on, the
+// graph records its own event pairs around the pair-sum launch; the caller
+// reads them with arnoldi_timing after synchronising.
 static int arnoldi_launch(lcp_ctx* ctx, int j, int prec) {
-  if (!ctx->stream || ctx->prof) return arnoldi_step(ctx, j, prec);
-  const int key = j * 3 + prec;
+  if (!ctx->stream) return arnoldi_step(ctx, j, prec);
+  const int key = (j * 3 + prec) * 2 + (ctx->prof ? 1 : 0);
   const int stamp = ctx->sym ? 1000 + ctx->sym_v : ctx->v32;
   if ((int)ctx->agraphs.size() <= key) ctx->agraphs.resize(key + 1);
   lcp_ctx::ArnoldiGraph& g = ctx->agraphs[key];
   if (!g.exec || g.stamp != stamp) {
     if (g.exec) {
+      LCP_CUDA(cudaStreamSynchronize(ctx->stream));
       cudaGraphExecDestroy(g.exec);
       g.exec = nullptr;
     }
+    for (cudaEvent_t e : g.ev) cudaEventDestroy(e);
+    g.ev.clear();
+    g.ev_kind.clear();
     const unsigned long long n0 = ctx->nlaunch;
     const int c32 = ctx->c_fp32, c64 = ctx->c_fp64, cdf = ctx->c_df64;
     LCP_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    if (ctx->prof) {
+      ctx->cap_ev = &g.ev;
+      ctx->cap_kind = &g.ev_kind;
+    }
     const int st = arnoldi_step(ctx, j, prec);
+    ctx->cap_ev = nullptr;
+    ctx->cap_kind = nullptr;
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
     if (st != LCP_OK || ce != cudaSuccess) {
@@ -339,6 +351,25 @@ static int arnoldi_launch(lcp_ctx* ctx, int j, int prec) {
   ctx->c_fp32 += g.c32;
   ctx->c_fp64 += g.c64;
   ctx->c_df64 += g.cdf;
+  ctx->timed_key = g.ev.empty() ? -1 : key;
+  return LCP_OK;
+}
+
+// After the stream has synchronised: adds the kernel times the last timed
+// graph replay recorded (before that graph can run, and record, again).
+static int arnoldi_timing(lcp_ctx* ctx) {
+  if (ctx->timed_key < 0) return LCP_OK;
+  const lcp_ctx::ArnoldiGraph& g = ctx->agraphs[ctx->timed_key];
+  ctx->timed_key = -1;
+  for (size_t k = 0; k < g.ev_kind.size(); k++) {
+    float ms = 0.f;
+    LCP_CUDA(cudaEventElapsedTime(&ms, g.ev[2 * k], g.ev[2 * k + 1]));
+    const int kind = g.ev_kind[k];
+    if (kind >= 0 && kind < 8) {
+      ctx->prof_ms[kind] += ms;
+      ctx->prof_n[kind]++;
+    }
+  }
   return LCP_OK;
 }
 
@@ -386,6 +417,7 @@ static int gmres(lcp_ctx* ctx, const double* rhs, double* phi, int zero_init, do
       LCP_TRY(arnoldi_launch(ctx, j, prec));
       total++;
       LCP_CUDA(cudaStreamSynchronize(ctx->stream));
+      LCP_TRY(arnoldi_timing(ctx));
       st[0] = ctx->hscal[0];
       st[1] = ctx->hscal[1];
       res = st[0];

@@ -366,6 +366,11 @@ extern "C" int lcp_profile(lcp_ctx* ctx, int enable) {
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   ctx->ev_pool.clear();
   ctx->ev_kind.clear();
+  for (int k = 0; k < 8; k++) {
+    ctx->prof_ms[k] = 0.0;
+    ctx->prof_n[k] = 0;
+  }
+  ctx->timed_key = -1;
   ctx->prof = enable != 0;
   return LCP_OK;
 }
@@ -447,6 +452,10 @@ extern "C" int lcp_profile_read(lcp_ctx* ctx, int kind, int* count, double* tota
   LCP_CUDA(cudaStreamSynchronize(ctx->stream));
   int c = 0;
   double t = 0.0;
+  if (kind >= 0 && kind < 8) {   // launches inside timed graph replays
+    c = ctx->prof_n[kind];
+    t = ctx->prof_ms[kind];
+  }
   for (size_t k = 0; k < ctx->ev_kind.size(); k++) {
     if (ctx->ev_kind[k] != kind) continue;
     float ms = 0.f;
@@ -497,10 +506,12 @@ extern "C" int lcp_setup(const lcp_config* cfg, int n_bodies, const double* cent
 extern "C" void lcp_destroy(lcp_ctx* ctx) {
   if (!ctx) return;
   if (ctx->lo) lcp_destroy(ctx->lo);
-  for (auto& g : ctx->agraphs)
-    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
+  for (auto& g : ctx->agraphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e : g.ev) cudaEventDestroy(e);
+  }
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->arena) cudaFree(ctx->arena);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);

@@ -705,45 +705,36 @@ int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
     return stokes_sym_df_apply(ctx, out);
   }
   LCP_CUDA(cudaMemsetAsync(ctx->partial, 0, sizeof(double) * 3 * (size_t)N * slots, ctx->stream));
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (ctx->prof) {
-    LCP_CUDA(cudaEventCreate(&e0));
-    LCP_CUDA(cudaEventCreate(&e1));
-  }
+  cudaEvent_t e0 = nullptr;
   if (precision == LCP_MIXED) {
     ++ctx->nlaunch, k_to_f32<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(3 * N, phi, ctx->phi32);
     const int ns_pad = (ns + 3) & ~3;
     const size_t smem = pair32_smem(ns, ctx->v32);
-    if (e0) LCP_CUDA(cudaEventRecord(e0, ctx->stream));
+    e0 = prof_begin(ctx);
     ++ctx->nlaunch, kPair32Variants[ctx->v32].kernel<<<grid, PAIR_THREADS, smem, ctx->stream>>>(
                         N, ns, ns_pad, un, ctx->tmpl32, ctx->centers32, ctx->phi32, ctx->partial);
-    if (e1) LCP_CUDA(cudaEventRecord(e1, ctx->stream));
+    prof_end(ctx, e0, 0);
     ctx->c_fp32++;
   } else if (precision == LCP_DF64) {
     ++ctx->nlaunch, k_split_df<<<(3 * N + 255) / 256, 256, 0, ctx->stream>>>(3 * N, phi, ctx->phidf);
     const int ns_pad = (ns + 3) & ~3;
     const size_t smem = stokes_pair_smem(ns, LCP_DF64);
-    if (e0) LCP_CUDA(cudaEventRecord(e0, ctx->stream));
+    e0 = prof_begin(ctx);
     ++ctx->nlaunch, k_pair_df<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, ns_pad, un, ctx->tmpl64,
                                                                          ctx->centers, ctx->phidf, ctx->partial);
-    if (e1) LCP_CUDA(cudaEventRecord(e1, ctx->stream));
+    prof_end(ctx, e0, 2);
     ctx->c_df64++;
   } else {
     const size_t smem = sizeof(double) * (6 * ns + 3 * PAIR_CHUNK * ns);
-    if (e0) LCP_CUDA(cudaEventRecord(e0, ctx->stream));
+    e0 = prof_begin(ctx);
     ++ctx->nlaunch, k_pair64<<<grid, PAIR_THREADS, smem, ctx->stream>>>(N, ns, un, ctx->tmpl64, ctx->centers,
                                                                         phi, ctx->partial);
-    if (e1) LCP_CUDA(cudaEventRecord(e1, ctx->stream));
+    prof_end(ctx, e0, 1);
     ctx->c_fp64++;
   }
   ++ctx->nlaunch, k_finish<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ns, slots, ctx->partial, ctx->coef,
                                                                      ctx->tmpl64, out);
   LCP_CUDA(cudaGetLastError());
-  if (e0) {
-    ctx->ev_pool.push_back(e0);
-    ctx->ev_pool.push_back(e1);
-    ctx->ev_kind.push_back(precision == LCP_MIXED ? 0 : (precision == LCP_DF64 ? 2 : 1));
-  }
   return LCP_OK;
 }
 

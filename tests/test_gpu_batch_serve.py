@@ -278,3 +278,25 @@ def test_captured_arnoldi_graphs_match_direct_launches(small_batch):
     finally:
         L.lcp_destroy(direct)
         L.lcp_destroy(graphed)
+
+
+def test_kernel_timing_inside_graph_replays(small_batch):
+    """With kernel timing on, the GMRES steps still replay as graphs (their own
+    recorded events are read after each replay): the same bitwise result, one timed
+    launch per FP32 apply of the fine grid, positive durations; timing off again
+    returns to the untimed graphs."""
+    inst = small_batch[1]
+    ctx = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, own_stream=1), inst.centers, inst.axes)
+    try:
+        xa, sa, _ = L.lcp_solve(ctx, L.LCP_BI_PQN, inst.tol)
+        L.lcp_profile(ctx, True)
+        xb, sb, _ = L.lcp_solve(ctx, L.LCP_BI_PQN, inst.tol)
+        xc, sc, _ = L.lcp_solve(ctx, L.LCP_BI_PQN, inst.tol)
+        count, ms = L.lcp_profile_read(ctx, 0)
+        L.lcp_profile(ctx, False)
+        xd, _, _ = L.lcp_solve(ctx, L.LCP_BI_PQN, inst.tol)
+        assert np.array_equal(xa, xb) and np.array_equal(xa, xc) and np.array_equal(xa, xd)
+        assert count == sb["fp32_applies"] + sc["fp32_applies"] > 0
+        assert ms > 0.0
+    finally:
+        L.lcp_destroy(ctx)
