@@ -73,7 +73,7 @@ def parse():
     p.add_argument("--lowfi", default="auto",
                    help="Bi-PQN low-fidelity operator: rpy, a coarse boundary-integral grid NTxNP (e.g. 8x16), "
                         "or auto = (n_theta - 3) x 2(n_theta - 3) of the workload's grid")
-    p.add_argument("--lowfi-min-bodies", type=int, default=10 ** 9,
+    p.add_argument("--lowfi-min-bodies", type=int, default=8,
                    help="batched/serving modes: use --lowfi only for instances with at least this many spheres")
     p.add_argument("--inner-tol", type=float, default=1e-6,
                    help="relative tolerance of each FP32-operator refinement sweep (mixed precision)")
@@ -182,6 +182,20 @@ def lowfi_overrides(spec: str, n_theta: int = 0) -> dict:
         return {"lowfi_n_theta": nt, "lowfi_n_phi": 2 * nt, "lowfi_tol": 1e-4, "init_forcing": 1e-3}
     nt, nph = (int(v) for v in spec.lower().split("x"))
     return {"lowfi_n_theta": nt, "lowfi_n_phi": nph}
+
+
+def instance_lowfi(args, inst) -> dict:
+    """Batched and serving modes: the coarse-grid low fidelity (--lowfi) for instances of at
+    least --lowfi-min-bodies spheres, where it cuts high-fidelity MVPs; RPY below (and wherever
+    the coarse grid would not resolve neighbouring spheres)."""
+    return lowfi_overrides(args.lowfi, inst.n_theta) if inst.n_bodies >= args.lowfi_min_bodies else {}
+
+
+def batch_lowfi_description(args) -> str:
+    if args.lowfi == "rpy" or args.lowfi_min_bodies >= 10 ** 9:
+        return "rpy"
+    return (f"coarse grid ({args.lowfi}: n_theta - 3 for 9 x 18 spheres) for instances of at least "
+            f"{args.lowfi_min_bodies} spheres where it resolves neighbours (>= 6 x 12), else rpy")
 
 
 def pair32_kernel_name(variant: str) -> str:
@@ -471,12 +485,8 @@ def run_batched(args):
     insts = batched_instances(args.batch_count)
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    # low fidelity per instance: the coarse grid for instances of at least --lowfi-min-bodies
-    # spheres (where it cuts high-fidelity MVPs), RPY below
-    def lowfi_of(i):
-        return lowfi_overrides(args.lowfi, i.n_theta) if i.n_bodies >= args.lowfi_min_bodies else {}
-
-    ctxs = [L.lcp_setup(L.config_for(i, L.LCP_MIXED, own_stream=1, autotune=1, **lowfi_of(i)), i.centers, i.axes)
+    ctxs = [L.lcp_setup(L.config_for(i, L.LCP_MIXED, own_stream=1, autotune=1, **instance_lowfi(args, i)),
+                        i.centers, i.axes)
             for i in insts]
     t_setup = time.perf_counter() - t0
     xs = [torch.empty(max(L.lcp_sizes(c)[2], 1), dtype=torch.float64, device="cuda") for c in ctxs]
@@ -521,7 +531,8 @@ def run_batched(args):
             "setup_seconds_all": t_setup, "generation_seconds": t_gen,
             "kernel_variants": variants, "clocks": clk,
             "config": {"workload": "256 packings, 8-128 spheres, 98 or 162 nodes per sphere, phi 0.30-0.45",
-                       "method": "bi_pqn", "precision": "mixed", "tol": 1e-8}}
+                       "method": "bi_pqn", "precision": "mixed", "tol": 1e-8,
+                       "low_fidelity": batch_lowfi_description(args)}}
     return line
 
 
@@ -535,7 +546,7 @@ def run_serving(args):
 
     sims = serving_simulations(args.sims)
     rng = np.random.default_rng(77)
-    cfgs = [L.config_for(i, L.LCP_MIXED) for i in sims]
+    cfgs = [L.config_for(i, L.LCP_MIXED, **instance_lowfi(args, i)) for i in sims]
     est = [L.lcp_footprint_estimate(c, i.n_bodies, 6 * i.n_bodies) for c, i in zip(cfgs, sims)]
     budget = int(args.budget_frac * sum(est))
     srv = L.lcp_server_create(args.workers, budget)
@@ -583,7 +594,7 @@ def run_serving(args):
     # FP64 Mono-PQN on the GPU (every simulation, timed)
     t_seq = t64 = 0.0
     for i in sims:
-        c = L.lcp_setup(L.config_for(i, L.LCP_MIXED), i.centers, i.axes)
+        c = L.lcp_setup(L.config_for(i, L.LCP_MIXED, **instance_lowfi(args, i)), i.centers, i.axes)
         ts = time.perf_counter()
         L.lcp_solve(c, L.LCP_BI_PQN, 1e-8)
         t_seq += time.perf_counter() - ts
@@ -607,6 +618,7 @@ def run_serving(args):
             "config": {"workload": f"{len(sims)} simulations, 16-216 spheres, 162 nodes per sphere, "
                                    f"phi 0.35-0.45, {args.sim_steps} steps each",
                        "method": "bi_pqn", "precision": "mixed", "tol": 1e-8,
+                       "low_fidelity": batch_lowfi_description(args),
                        "admission": "server-held: a simulation's context is created once its estimated "
                                     "footprint fits the budget"}}
     return line
