@@ -56,8 +56,15 @@ def solve_alone(ctxs, insts):
     return out
 
 
-def test_batch_equals_alone(small_batch):
-    ctxs = make_ctxs(small_batch)
+# Bi-PQN's low fidelity in the batched and served solves: the RPY mobility, or the
+# boundary-integral mobility on a coarse 6 x 12 grid (the bench's choice where it resolves
+# neighbouring spheres)
+LOWFI = {"rpy": {}, "coarse": dict(lowfi_n_theta=6, lowfi_n_phi=12, lowfi_tol=1e-4, init_forcing=1e-3)}
+
+
+@pytest.mark.parametrize("lowfi", ["rpy", "coarse"])
+def test_batch_equals_alone(small_batch, lowfi):
+    ctxs = make_ctxs(small_batch, **LOWFI[lowfi])
     try:
         alone = solve_alone(ctxs, small_batch)
         xs = [torch.empty(L.lcp_sizes(c)[2], dtype=torch.float64, device="cuda") for c in ctxs]
@@ -118,14 +125,15 @@ def test_server_continuous_batching_and_admission(small_batch):
             L.lcp_destroy(c)
 
 
-def test_server_simulations_held_admission(small_batch):
+@pytest.mark.parametrize("lowfi", ["rpy", "coarse"])
+def test_server_simulations_held_admission(small_batch, lowfi):
     """Server-owned simulations: each request carries its problem, the server creates the
     context only when its estimated footprint fits the budget (holding the request until
     then), keeps it resident across time steps and frees it on close.  Results equal solving
     alone (two steps each), the first solves are checked against the oracle, and the budget
     is never exceeded."""
     insts = small_batch[:6]
-    cfgs = [L.config_for(i, L.LCP_MIXED) for i in insts]
+    cfgs = [L.config_for(i, L.LCP_MIXED, **LOWFI[lowfi]) for i in insts]
     est = [L.lcp_footprint_estimate(c, i.n_bodies, 6 * i.n_bodies) for c, i in zip(cfgs, insts)]
     budget = sum(sorted(est)[:2]) + max(est)          # at most three at once, often two
     # alone: solve, step, solve on a context of its own
