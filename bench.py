@@ -75,6 +75,8 @@ def parse():
                         "or auto = (n_theta - 3) x 2(n_theta - 3) of the workload's grid")
     p.add_argument("--lowfi-min-bodies", type=int, default=8,
                    help="batched/serving modes: use --lowfi only for instances with at least this many spheres")
+    p.add_argument("--warm-start", type=int, default=None,
+                   help="trajectory warm starts (1 slip solve, 2 LCP forces, 3 both); default: the library's")
     p.add_argument("--inner-tol", type=float, default=1e-6,
                    help="relative tolerance of each FP32-operator refinement sweep (mixed precision)")
     p.add_argument("--recycle", type=int, default=0,
@@ -236,8 +238,9 @@ def run_ours(args, rank, world, local):
     prec = L.LCP_MIXED if args.precision == "mixed" else L.LCP_FP64
     method = L.LCP_BI_PQN if args.method == "bi" else L.LCP_MONO_PQN
     lowfi = lowfi_overrides(args.lowfi, insts[0].n_theta)
+    extra = {} if args.warm_start is None else {"warm_start": args.warm_start}
     cfg = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream, recycle=args.recycle,
-                       inner_tol=args.inner_tol, **lowfi)
+                       inner_tol=args.inner_tol, **extra, **lowfi)
     tol = insts[0].tol
     with torch.cuda.stream(stream):
         cen = [torch.tensor(i.centers, dtype=torch.float64, device=dev) for i in insts]
@@ -346,7 +349,7 @@ def run_ours(args, rank, world, local):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             hi = lo = 0
-            kkts, ncs, unc, warm = [], [], [], []
+            kkts, ncs, unc, warm, warm_x = [], [], [], [], []
             for _ in range(steps):
                 _, st, _ = L.lcp_solve(c, method, tol)
                 hi += st["hi_mvps"]
@@ -355,6 +358,7 @@ def run_ours(args, rank, world, local):
                 ncs.append(L.lcp_sizes(c)[2])
                 unc.append(st["unc_gmres_iterations"])
                 warm.append(st["unc_warm_started"])
+                warm_x.append(st["warm_x0"])
                 L.lcp_step(c, inst.dt)
             torch.cuda.synchronize()
             tt = time.perf_counter() - t0
@@ -364,10 +368,10 @@ def run_ours(args, rank, world, local):
                     "hi_mvps_per_step": hi / steps, "lo_mvps_per_step": lo / steps, "max_kkt": max(kkts),
                     "contacts_first_last": [ncs[0], ncs[-1]],
                     "slip_gmres_iterations_per_step": float(np.mean(later)) if later else None,
-                    "slip_warm_started_steps": int(sum(warm))}
+                    "slip_warm_started_steps": int(sum(warm)), "force_warm_started_steps": int(sum(warm_x))}
 
         traj = trajectory(ctx, args.trajectory)
-        traj["warm_start"] = True
+        traj["warm_start_flags"] = int(cfg.warm_start)
         if args.trajectory_cold:
             cfg_cold = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream, warm_start=0, **lowfi)
             ctx_cold = L.lcp_setup(cfg_cold, inst.centers, inst.axes)

@@ -59,6 +59,7 @@ enum { LCP_MONO_PQN = 0, LCP_BI_PQN = 1 };     /* Algorithm 1 / Algorithm 4 */
 enum { LCP_BB_PGD = 2 };                        /* baseline of Sec. 6: PGD with the Barzilai-Borwein step */
 enum { LCP_HIGH = 0, LCP_LOW_RPY = 1 };        /* mobility fidelity */
 enum { LCP_LOW_BIE = 2 };                       /* the boundary-integral mobility on the coarse low-fidelity grid */
+enum { LCP_WARM_SLIP = 1, LCP_WARM_FORCES = 2 };  /* lcp_config.warm_start flags */
 
 typedef struct {
   int n_theta, n_phi;       /* node grid per sphere; n_phi must be even */
@@ -95,11 +96,16 @@ typedef struct {
   /* Bi-PQN's low-fidelity initialisation (Sec. 5.2, solved "approximately"):
    * stops at max(tol, init_forcing * its initial KKT error); 0 = to tol. */
   double init_forcing;
-  /* Warm start of the slip solve for U_nc along a trajectory (lcp_step): start
-   * GMRES from the previous step's density instead of zero.  Consecutive
-   * configurations differ by one time step, so the start is close and fewer
-   * iterations reach the same tolerance.  The paper names reuse across solves as
-   * future work ("Conclusions and Future Work"); 0 = always start from zero. */
+  /* Warm starts along a trajectory (lcp_step), a combination of flags:
+   * LCP_WARM_SLIP: the slip solve for U_nc starts GMRES from the previous step's
+   * density instead of zero; LCP_WARM_FORCES: the next LCP solve (when the caller
+   * gives no x0) starts from the previous step's force on every contact whose
+   * body pair persists (0 on new contacts).  Consecutive configurations differ by
+   * one time step, so both starts are close.  Default LCP_WARM_FORCES: in mixed
+   * precision a started slip solve needs one more double-float residual than it
+   * saves in FP32 iterations; in FP64 mode LCP_WARM_SLIP saves outright.  The
+   * paper names reuse across solves as future work ("Conclusions and Future
+   * Work"); 0 = always start from zero. */
   int warm_start;
   /* Reuse across the mobility solves of one configuration (the MVPs of one LCP
    * share K + P and their right-hand sides differ little): the context keeps
@@ -146,6 +152,7 @@ typedef struct {
   int unc_warm_started;     /* 1 if that slip solve started from the previous step's density */
   int lo_gmres_iterations;  /* GMRES iterations of the coarse-grid low-fidelity solves, summed */
   int recycled_solves;      /* mobility solves (both grids) started from the projection (cfg.recycle) */
+  int warm_x0;              /* 1 if the solve started from the previous time step's forces */
 } lcp_stats;
 
 typedef struct lcp_ctx lcp_ctx;   /* opaque, library-owned */

@@ -18,6 +18,7 @@ LCP_ERR_REJECTED = -8
 LCP_FP64, LCP_MIXED, LCP_DF64 = 0, 1, 2
 LCP_MONO_PQN, LCP_BI_PQN, LCP_BB_PGD = 0, 1, 2
 LCP_HIGH, LCP_LOW_RPY, LCP_LOW_BIE = 0, 1, 2
+LCP_WARM_SLIP, LCP_WARM_FORCES = 1, 2
 
 STATUS_NAMES = {0: "LCP_OK", -1: "LCP_ERR_INVALID_ARG", -2: "LCP_ERR_OOM", -3: "LCP_ERR_CUDA",
                 -4: "LCP_ERR_NOT_CONVERGED", -5: "LCP_ERR_NUMERICAL", -6: "LCP_ERR_TIMEOUT",
@@ -55,7 +56,8 @@ class lcp_stats(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("df64_applies", ctypes.c_int), ("resets", ctypes.c_int),
                 ("ssn_iterations", ctypes.c_int), ("ssn_fallbacks", ctypes.c_int), ("h0_delta", ctypes.c_double),
                 ("unc_gmres_iterations", ctypes.c_int), ("unc_warm_started", ctypes.c_int),
-                ("lo_gmres_iterations", ctypes.c_int), ("recycled_solves", ctypes.c_int)]
+                ("lo_gmres_iterations", ctypes.c_int), ("recycled_solves", ctypes.c_int),
+                ("warm_x0", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

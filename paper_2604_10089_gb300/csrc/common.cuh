@@ -117,6 +117,11 @@ struct lcp_ctx {
   double* phi_unc = nullptr;  // [3N]: density of the last slip solve (warm start along a trajectory)
   bool phi_unc_valid = false;
   int unc_its = 0, unc_warm = 0;   // GMRES iterations / warm start of the last slip solve
+  // warm start of the next LCP solve along a trajectory (cfg.warm_start): the last
+  // solution and its contact pairs, carried onto the next step's contacts
+  double *x_prev = nullptr, *x_warm = nullptr;   // [pair_cap]
+  int *ci_prev = nullptr, *cj_prev = nullptr;    // [pair_cap]
+  bool x_warm_valid = false;
   double* MDx = nullptr;      // [M][6] collisional velocities M D x of the last solve
   double *cnext = nullptr, *anext = nullptr;   // [M][3] advanced centres / axes
   bool have_solution = false;
@@ -260,6 +265,7 @@ int geometry_update(lcp_ctx* ctx);
 int contacts_detect(lcp_ctx* ctx, int* n_out);
 int contacts_upload(lcp_ctx* ctx, int n, const lcp_contact* c);
 int contacts_csr(lcp_ctx* ctx);
+int contacts_carry(lcp_ctx* ctx, int n_prev);   // x_warm from x_prev by body pair
 int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision);
 int stokes_rhs(lcp_ctx* ctx, const double* FT, int include_slip, double* rhs);
 int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef);

@@ -251,6 +251,13 @@ int geometry_build(lcp_ctx* ctx) {
   if (!ctx->tmpl64 || !ctx->tmpl32 || !ctx->ginv || !tn || !ctx->centers32 || !ctx->flags || !ctx->csr_cnt ||
       !ctx->bc_ptr || !ctx->ci || !ctx->cj || !ctx->cnrm || !ctx->gap)
     return LCP_ERR_OOM;
+  if (ctx->cfg.warm_start & LCP_WARM_FORCES) {
+    ctx->x_prev = (double*)ctx_alloc(ctx, sizeof(double) * cap);
+    ctx->x_warm = (double*)ctx_alloc(ctx, sizeof(double) * cap);
+    ctx->ci_prev = (int*)ctx_alloc(ctx, sizeof(int) * cap);
+    ctx->cj_prev = (int*)ctx_alloc(ctx, sizeof(int) * cap);
+    if (!ctx->x_prev || !ctx->x_warm || !ctx->ci_prev || !ctx->cj_prev) return LCP_ERR_OOM;
+  }
   ++ctx->nlaunch, k_template<<<1, 256, 0, ctx->stream>>>(ctx->cfg.n_theta, ctx->cfg.n_phi, ctx->cfg.radius, ctx->tmpl64,
                                          ctx->tmpl32, tn);
   ++ctx->nlaunch, k_gram_inverse<<<1, 32, 0, ctx->stream>>>(ns, ctx->tmpl64, ctx->ginv);
@@ -278,6 +285,32 @@ int contacts_detect(lcp_ctx* ctx, int* n_out) {
   int n = 0;
   memcpy(&n, ctx->hscal + 63, sizeof(int));
   *n_out = n;
+  return LCP_OK;
+}
+
+// x_warm[l] = the previous step's force on the same body pair (i, j), or 0 for
+// a new contact.  Linear search: the previous list need not be sorted (caller
+// contacts), and n_prev is a few hundred to a few thousand.
+__global__ void k_carry_forces(int n, const int* __restrict__ ci, const int* __restrict__ cj, int n_prev,
+                               const int* __restrict__ pi, const int* __restrict__ pj,
+                               const double* __restrict__ x_prev, double* __restrict__ x_warm) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  const int i = ci[l], j = cj[l];
+  double v = 0.0;
+  for (int k = 0; k < n_prev; k++)
+    if (pi[k] == i && pj[k] == j) {
+      v = x_prev[k];
+      break;
+    }
+  x_warm[l] = v;
+}
+
+int contacts_carry(lcp_ctx* ctx, int n_prev) {
+  if (ctx->n == 0) return LCP_OK;
+  ++ctx->nlaunch, k_carry_forces<<<(ctx->n + 127) / 128, 128, 0, ctx->stream>>>(
+                      ctx->n, ctx->ci, ctx->cj, n_prev, ctx->ci_prev, ctx->cj_prev, ctx->x_prev, ctx->x_warm);
+  LCP_CUDA(cudaGetLastError());
   return LCP_OK;
 }
 

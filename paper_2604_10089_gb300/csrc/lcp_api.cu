@@ -61,7 +61,7 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->autotune = 0;
   c->own_stream = 0;
   c->h0_scaling = 1;
-  c->warm_start = 1;
+  c->warm_start = LCP_WARM_FORCES;
   c->recycle = 0;
   c->cuda_stream = nullptr;
 }
@@ -84,6 +84,7 @@ static int validate(const lcp_config* c, int M, const double* centers, std::stri
     *err = "low-fidelity grid: lowfi_n_theta >= 2, even lowfi_n_phi >= 4, at most 512 nodes, lowfi_tol in (0, 0.1]";
     return LCP_ERR_INVALID_ARG;
   }
+  if (c->warm_start < 0 || c->warm_start > (LCP_WARM_SLIP | LCP_WARM_FORCES)) { *err = "warm_start: a combination of LCP_WARM_SLIP and LCP_WARM_FORCES"; return LCP_ERR_INVALID_ARG; }
   if (c->recycle < 0 || c->recycle > c->gmres_restart) { *err = "recycle in [0, gmres_restart]"; return LCP_ERR_INVALID_ARG; }
   if (!(c->init_forcing >= 0.0) || c->init_forcing >= 1.0) { *err = "init_forcing in [0, 1)"; return LCP_ERR_INVALID_ARG; }
   // the direction kernel keeps its r x r systems in shared memory (<= 227 KB: r <= 48)
@@ -239,6 +240,7 @@ static int configure(lcp_ctx* ctx, const double* centers, const double* axes, in
   const int M = ctx->M;
   const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   recycle_reset(ctx);   // K + P changes with the configuration
+  ctx->x_warm_valid = false;
   LCP_CUDA(cudaMemcpyAsync(ctx->centers, centers, sizeof(double) * 3 * M, kind, ctx->stream));
   ctx->has_axes = axes != nullptr;
   if (axes) LCP_CUDA(cudaMemcpyAsync(ctx->axes, axes, sizeof(double) * 3 * M, kind, ctx->stream));
@@ -268,7 +270,7 @@ static int configure(lcp_ctx* ctx, const double* centers, const double* axes, in
   ctx->unc_its = 0;
   ctx->unc_warm = 0;
   if (ctx->has_axes) {
-    const bool use_warm = warm && ctx->cfg.warm_start && ctx->phi_unc_valid;
+    const bool use_warm = warm && (ctx->cfg.warm_start & LCP_WARM_SLIP) && ctx->phi_unc_valid;
     const int g0 = ctx->c_gmres;
     LCP_TRY(mobility_solve(ctx, ctx->FT, 1, ctx->U_nc, use_warm ? ctx->phi_unc : nullptr));
     ctx->unc_its = ctx->c_gmres - g0;
@@ -349,11 +351,24 @@ extern "C" int lcp_step(lcp_ctx* ctx, double dt, double* centers_out, double* ax
   if (!ctx || !(dt > 0.0)) return LCP_ERR_INVALID_ARG;
   if (!ctx->have_solution) { ctx->err = "lcp_step needs a solved LCP (call lcp_solve first)"; return LCP_ERR_INVALID_ARG; }
   const int M = ctx->M;
+  // the solution and its body pairs, carried onto the next step's contacts below
+  const bool carry = (ctx->cfg.warm_start & LCP_WARM_FORCES) && ctx->x_prev && ctx->n > 0;
+  const int n_prev = carry ? ctx->n : 0;
+  if (carry) {
+    LCP_CUDA(cudaMemcpyAsync(ctx->x_prev, ctx->pq_outer.x, sizeof(double) * n_prev, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    LCP_CUDA(cudaMemcpyAsync(ctx->ci_prev, ctx->ci, sizeof(int) * n_prev, cudaMemcpyDeviceToDevice, ctx->stream));
+    LCP_CUDA(cudaMemcpyAsync(ctx->cj_prev, ctx->cj, sizeof(int) * n_prev, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
   ++ctx->nlaunch, k_advance<<<(M + 127) / 128, 128, 0, ctx->stream>>>(M, dt, ctx->centers, ctx->axes, ctx->U_nc,
                                                                      ctx->MDx, ctx->has_axes, ctx->cnext, ctx->anext);
   LCP_CUDA(cudaGetLastError());
   LCP_TRY(configure(ctx, ctx->cnext, ctx->has_axes ? ctx->anext : nullptr, 0, nullptr, true, true));
   ctx->have_solution = false;
+  if (carry) {
+    LCP_TRY(contacts_carry(ctx, n_prev));
+    ctx->x_warm_valid = ctx->n > 0;
+  }
   if (centers_out) LCP_TRY(copy_out(ctx, centers_out, ctx->centers, 3 * (size_t)M));
   if (axes_out && ctx->has_axes) LCP_TRY(copy_out(ctx, axes_out, ctx->axes, 3 * (size_t)M));
   return LCP_OK;
@@ -386,6 +401,8 @@ extern "C" int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n
   size_t b = 0;
   b += sizeof(double) * L * (m + 1) + (cfg->precondition ? sizeof(double) * L * m : 0);   // Krylov bases
   b += sizeof(double) * L * 6 + sizeof(float) * L * 3;                                      // node vectors
+  if (cfg->warm_start & LCP_WARM_FORCES)                                                    // carried forces
+    b += (sizeof(double) * 2 + sizeof(int) * 2) * pairs;
   if (cfg->recycle > 0)                                                                      // reuse pairs
     b += sizeof(double) * (L * (2 * (size_t)cfg->recycle + 2) + 3 * (size_t)cfg->recycle);
   const size_t ntb = (N + 511) / 512, units = ntb * M / 2 + 1;                               // symmetric pair sum

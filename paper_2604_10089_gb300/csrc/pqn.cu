@@ -1167,6 +1167,13 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
   if (ctx->lo) ctx->lo->c_gmres = ctx->lo->c_recycled = 0;
   recycle_reset(ctx);   // each LCP solve depends only on its configuration
   lcp_stats s{};
+  // along a trajectory (lcp_step, cfg.warm_start & LCP_WARM_FORCES) start from the previous step's
+  // forces on the contacts that persist, unless the caller gives x0
+  if (!x0 && ctx->x_warm_valid) {
+    x0 = ctx->x_warm;
+    s.warm_x0 = 1;
+  }
+  ctx->x_warm_valid = false;
   s.unc_gmres_iterations = ctx->unc_its;
   s.unc_warm_started = ctx->unc_warm;
   if (n == 0) {

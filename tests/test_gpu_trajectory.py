@@ -1,9 +1,12 @@
-"""Warm start of the slip solve along a trajectory (lcp_step).
+"""Warm starts along a trajectory (lcp_step).
 
 The slip-driven density of the U_nc solve changes little over one time step,
 so starting GMRES from the previous step's density reaches the same tolerance
 in fewer iterations.  The next LCP's b must not change: it is compared with a
-cold-started run at every step and with the oracle after the first step.
+cold-started run at every step and with the oracle after the first step.  The
+next LCP solve starts from the previous step's forces on the contacts whose
+body pairs persist: checked against a start built here by matching the pairs,
+and against the oracle's KKT error at the advanced configuration.
 """
 import numpy as np
 import pytest
@@ -17,7 +20,7 @@ from oracle.contacts import contact_matrix, detect_contacts  # noqa: E402
 from oracle.lcp import lcp_data  # noqa: E402
 from workloads import make_instance  # noqa: E402
 
-from .cases import dense_case  # noqa: E402
+from .cases import dense_case, kkt_bound  # noqa: E402
 
 
 def rel(a, b):
@@ -36,13 +39,15 @@ def _rotate(e, w, dt):
 @pytest.mark.parametrize("precision", [L.LCP_FP64, L.LCP_MIXED])
 def test_warm_started_slip_solve_same_b_fewer_iterations(precision):
     inst = make_instance("spheres8_grid7x14", 2)
-    warm = L.lcp_setup(L.config_for(inst, precision, warm_start=1), inst.centers, inst.axes)
+    warm = L.lcp_setup(L.config_for(inst, precision, warm_start=L.LCP_WARM_SLIP), inst.centers, inst.axes)
     cold = L.lcp_setup(L.config_for(inst, precision, warm_start=0), inst.centers, inst.axes)
     try:
         its_w, its_c = [], []
         for step in range(4):
-            xw, sw, _ = L.lcp_solve(warm, L.LCP_MONO_PQN, inst.tol)
-            xc, sc, _ = L.lcp_solve(cold, L.LCP_MONO_PQN, inst.tol)
+            # both LCPs from x = 0, so that only the slip solve's start differs
+            n = L.lcp_sizes(warm)[2]
+            xw, sw, _ = L.lcp_solve(warm, L.LCP_MONO_PQN, inst.tol, x0=np.zeros(n))
+            xc, sc, _ = L.lcp_solve(cold, L.LCP_MONO_PQN, inst.tol, x0=np.zeros(n))
             assert sw["converged"] == 1 and sc["converged"] == 1
             assert sw["unc_warm_started"] == (1 if step > 0 else 0) and sc["unc_warm_started"] == 0
             if step > 0:
@@ -53,8 +58,9 @@ def test_warm_started_slip_solve_same_b_fewer_iterations(precision):
             L.lcp_step(cold, inst.dt)
             assert rel(L.lcp_get_b(warm), L.lcp_get_b(cold)) <= 1e-10
             assert rel(L.lcp_get_unc(warm), L.lcp_get_unc(cold)) <= 1e-10
-        _, sw, _ = L.lcp_solve(warm, L.LCP_MONO_PQN, inst.tol)
-        _, sc, _ = L.lcp_solve(cold, L.LCP_MONO_PQN, inst.tol)
+        n = L.lcp_sizes(warm)[2]
+        _, sw, _ = L.lcp_solve(warm, L.LCP_MONO_PQN, inst.tol, x0=np.zeros(n))
+        _, sc, _ = L.lcp_solve(cold, L.LCP_MONO_PQN, inst.tol, x0=np.zeros(n))
         its_w.append(sw["unc_gmres_iterations"])
         its_c.append(sc["unc_gmres_iterations"])
         assert all(w > 0 for w in its_w)
@@ -68,7 +74,7 @@ def test_warm_started_step_matches_oracle():
     """Eq. (dvi) with the warm-started slip solve: the next b against the oracle."""
     case = dense_case("spheres8_grid7x14", 4)
     inst = case["inst"]
-    ctx = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, warm_start=1), inst.centers, inst.axes)
+    ctx = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, warm_start=L.LCP_WARM_SLIP), inst.centers, inst.axes)
     try:
         x, _, _ = L.lcp_solve(ctx, L.LCP_MONO_PQN, inst.tol)
         c_new, a_new = L.lcp_step(ctx, inst.dt)
@@ -86,3 +92,73 @@ def test_warm_started_step_matches_oracle():
         assert rel(L.lcp_get_b(ctx), b_next) <= 1e-9
     finally:
         L.lcp_destroy(ctx)
+
+
+def carried(x, pairs_prev, pairs_next):
+    """The previous forces on the next contacts, matched by body pair (0 for new pairs)."""
+    prev = {}
+    for l, (i, j) in enumerate(map(tuple, pairs_prev)):
+        prev.setdefault((int(i), int(j)), x[l])
+    return np.array([prev.get((int(i), int(j)), 0.0) for i, j in pairs_next])
+
+
+@pytest.mark.parametrize("method", [L.LCP_MONO_PQN, L.LCP_BI_PQN])
+def test_lcp_warm_start_carries_forces_by_body_pair(method):
+    """After lcp_step the next solve starts from the previous forces on persisting pairs:
+    bitwise the same solve as one started from that x0 built here."""
+    inst = make_instance("spheres8_grid7x14", 3)
+    ctx = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, warm_start=L.LCP_WARM_FORCES), inst.centers, inst.axes)
+    try:
+        x, st, _ = L.lcp_solve(ctx, method, inst.tol)
+        assert st["warm_x0"] == 0
+        kept = new = 0
+        for step in range(3):
+            pairs_prev = L.lcp_get_contacts(ctx)[0]
+            L.lcp_step(ctx, inst.dt)
+            pairs = L.lcp_get_contacts(ctx)[0]
+            x0 = carried(x, pairs_prev, pairs)
+            xa, sa, _ = L.lcp_solve(ctx, method, inst.tol)            # carried start
+            xb, sb, _ = L.lcp_solve(ctx, method, inst.tol, x0=x0)     # the same start, given
+            assert sa["warm_x0"] == 1 and sb["warm_x0"] == 0
+            assert sa["converged"] == 1
+            assert np.array_equal(xa, xb)
+            kept += int(np.count_nonzero(x0))
+            new += int(x0.size - np.count_nonzero(x0))
+            x = xa
+        assert kept > 0
+        # an update to an arbitrary configuration starts from zero again
+        L.lcp_update(ctx, inst.centers, inst.axes)
+        _, sc, _ = L.lcp_solve(ctx, method, inst.tol)
+        assert sc["warm_x0"] == 0
+    finally:
+        L.lcp_destroy(ctx)
+
+
+def test_lcp_warm_started_trajectory_matches_oracle():
+    """Three warm-started steps: each solution's KKT error against the oracle's dense A
+    and b at the advanced configuration."""
+    inst = make_instance("spheres8_grid7x14", 4)
+    warm = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, warm_start=L.LCP_WARM_SLIP | L.LCP_WARM_FORCES),
+                       inst.centers, inst.axes)
+    cold = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, warm_start=0), inst.centers, inst.axes)
+    try:
+        L.lcp_solve(warm, L.LCP_BI_PQN, inst.tol)
+        L.lcp_solve(cold, L.LCP_BI_PQN, inst.tol)
+        for step in range(3):
+            c, a = L.lcp_step(warm, inst.dt)
+            L.lcp_step(cold, inst.dt)
+            x, st, _ = L.lcp_solve(warm, L.LCP_BI_PQN, inst.tol)
+            _, sc, _ = L.lcp_solve(cold, L.LCP_BI_PQN, inst.tol)
+            assert st["warm_x0"] == 1 and sc["warm_x0"] == 0
+            mob = DenseMobility(c, inst.n_theta, inst.n_phi, a=inst.radius)
+            pairs, normals, gaps = detect_contacts(c, inst.contact_radius, inst.delta)
+            assert np.array_equal(pairs, L.lcp_get_contacts(warm)[0])
+            D = contact_matrix(inst.n_bodies, pairs, normals)
+            A, b = lcp_data(D, mob.matrix(), mob.apply(np.zeros(6 * inst.n_bodies), axes=a), gaps, inst.dt)
+            g = A @ x + b
+            g_gpu = L.lcp_apply_A(warm, x) + L.lcp_get_b(warm)
+            eps_op, _ = kkt_bound(inst.tol, x, g, g_gpu, b, st["hi_mvps"])
+            assert np.linalg.norm(np.minimum(x, g)) <= inst.tol + eps_op
+    finally:
+        L.lcp_destroy(warm)
+        L.lcp_destroy(cold)
