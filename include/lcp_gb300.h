@@ -59,7 +59,7 @@ enum { LCP_MONO_PQN = 0, LCP_BI_PQN = 1 };     /* Algorithm 1 / Algorithm 4 */
 enum { LCP_BB_PGD = 2 };                        /* baseline of Sec. 6: PGD with the Barzilai-Borwein step */
 enum { LCP_HIGH = 0, LCP_LOW_RPY = 1 };        /* mobility fidelity */
 enum { LCP_LOW_BIE = 2 };                       /* the boundary-integral mobility on the coarse low-fidelity grid */
-enum { LCP_WARM_SLIP = 1, LCP_WARM_FORCES = 2 };  /* lcp_config.warm_start flags */
+enum { LCP_WARM_SLIP = 1, LCP_WARM_FORCES = 2, LCP_WARM_NO_INIT = 4 };  /* lcp_config.warm_start flags */
 
 typedef struct {
   int n_theta, n_phi;       /* node grid per sphere; n_phi must be even */
@@ -101,7 +101,10 @@ typedef struct {
    * density instead of zero; LCP_WARM_FORCES: the next LCP solve (when the caller
    * gives no x0) starts from the previous step's force on every contact whose
    * body pair persists (0 on new contacts).  Consecutive configurations differ by
-   * one time step, so both starts are close.  Default LCP_WARM_FORCES: in mixed
+   * one time step, so both starts are close.  LCP_WARM_NO_INIT (with
+   * LCP_WARM_FORCES): Bi-PQN takes the carried forces as x(0) instead of running
+   * its low-fidelity initialisation from them (Algorithm 4 runs it; off by
+   * default).  Default LCP_WARM_FORCES: in mixed
    * precision a started slip solve needs one more double-float residual than it
    * saves in FP32 iterations; in FP64 mode LCP_WARM_SLIP saves outright.  The
    * paper names reuse across solves as future work ("Conclusions and Future

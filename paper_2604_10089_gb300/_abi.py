@@ -18,7 +18,7 @@ LCP_ERR_REJECTED = -8
 LCP_FP64, LCP_MIXED, LCP_DF64 = 0, 1, 2
 LCP_MONO_PQN, LCP_BI_PQN, LCP_BB_PGD = 0, 1, 2
 LCP_HIGH, LCP_LOW_RPY, LCP_LOW_BIE = 0, 1, 2
-LCP_WARM_SLIP, LCP_WARM_FORCES = 1, 2
+LCP_WARM_SLIP, LCP_WARM_FORCES, LCP_WARM_NO_INIT = 1, 2, 4
 
 STATUS_NAMES = {0: "LCP_OK", -1: "LCP_ERR_INVALID_ARG", -2: "LCP_ERR_OOM", -3: "LCP_ERR_CUDA",
                 -4: "LCP_ERR_NOT_CONVERGED", -5: "LCP_ERR_NUMERICAL", -6: "LCP_ERR_TIMEOUT",

@@ -84,7 +84,7 @@ static int validate(const lcp_config* c, int M, const double* centers, std::stri
     *err = "low-fidelity grid: lowfi_n_theta >= 2, even lowfi_n_phi >= 4, at most 512 nodes, lowfi_tol in (0, 0.1]";
     return LCP_ERR_INVALID_ARG;
   }
-  if (c->warm_start < 0 || c->warm_start > (LCP_WARM_SLIP | LCP_WARM_FORCES)) { *err = "warm_start: a combination of LCP_WARM_SLIP and LCP_WARM_FORCES"; return LCP_ERR_INVALID_ARG; }
+  if (c->warm_start < 0 || c->warm_start > (LCP_WARM_SLIP | LCP_WARM_FORCES | LCP_WARM_NO_INIT)) { *err = "warm_start: a combination of the LCP_WARM_* flags"; return LCP_ERR_INVALID_ARG; }
   if (c->recycle < 0 || c->recycle > c->gmres_restart) { *err = "recycle in [0, gmres_restart]"; return LCP_ERR_INVALID_ARG; }
   if (!(c->init_forcing >= 0.0) || c->init_forcing >= 1.0) { *err = "init_forcing in [0, 1)"; return LCP_ERR_INVALID_ARG; }
   // the direction kernel keeps its r x r systems in shared memory (<= 227 KB: r <= 48)

@@ -1210,7 +1210,9 @@ int lcp_solve_device(lcp_ctx* ctx, int method, double tol, const double* x0, dou
     // low-fidelity initialisation: Mono-PQN on A_hat from x0, its pairs kept in pi
     RunStats r0;
     ++ctx->nlaunch, k_pqn_init<<<1, PQN_T, 0, ctx->stream>>>(pi, x0);
-    LCP_TRY(run_mono(ctx, pi, mvp_low, 0, ctx->b, nullptr, tol, ctx->cfg.kmax_inner, &r0, ctx->cfg.init_forcing));
+    // LCP_WARM_NO_INIT: a start carried from the previous step is taken as x(0) as it is
+    const int kinit = (s.warm_x0 && (ctx->cfg.warm_start & LCP_WARM_NO_INIT)) ? 0 : ctx->cfg.kmax_inner;
+    LCP_TRY(run_mono(ctx, pi, mvp_low, 0, ctx->b, nullptr, tol, kinit, &r0, ctx->cfg.init_forcing));
     int lo = r0.mvps, hi = 0, inner_total = r0.iterations;
     s.resets = r0.resets;
     double t_lo = r0.t_mvp, t_hi = 0.0;

@@ -14,7 +14,8 @@ import numpy as np
 from . import _abi
 from ._abi import (LCP_BB_PGD, LCP_BI_PQN, LCP_ERR_CUDA, LCP_ERR_INVALID_ARG, LCP_ERR_NOT_CONVERGED,  # noqa: F401
                    LCP_ERR_NUMERICAL, LCP_ERR_OOM, LCP_ERR_REJECTED, LCP_ERR_TIMEOUT, LCP_DF64, LCP_FP64, LCP_HIGH,
-                   LCP_LOW_BIE, LCP_LOW_RPY, LCP_MIXED, LCP_MONO_PQN, LCP_OK, LCP_WARM_FORCES, LCP_WARM_SLIP,
+                   LCP_LOW_BIE, LCP_LOW_RPY, LCP_MIXED, LCP_MONO_PQN, LCP_OK, LCP_WARM_FORCES, LCP_WARM_NO_INIT,
+                   LCP_WARM_SLIP,
                    STATUS_NAMES)
 
 

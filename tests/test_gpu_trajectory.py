@@ -134,12 +134,13 @@ def test_lcp_warm_start_carries_forces_by_body_pair(method):
         L.lcp_destroy(ctx)
 
 
-def test_lcp_warm_started_trajectory_matches_oracle():
-    """Three warm-started steps: each solution's KKT error against the oracle's dense A
-    and b at the advanced configuration."""
+@pytest.mark.parametrize("flags", [L.LCP_WARM_SLIP | L.LCP_WARM_FORCES, L.LCP_WARM_FORCES | L.LCP_WARM_NO_INIT])
+def test_lcp_warm_started_trajectory_matches_oracle(flags):
+    """Three warm-started steps (with Bi-PQN's low-fidelity initialisation, or with the
+    carried forces taken as x(0) directly): each solution's KKT error against the
+    oracle's dense A and b at the advanced configuration."""
     inst = make_instance("spheres8_grid7x14", 4)
-    warm = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, warm_start=L.LCP_WARM_SLIP | L.LCP_WARM_FORCES),
-                       inst.centers, inst.axes)
+    warm = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, warm_start=flags), inst.centers, inst.axes)
     cold = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, warm_start=0), inst.centers, inst.axes)
     try:
         L.lcp_solve(warm, L.LCP_BI_PQN, inst.tol)
