@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -424,6 +425,8 @@ def run_ours(args, rank, world, local):
         "hi_mvps": [s["hi_mvps"] for s in stats], "lo_mvps": [s["lo_mvps"] for s in stats],
         "e_mvps": [round(s["e_mvps"], 3) for s in stats], "iterations": [s["iterations"] for s in stats],
         "gmres_iterations": [s["gmres_iterations"] for s in stats],
+        "gmres_iterations_per_hi_mvp": float(sum(s["gmres_iterations"] for s in stats)
+                                             / max(1, sum(s["hi_mvps"] for s in stats))),
         "lo_gmres_iterations": [s["lo_gmres_iterations"] for s in stats],
         "recycled_solves": [s["recycled_solves"] for s in stats],
         "fp32_applies": [s["fp32_applies"] for s in stats], "fp64_applies": [s["fp64_applies"] for s in stats],
@@ -702,6 +705,26 @@ def c1_oracle_solve(index: int = 1) -> dict:
             "kkt": float(kkt_abs(x, A @ x + b)), "solves_per_s": 1.0 / t}
 
 
+def host_cpu() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm implementer and part)."""
+    try:
+        text = open("/proc/cpuinfo").read()
+    except OSError:
+        return platform.machine()
+    fields = {}
+    for line in text.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip(), v.strip())
+    if "model name" in fields:
+        return fields["model name"]
+    parts = [platform.machine()]
+    for k in ("CPU implementer", "CPU part", "CPU variant"):
+        if k in fields:
+            parts.append(f"{k.split()[-1]} {fields[k]}")
+    return " ".join(parts)
+
+
 def c1_anchor() -> dict:
     """The complete 8-sphere oracle solve on one core and on all host cores (subprocesses,
     so that the BLAS thread count is fixed before numpy loads)."""
@@ -774,7 +797,8 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "ms_per_step": 1e3 * float(np.mean(step_s)), "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(args, M, N, lowfi_description(lowfi), world),
-            "cpu_baseline": {"value": value, "unit": "LCP solves/s", "cores": first["cores"], "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "LCP solves/s", "cores": first["cores"], "cpu": host_cpu(),
+                             "kind": "oracle",
                              "sample": sample, "fine_solve_seconds": first["fine_seconds"],
                              "fine_gmres_iterations": first["fine_gmres_iterations"],
                              "coarse_solve_seconds": t_c, "mvps_per_lcp": REFERENCE_MVPS,
@@ -822,7 +846,7 @@ def main():
             o = oracle_mobility_solves(args.workload, 0, r["lowfi_cfg"], coarse_solves=2)
             t_c = float(np.mean(o["coarse_seconds"]))
             cpu = {"value": oracle_lcp_rate(o["fine_seconds"], t_c, hi, lo), "unit": "LCP solves/s",
-                   "cores": o["cores"], "kind": "oracle",
+                   "cores": o["cores"], "cpu": host_cpu(), "kind": "oracle",
                    "sample": f"one complete fine-grid slip solve of a {args.workload} configuration "
                              f"({o['fine_seconds']:.2f} s, {o['fine_gmres_iterations']} FP64 GMRES iterations to "
                              f"1e-12) and {len(o['coarse_seconds'])} complete low-fidelity solves ({t_c:.3f} s each"
