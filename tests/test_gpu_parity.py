@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_2604_10089_gb300 as L  # noqa: E402
 from oracle.bie import DenseMobility  # noqa: E402
-from oracle.lcp import kkt_abs  # noqa: E402
+from oracle.lcp import brute_force, kkt_abs  # noqa: E402
 from oracle.mf import MatrixFreeMobility  # noqa: E402
 from oracle.rpy import rpy_matrix  # noqa: E402
 from workloads import make_instance  # noqa: E402
@@ -161,6 +161,26 @@ def check_solution(case, x, tol, ctx, hi_mvps):
     act_ref, amb_ref = active_set(xs, A @ xs + b)
     assert act - amb_ref == act_ref - amb, (sorted(act), sorted(act_ref))
     assert np.abs(x - xs).max() <= 1e-5 * max(1.0, np.abs(xs).max())
+
+
+def test_c1_thirty_two_seeds_plain_fp64_mono_pqn():
+    """The 8-sphere configuration's run: plain FP64 Mono-PQN on 32 seeded instances (9-11
+    contacts each), each against its dense oracle: same active set, KKT error within
+    tol + eps_op, x within 1e-5 of the projected Gauss-Seidel solution, and that solution
+    equal to the brute-force enumeration of active sets."""
+    for index in range(32):
+        case = dense_case("spheres8_grid7x14", index)
+        inst = case["inst"]
+        xbf = brute_force(case["A"], case["b"])
+        assert np.abs(xbf - case["x"]).max() <= 1e-9 * max(1.0, np.abs(xbf).max()), index
+        ctx = L.lcp_setup(L.config_for(inst, L.LCP_FP64), inst.centers, inst.axes)
+        try:
+            assert L.lcp_sizes(ctx)[2] == case["b"].size, index
+            x, st, status = L.lcp_solve(ctx, L.LCP_MONO_PQN, inst.tol)
+            assert status == L.LCP_OK and st["converged"] == 1, index
+            check_solution(case, x, inst.tol, ctx, st["hi_mvps"])
+        finally:
+            L.lcp_destroy(ctx)
 
 
 @pytest.mark.parametrize("index", [0, 1, 2, 3])
