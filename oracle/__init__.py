@@ -22,8 +22,10 @@ Contents (each function cites the passage it follows):
                   dense matrix does not fit
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
-against closed forms, invariants or brute force, except the physical accuracy
-of the discretised boundary-integral operator near contact, which no closed
-form fixes (parity unpinned: the GPU path is compared with the same discrete
-operator, not with exact Stokes flow).
+against closed forms, invariants or brute force.  The physical accuracy of the
+discretised boundary-integral operator for interacting spheres is pinned
+against exact two-sphere Stokes flow (moving together and approaching each
+other along the line of centres) at centre distances of 2.5 radii and more;
+closer than that, at gaps below about 0.2 radii, the plain quadrature misses
+the lubrication resistance and that regime stays outside the workloads.
 """

@@ -374,3 +374,26 @@ def test_update_grows_the_contact_buffers():
         check_solution(case, x, inst.tol, ctx, st["hi_mvps"])
     finally:
         L.lcp_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [L.LCP_FP64, L.LCP_MIXED])
+@pytest.mark.parametrize("R", [2.5, 4.0])
+def test_two_sphere_resistances_match_exact_stokes_flow(precision, R):
+    """The GPU mobility of two spheres on the workloads' 11 x 22 grid against exact Stokes
+    flow (not only against the oracle): moving together along their line of centres
+    (Stimson & Jeffery) and approaching each other (Brenner), at the steric-shell distance
+    2.5 radii and at 4."""
+    from .exact_stokes import brenner_approach, stimson_jeffery
+    cfg = L.lcp_default_config(n_theta=11, n_phi=22, radius=1.0, contact_radius=1.25, precision=precision)
+    centers = np.array([[0.0, 0.0, -R / 2], [0.0, 0.0, R / 2]])
+    ctx = L.lcp_setup(cfg, centers)
+    try:
+        for sign, exact, bound in ((1.0, stimson_jeffery(R), 1e-5), (-1.0, brenner_approach(R), 6e-4)):
+            FT = np.zeros(12)
+            FT[2], FT[8] = 1.0, sign
+            U = L.mobility_apply(ctx, FT)
+            assert abs(U[8] - sign * U[2]) <= 1e-9 * abs(U[2])
+            lam = 1.0 / (6.0 * np.pi * U[2])
+            assert abs(lam - exact) <= bound * exact, (sign, lam, exact)
+    finally:
+        L.lcp_destroy(ctx)
