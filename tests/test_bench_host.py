@@ -29,3 +29,29 @@ def test_kernel_names_and_traffic_guard():
         assert info["bytes_per_launch"] > 0
         h = bench.source_sha1(kname)
         assert len(h) == 40 and int(h, 16) >= 0, kname
+
+
+def test_batched_and_serving_low_fidelity_per_instance():
+    """Batched and serving modes: the coarse grid for instances of at least --lowfi-min-bodies
+    spheres where it resolves neighbours (9 x 18 -> 6 x 12), RPY for 7 x 14 spheres and below
+    the threshold; the description says which."""
+    import argparse
+
+    from workloads import make_instance
+    big = make_instance("spheres64_grid9x18", 0)          # 9 x 18 nodes
+    small = make_instance("spheres8_grid7x14", 0)         # 7 x 14 nodes
+    args = argparse.Namespace(lowfi="auto", lowfi_min_bodies=8)
+    assert bench.instance_lowfi(args, big)["lowfi_n_theta"] == 6
+    assert bench.instance_lowfi(args, small) == {}
+    assert "coarse grid" in bench.batch_lowfi_description(args)
+    args.lowfi_min_bodies = 100
+    assert bench.instance_lowfi(args, big) == {}
+    args.lowfi_min_bodies = 10 ** 9
+    assert bench.batch_lowfi_description(args) == "rpy"
+    args = argparse.Namespace(lowfi="rpy", lowfi_min_bodies=8)
+    assert bench.instance_lowfi(args, big) == {} and bench.batch_lowfi_description(args) == "rpy"
+
+
+def test_host_cpu_names_the_processor():
+    name = bench.host_cpu()
+    assert isinstance(name, str) and name.strip()
