@@ -381,9 +381,9 @@ def test_update_grows_the_contact_buffers():
 def test_two_sphere_resistances_match_exact_stokes_flow(precision, R):
     """The GPU mobility of two spheres on the workloads' 11 x 22 grid against exact Stokes
     flow (not only against the oracle): moving together along their line of centres
-    (Stimson & Jeffery) and approaching each other (Brenner), at the steric-shell distance
-    2.5 radii and at 4."""
-    from .exact_stokes import brenner_approach, stimson_jeffery
+    (Stimson & Jeffery), approaching each other (Brenner) and rotating about that line in
+    the same or opposite senses (Jeffery), at the steric-shell distance 2.5 radii and at 4."""
+    from .exact_stokes import brenner_approach, jeffery_rotation, stimson_jeffery
     cfg = L.lcp_default_config(n_theta=11, n_phi=22, radius=1.0, contact_radius=1.25, precision=precision)
     centers = np.array([[0.0, 0.0, -R / 2], [0.0, 0.0, R / 2]])
     ctx = L.lcp_setup(cfg, centers)
@@ -395,5 +395,14 @@ def test_two_sphere_resistances_match_exact_stokes_flow(precision, R):
             assert abs(U[8] - sign * U[2]) <= 1e-9 * abs(U[2])
             lam = 1.0 / (6.0 * np.pi * U[2])
             assert abs(lam - exact) <= bound * exact, (sign, lam, exact)
+        # rotation about the line of centres, in the same and in opposite senses (Jeffery)
+        for sign in (1.0, -1.0):
+            exact = jeffery_rotation(R, same_sense=sign > 0)
+            FT = np.zeros(12)
+            FT[5], FT[11] = 1.0, sign
+            U = L.mobility_apply(ctx, FT)
+            assert abs(U[11] - sign * U[5]) <= 1e-9 * abs(U[5])
+            zeta = 1.0 / (8.0 * np.pi * U[5])
+            assert abs(zeta - exact) <= 3e-5 * exact, (sign, zeta, exact)
     finally:
         L.lcp_destroy(ctx)

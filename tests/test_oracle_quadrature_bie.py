@@ -243,3 +243,33 @@ def test_approaching_spheres_match_the_exact_resistance(R):
         assert abs(U[8] + U[2]) <= 1e-13 * abs(U[2])
         errs.append(abs(1.0 / (6.0 * np.pi * U[2]) - exact) / exact)
     assert errs[0] <= 6e-4 and errs[1] < errs[0], errs
+
+
+def test_rotation_series_limits():
+    """Jeffery's series against its far-field limits 1 -+ (a/R)^3 (and 1 at infinity)."""
+    from .exact_stokes import jeffery_rotation
+    for R in (30.0, 100.0):
+        assert abs(jeffery_rotation(R, same_sense=True) - (1.0 - R ** -3)) <= 10.0 * R ** -6
+        assert abs(jeffery_rotation(R, same_sense=False) - (1.0 + R ** -3)) <= 10.0 * R ** -6
+    assert (jeffery_rotation(2.5, same_sense=True) < jeffery_rotation(4.0, same_sense=True) < 1.0
+            < jeffery_rotation(4.0, same_sense=False) < jeffery_rotation(2.5, same_sense=False))
+
+
+@pytest.mark.parametrize("same_sense", [True, False])
+@pytest.mark.parametrize("R", [2.5, 3.0, 4.0])
+def test_spheres_rotating_about_line_of_centres_match_jeffery(R, same_sense):
+    """Torques about the line of centres (the rotlet right-hand side and the rigid-body
+    extraction): the discretised mobility gives Jeffery's exact torque to <= 3e-5 on
+    11 x 22 nodes and converges under refinement; no translation results."""
+    from .exact_stokes import jeffery_rotation
+    exact = jeffery_rotation(R, same_sense=same_sense)
+    c = np.array([[0.0, 0.0, -R / 2], [0.0, 0.0, R / 2]])
+    FT = np.zeros(12)
+    FT[5], FT[11] = 1.0, (1.0 if same_sense else -1.0)
+    errs = []
+    for nt in (11, 15):
+        U = DenseMobility(c, nt, 2 * nt).apply(FT)
+        assert abs(U[11] - FT[11] * U[5]) <= 1e-13 * abs(U[5])
+        assert np.abs(U[[0, 1, 2, 6, 7, 8]]).max() <= 1e-12 * abs(U[5])
+        errs.append(abs(1.0 / (8.0 * np.pi * U[5]) - exact) / exact)
+    assert errs[0] <= 3e-5 and errs[1] < errs[0], errs
