@@ -78,6 +78,8 @@ def parse():
                    help="batched/serving modes: use --lowfi only for instances with at least this many spheres")
     p.add_argument("--warm-start", type=int, default=None,
                    help="trajectory warm starts (1 slip solve, 2 LCP forces, 3 both); default: the library's")
+    p.add_argument("--self-quadrature", type=int, default=0,
+                   help="1: high-order self-interaction quadrature (one 3ns x 3ns correction per body)")
     p.add_argument("--inner-tol", type=float, default=1e-6,
                    help="relative tolerance of each FP32-operator refinement sweep (mixed precision)")
     p.add_argument("--recycle", type=int, default=0,
@@ -241,7 +243,7 @@ def run_ours(args, rank, world, local):
     lowfi = lowfi_overrides(args.lowfi, insts[0].n_theta)
     extra = {} if args.warm_start is None else {"warm_start": args.warm_start}
     cfg = L.config_for(insts[0], prec, cuda_stream=stream.cuda_stream, recycle=args.recycle,
-                       inner_tol=args.inner_tol, **extra, **lowfi)
+                       inner_tol=args.inner_tol, self_quadrature=args.self_quadrature, **extra, **lowfi)
     tol = insts[0].tol
     with torch.cuda.stream(stream):
         cen = [torch.tensor(i.centers, dtype=torch.float64, device=dev) for i in insts]
@@ -748,7 +750,8 @@ def config_dict(args, M: int, N: int, lowfi_desc: str, world: int) -> dict:
             "low_fidelity": lowfi_desc,
             "gmres_tol": 1e-12, "step": "contacts + U_nc slip solve + b + LCP solve",
             "l2": "inputs larger than L2 (Krylov basis 76 MB + operator sweeps per apply)",
-            "inner_tol": args.inner_tol, "recycle": args.recycle, "parallelism": f"instances x{world}"}
+            "inner_tol": args.inner_tol, "recycle": args.recycle, "self_quadrature": args.self_quadrature,
+            "parallelism": f"instances x{world}"}
 
 
 def lowfi_description(lowfi: dict) -> str:

@@ -124,6 +124,16 @@ typedef struct {
    * pairs do not predict.  The paper names reuse across solves as future work.
    * 0 = off (default); at most gmres_restart. */
   int recycle;
+  /* 1: high-order quadrature of each sphere's self-interaction.  The pair sums
+   * take a sphere's double layer on its own nodes by the product rule with the
+   * global singularity subtraction (exact on rigid motions, algebraically
+   * accurate otherwise); this adds one dense 3 ns x 3 ns correction, the same
+   * for every body (all share the template), computed once per grid from a
+   * polar quadrature about each node and the band-limited projection of the
+   * density, and applied per body as a small GEMM in the sums' precision.  It
+   * makes the two-sphere mobilities converge spectrally (the isolated-sphere
+   * preconditioner includes it).  0 (default): the product rule only. */
+  int self_quadrature;
 } lcp_config;
 
 typedef struct {
@@ -284,6 +294,14 @@ LCP_API int lcp_server_close(lcp_server* srv, uint64_t sim);
 LCP_API int lcp_profile(lcp_ctx* ctx, int enable);
 LCP_API int lcp_profile_read(lcp_ctx* ctx, int kind, int* count, double* total_ms);
 
+/* The self-interaction correction of cfg.self_quadrature for one sphere
+ * template (Gauss-Legendre n_theta x uniform n_phi nodes of radius `radius`,
+ * node q = j n_phi + k with cos(theta_j) ascending): C, host [3 ns x 3 ns]
+ * row-major (ns = n_theta n_phi), (C phi)_{3p+i} = sum_q C[3p+i][3q+j] phi_{3q+j}
+ * is added to (K phi) on every body.  Computed on the host (cached per grid).
+ * LCP_ERR_INVALID_ARG for a grid lcp_setup would refuse or a NULL C. */
+LCP_API int lcp_self_correction(int n_theta, int n_phi, double radius, double* C);
+
 /* Number of kernels this context has launched since lcp_setup. */
 LCP_API int lcp_launch_count(const lcp_ctx* ctx, unsigned long long* count);
 
@@ -352,7 +370,8 @@ LCP_API int lcp_rigid_velocity_dev(lcp_ctx* ctx, const double* phi, double* UO);
  * code running inside an allocator or memory-pool callback, hosts that give
  * the whole device budget to another component, or real-time loops where an
  * allocation could block or fail.  The paper has no counterpart; it is the
- * same operator as lcp_stokes_apply_dev.
+ * same operator as lcp_stokes_apply_dev with self_quadrature = 0 (the product
+ * rule for the self-interaction).
  *   centers [M*3], phi [N*3] and out [N*3] are device pointers (FP64), N =
  *   n_bodies * n_theta * n_phi; precision LCP_FP64 or LCP_MIXED; cuda_stream
  *   is a cudaStream_t (NULL = legacy default stream).  Returns after the

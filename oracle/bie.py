@@ -24,11 +24,16 @@ zero outside the body and the identity inside):
     T(r, n) v = -(3 / (4 pi)) r (r . n)(r . v) / |r|^5.
 
 Everything here is dense FP64 and solved by LU (SciPy/LAPACK).
+
+Optionally (``self_quadrature``) each body's self-interaction is taken by a
+high-order rule instead of the product rule: ``self_correction`` below.
 """
+import functools
+
 import numpy as np
 import scipy.linalg as sla
 
-from .quadrature import surface_nodes
+from .quadrature import sphere_template, surface_nodes
 
 
 def stresslet_matrix(x: np.ndarray, n: np.ndarray, w: np.ndarray) -> np.ndarray:
@@ -111,14 +116,88 @@ def janus_slip(n: np.ndarray, body: np.ndarray, axes: np.ndarray) -> np.ndarray:
     return s
 
 
+def _real_harmonics(u: np.ndarray, L: int) -> np.ndarray:
+    """Orthonormal real spherical harmonics of degree <= L at unit vectors u: [len(u), (L+1)^2]."""
+    from scipy.special import sph_harm_y
+    th = np.arccos(np.clip(u[:, 2], -1.0, 1.0))
+    ph = np.arctan2(u[:, 1], u[:, 0])
+    cols = []
+    for l in range(L + 1):
+        for m in range(-l, l + 1):
+            y = sph_harm_y(l, abs(m), th, ph)
+            if m < 0:
+                cols.append(np.sqrt(2.0) * y.imag)
+            elif m == 0:
+                cols.append(y.real)
+            else:
+                cols.append(np.sqrt(2.0) * y.real)
+    return np.stack(cols, axis=1)
+
+
+def self_correction(n_theta: int, n_phi: int, a: float = 1.0, n_polar=None, n_azim=None) -> np.ndarray:
+    """Cached wrapper of _self_correction (a fresh copy per call)."""
+    return _self_correction(int(n_theta), int(n_phi), float(a), n_polar, n_azim).copy()
+
+
+@functools.lru_cache(maxsize=8)
+def _self_correction(n_theta: int, n_phi: int, a: float = 1.0, n_polar=None, n_azim=None) -> np.ndarray:
+    """Accurate minus product-rule self-interaction block of one sphere template [3ns, 3ns].
+
+    The exact self part of (K phi)_p is the integral over the sphere of
+    T(x_p - y, n(y)) (phi(y) - phi_p).  Around each node p it is taken on a polar
+    grid with its pole at x_p: Gauss-Legendre in the polar angle on (0, pi) and the
+    uniform rule in the azimuth.  On a sphere (x - y).n(y) = -|x - y|^2/(2a), so the
+    kernel is O(1/|x - y|) and the area element a^2 sin(theta) removes the
+    singularity.  phi(y) is the projection of the nodal values on the real spherical
+    harmonics of degree <= n_theta - 1 (coefficients by the template's own
+    quadrature).  The product-rule block is the one stresslet_matrix takes for a
+    single sphere.  (A refinement of the stand-in operator above, not the paper's.)
+    """
+    xi, nrm, w = sphere_template(n_theta, n_phi, a)
+    ns = xi.shape[0]
+    L = n_theta - 1
+    n_polar = n_polar or 3 * n_theta
+    n_azim = n_azim or 6 * n_theta
+    coef_of = (_real_harmonics(nrm, L) * (w / a ** 2)[:, None]).T          # nodal values -> coefficients
+    tg, wg = np.polynomial.legendre.leggauss(n_polar)
+    th = 0.5 * np.pi * (tg + 1.0)
+    wth = 0.5 * np.pi * wg
+    ph = 2.0 * np.pi * np.arange(n_azim) / n_azim
+    c = -3.0 / (4.0 * np.pi)
+    S = np.zeros((3 * ns, 3 * ns))
+    for p in range(ns):
+        e = nrm[p]
+        helper = np.array([1.0, 0.0, 0.0]) if abs(e[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+        t1 = np.cross(e, helper)
+        t1 /= np.linalg.norm(t1)
+        t2 = np.cross(e, t1)
+        u = (np.cos(th)[:, None, None] * e
+             + np.sin(th)[:, None, None] * (np.cos(ph)[None, :, None] * t1 + np.sin(ph)[None, :, None] * t2))
+        u = u.reshape(-1, 3)
+        W = (a * a * (np.sin(th) * wth)[:, None] * (2.0 * np.pi / n_azim) * np.ones(n_azim)[None, :]).reshape(-1)
+        r = xi[p] - a * u
+        r2 = np.einsum("ij,ij->i", r, r)
+        rn = np.einsum("ij,ij->i", r, u)
+        blocks = (c * W * rn / r2 ** 2.5)[:, None, None] * r[:, :, None] * r[:, None, :]
+        interp = _real_harmonics(u, L) @ coef_of                            # [points, ns]
+        S[3 * p:3 * p + 3, :] = np.einsum("kab,kq->aqb", blocks, interp).reshape(3, 3 * ns)
+        S[3 * p:3 * p + 3, 3 * p:3 * p + 3] -= blocks.sum(axis=0)
+    return S - stresslet_matrix(xi, nrm, w)
+
+
 class DenseMobility:
     """Dense LU of (K + P) for one configuration; applies the mobility M."""
 
-    def __init__(self, centers, n_theta, n_phi, a=1.0, mu=1.0):
+    def __init__(self, centers, n_theta, n_phi, a=1.0, mu=1.0, self_quadrature=False):
         self.centers = np.asarray(centers, dtype=np.float64)
         self.a, self.mu = a, mu
         self.x, self.n, self.w, self.body = surface_nodes(self.centers, n_theta, n_phi, a)
         self.K = stresslet_matrix(self.x, self.n, self.w)
+        if self_quadrature:   # the accurate self-interaction on every body
+            C = self_correction(n_theta, n_phi, a)
+            b = C.shape[0]
+            for i in range(self.centers.shape[0]):
+                self.K[i * b:(i + 1) * b, i * b:(i + 1) * b] += C
         self.P, self.parts = rigid_projector(self.centers, self.x, self.w, self.body)
         self.lu = sla.lu_factor(self.K + self.P)
 

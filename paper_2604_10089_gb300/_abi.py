@@ -38,7 +38,7 @@ class lcp_config(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("lowfi_n_theta", ctypes.c_int),
                 ("lowfi_n_phi", ctypes.c_int), ("lowfi_tol", ctypes.c_double),
                 ("init_forcing", ctypes.c_double), ("warm_start", ctypes.c_int),
-                ("recycle", ctypes.c_int)]
+                ("recycle", ctypes.c_int), ("self_quadrature", ctypes.c_int)]
 
 
 class lcp_contact(ctypes.Structure):
@@ -77,6 +77,7 @@ PROTOTYPES = {
     "lcp_step": (_I, [_P, ctypes.c_double, _D, _D]),
     "lcp_profile": (_I, [_P, _I]),
     "lcp_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "lcp_self_correction": (_I, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P]),
     "lcp_solve_counters": (_I, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "lcp_profile_read": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),

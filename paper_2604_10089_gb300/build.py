@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblcp_gb300.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["geometry.cu", "stokes.cu", "stokes_sym.cu", "stokes_sym_df.cu", "krylov.cu", "pqn.cu", "lcp_api.cu", "noalloc.cu", "precond.cu", "serve.cu"]
+SOURCES = ["geometry.cu", "stokes.cu", "stokes_sym.cu", "stokes_sym_df.cu", "krylov.cu", "pqn.cu", "lcp_api.cu", "noalloc.cu", "precond.cu", "serve.cu", "selfquad.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE]

@@ -143,6 +143,8 @@ struct lcp_ctx {
   double *V = nullptr, *H = nullptr;  // Krylov basis [(m+1)][3N], Hessenberg etc.
   double* Z = nullptr;                 // preconditioned basis [m][3N] (flexible GMRES)
   float* pinv = nullptr;               // isolated-sphere inverse (3 ns x 3 ns, FP32)
+  float* cself32 = nullptr;            // self-interaction correction (3 ns x 3 ns, FP32, row-major)
+  double* cself64t = nullptr;          // the same in FP64, transposed
   float* ppart = nullptr;              // split-k partial products of the preconditioner GEMM
   double *phi = nullptr, *rhs = nullptr, *res = nullptr, *wv = nullptr, *dphi = nullptr;
   float* phi32 = nullptr;
@@ -273,6 +275,10 @@ int mobility_solve(lcp_ctx* ctx, const double* FT, int include_slip, double* UO,
 void recycle_reset(lcp_ctx* ctx);   // forget the kept solve pairs (this context and its coarse grid)
 int precond_build(lcp_ctx* ctx);
 int precond_apply(lcp_ctx* ctx, const double* v, double* z);
+int block_apply_reserve(lcp_ctx* ctx);
+int block_apply32(lcp_ctx* ctx, const float* mat, const double* v, double* z, bool accumulate);
+int self_correction_build(lcp_ctx* ctx);
+int self_correction_apply(lcp_ctx* ctx, const double* phi, double* out, int precision);
 int scatter_D(lcp_ctx* ctx, const double* x, double* FT);
 int gather_Dt(lcp_ctx* ctx, const double* UO, double* out, const double* add);
 int rpy_apply(lcp_ctx* ctx, const double* FT, double* UO);

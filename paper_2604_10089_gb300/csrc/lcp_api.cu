@@ -63,6 +63,7 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->h0_scaling = 1;
   c->warm_start = LCP_WARM_FORCES;
   c->recycle = 0;
+  c->self_quadrature = 0;
   c->cuda_stream = nullptr;
 }
 
@@ -85,6 +86,7 @@ static int validate(const lcp_config* c, int M, const double* centers, std::stri
     return LCP_ERR_INVALID_ARG;
   }
   if (c->warm_start < 0 || c->warm_start > (LCP_WARM_SLIP | LCP_WARM_FORCES | LCP_WARM_NO_INIT)) { *err = "warm_start: a combination of the LCP_WARM_* flags"; return LCP_ERR_INVALID_ARG; }
+  if (c->self_quadrature != 0 && c->self_quadrature != 1) { *err = "self_quadrature must be 0 or 1"; return LCP_ERR_INVALID_ARG; }
   if (c->recycle < 0 || c->recycle > c->gmres_restart) { *err = "recycle in [0, gmres_restart]"; return LCP_ERR_INVALID_ARG; }
   if (!(c->init_forcing >= 0.0) || c->init_forcing >= 1.0) { *err = "init_forcing in [0, 1)"; return LCP_ERR_INVALID_ARG; }
   // the direction kernel keeps its r x r systems in shared memory (<= 227 KB: r <= 48)
@@ -180,6 +182,10 @@ static int alloc_static(lcp_ctx* ctx) {
       !ctx->partial || !ctx->coef || !ctx->dotp || !ctx->FT || !ctx->UO || !ctx->U_nc || !ctx->phi_unc || !ctx->phidf) {
     ctx->err = "device allocation failed";
     return LCP_ERR_OOM;
+  }
+  if (ctx->cfg.self_quadrature) {   // before the preconditioner, which includes it
+    LCP_TRY(self_correction_build(ctx));
+    LCP_TRY(block_apply_reserve(ctx));
   }
   LCP_TRY(pqn_configure(ctx, ctx->cfg.memory));
   if (ctx->cfg.precondition) LCP_TRY(precond_build(ctx));
@@ -411,6 +417,8 @@ extern "C" int lcp_footprint_estimate(const lcp_config* cfg, int n_bodies, int n
   b += sizeof(double) * ((m + 1) * m + 6 * m + 16 + (m + 2) * 304);                          // Hessenberg, dots
   b += sizeof(double) * (8 * ns + 36) + sizeof(float) * 6 * ns + sizeof(double) * 30 * M + sizeof(float) * 8 * M;
   b += (sizeof(int) * 2 + sizeof(double) * 4) * pairs + sizeof(int) * M * (M + 2);           // contact buffers
+  if (cfg->self_quadrature)                                                                  // self correction
+    b += (sizeof(float) + sizeof(double)) * 9 * ns * ns + (cfg->precondition ? 0 : sizeof(float) * 4 * L);
   if (cfg->precondition)                                                                     // preconditioner
     b += sizeof(double) * 9 * ns * ns * 3 + sizeof(float) * 9 * ns * ns + sizeof(float) * 4 * L;
   b += sizeof(double) * n * (6 + 2 * K) + sizeof(int) * (2 * n + 1);                         // arena

@@ -175,13 +175,22 @@ __global__ void __launch_bounds__(256) k_precond(int n, int M, int kc, const flo
     }
 }
 
-__global__ void k_precond_sum(int L, const float* __restrict__ part, double* __restrict__ z) {
+// z = the sum of the splits (or z += it)
+__global__ void k_precond_sum(int L, const float* __restrict__ part, double* __restrict__ z, int accumulate) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L) return;
   double s = 0.0;
 #pragma unroll
   for (int k = 0; k < PT_KS; k++) s += (double)part[(size_t)k * L + i];
-  z[i] = s;
+  z[i] = accumulate ? z[i] + s : s;
+}
+
+// A += Bt^T (n x n, row-major)
+__global__ void k_add_transposed(int n, const double* __restrict__ Bt, double* __restrict__ A) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  A[t] += Bt[(size_t)j * n + i];
 }
 
 int precond_build(lcp_ctx* ctx) {
@@ -189,13 +198,16 @@ int precond_build(lcp_ctx* ctx) {
   double* aug = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)n * 2 * n);
   double* colk = (double*)ctx_alloc(ctx, sizeof(double) * n);
   ctx->pinv = (float*)ctx_alloc(ctx, sizeof(float) * (size_t)n * n);
-  ctx->ppart = (float*)ctx_alloc(ctx, sizeof(float) * PT_KS * (size_t)n * ctx->M);
-  if (!aug || !colk || !ctx->pinv || !ctx->ppart) return LCP_ERR_OOM;
+  LCP_TRY(block_apply_reserve(ctx));
+  if (!aug || !colk || !ctx->pinv) return LCP_ERR_OOM;
   // assemble K_iso + P_iso (n x n), then copy it into the left half of [A | I]
   double* tmp = (double*)ctx_alloc(ctx, sizeof(double) * (size_t)n * n);
   if (!tmp) return LCP_ERR_OOM;
   ++ctx->nlaunch, k_iso_matrix<<<(ns * ns + 127) / 128, 128, 0, ctx->stream>>>(ns, ctx->tmpl64, ctx->ginv, tmp);
   ++ctx->nlaunch, k_iso_diag<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(ns, ctx->tmpl64, tmp);
+  if (ctx->cself64t)   // the corrected self-interaction is part of the isolated sphere's operator
+    ++ctx->nlaunch, k_add_transposed<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, ctx->stream>>>(
+                        n, ctx->cself64t, tmp);
   LCP_CUDA(cudaMemsetAsync(aug, 0, sizeof(double) * (size_t)n * 2 * n, ctx->stream));
   LCP_CUDA(cudaMemcpy2DAsync(aug, sizeof(double) * 2 * n, tmp, sizeof(double) * n, sizeof(double) * n, n,
                              cudaMemcpyDeviceToDevice, ctx->stream));
@@ -211,13 +223,25 @@ int precond_build(lcp_ctx* ctx) {
   return LCP_OK;
 }
 
-int precond_apply(lcp_ctx* ctx, const double* v, double* z) {
+// The split-k partial products of the per-body block GEMMs (once per context).
+int block_apply_reserve(lcp_ctx* ctx) {
+  if (ctx->ppart) return LCP_OK;
+  ctx->ppart = (float*)ctx_alloc(ctx, sizeof(float) * PT_KS * (size_t)3 * ctx->ns * ctx->M);
+  return ctx->ppart ? LCP_OK : LCP_ERR_OOM;
+}
+
+// z_b = mat v_b (or z_b += mat v_b) for every body b; mat is 3 ns x 3 ns, FP32, row-major.
+int block_apply32(lcp_ctx* ctx, const float* mat, const double* v, double* z, bool accumulate) {
   const int n = 3 * ctx->ns;
   const int kc = ((n + PT_K - 1) / PT_K + PT_KS - 1) / PT_KS * PT_K;
   dim3 grid((n + PT_R - 1) / PT_R, (ctx->M + PT_C - 1) / PT_C, PT_KS);
-  ++ctx->nlaunch, k_precond<<<grid, 256, 0, ctx->stream>>>(n, ctx->M, kc, ctx->pinv, v, ctx->ppart);
+  ++ctx->nlaunch, k_precond<<<grid, 256, 0, ctx->stream>>>(n, ctx->M, kc, mat, v, ctx->ppart);
   const int L = n * ctx->M;
-  ++ctx->nlaunch, k_precond_sum<<<(L + 255) / 256, 256, 0, ctx->stream>>>(L, ctx->ppart, z);
+  ++ctx->nlaunch, k_precond_sum<<<(L + 255) / 256, 256, 0, ctx->stream>>>(L, ctx->ppart, z, accumulate ? 1 : 0);
   LCP_CUDA(cudaGetLastError());
   return LCP_OK;
+}
+
+int precond_apply(lcp_ctx* ctx, const double* v, double* z) {
+  return block_apply32(ctx, ctx->pinv, v, z, false);
 }

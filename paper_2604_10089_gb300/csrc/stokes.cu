@@ -682,7 +682,17 @@ int stokes_coefs(lcp_ctx* ctx, const double* phi, double* coef) {
   return LCP_OK;
 }
 
+static int stokes_apply_sums(lcp_ctx* ctx, const double* phi, double* out, int precision);
+
+// (K + P) phi with the pair sums of `precision`, plus the self-interaction
+// correction of every body when cfg.self_quadrature is on.
 int stokes_apply(lcp_ctx* ctx, const double* phi, double* out, int precision) {
+  LCP_TRY(stokes_apply_sums(ctx, phi, out, precision));
+  if (ctx->cself32) LCP_TRY(self_correction_apply(ctx, phi, out, precision));
+  return LCP_OK;
+}
+
+static int stokes_apply_sums(lcp_ctx* ctx, const double* phi, double* out, int precision) {
   const int N = ctx->N, ns = ctx->ns, M = ctx->M;
   const int tpb = pair_targets(precision, ctx->v32);
   const int ntb = (N + tpb - 1) / tpb;

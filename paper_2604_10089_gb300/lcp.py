@@ -123,6 +123,14 @@ def lcp_launch_count(ctx) -> int:
     return c.value
 
 
+def lcp_self_correction(n_theta: int, n_phi: int, radius: float = 1.0) -> np.ndarray:
+    """The 3 ns x 3 ns self-interaction correction of one sphere template (host computation)."""
+    n = 3 * n_theta * n_phi
+    C = np.empty((n, n))
+    _check(_lib().lcp_self_correction(int(n_theta), int(n_phi), float(radius), _dptr(C)))
+    return C
+
+
 def lcp_solve_counters(ctx, fidelity: int = 0):
     """(mobility solves, their GMRES iterations, projected starts) of one grid since set-up."""
     a, b, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
