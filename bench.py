@@ -78,7 +78,7 @@ def parse():
                    help="batched/serving modes: use --lowfi only for instances with at least this many spheres")
     p.add_argument("--warm-start", type=int, default=None,
                    help="trajectory warm starts (1 slip solve, 2 LCP forces, 3 both); default: the library's")
-    p.add_argument("--self-quadrature", type=int, default=0,
+    p.add_argument("--self-quadrature", type=int, default=1,
                    help="1: high-order self-interaction quadrature (one 3ns x 3ns correction per body)")
     p.add_argument("--inner-tol", type=float, default=1e-6,
                    help="relative tolerance of each FP32-operator refinement sweep (mixed precision)")
@@ -657,7 +657,8 @@ def oracle_mobility_solves(workload: str, index: int, lowfi: dict, coarse_solves
     inst = make_instance(workload, index)
     out = {"cores": len(os.sched_getaffinity(0))}
     if fine:
-        mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, tol=1e-12)
+        mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, tol=1e-12,
+                                self_quadrature=True)
         t0 = time.perf_counter()
         mf.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes)
         out["fine_seconds"] = time.perf_counter() - t0
@@ -666,7 +667,7 @@ def oracle_mobility_solves(workload: str, index: int, lowfi: dict, coarse_solves
     times, iters = [], []
     if lowfi:
         mc = MatrixFreeMobility(inst.centers, lowfi["lowfi_n_theta"], lowfi["lowfi_n_phi"], a=inst.radius,
-                                tol=lowfi.get("lowfi_tol", 1e-6))
+                                tol=lowfi.get("lowfi_tol", 1e-6), self_quadrature=True)
     for _ in range(coarse_solves):
         FT = rng.standard_normal(6 * inst.n_bodies)
         t0 = time.perf_counter()
@@ -689,15 +690,19 @@ def oracle_lcp_rate(fine_s: float, coarse_s: float, hi: float, lo: float) -> flo
 
 def c1_oracle_solve(index: int = 1) -> dict:
     """One complete oracle collision resolution at 8 spheres (7 x 14 nodes): dense K + P by
-    LU, dense M and A = D^T M D, the slip solve for b, and the LCP by projected Gauss-Seidel."""
-    from oracle.bie import DenseMobility
+    LU, dense M and A = D^T M D, the slip solve for b, and the LCP by projected Gauss-Seidel.
+    The self-interaction correction of the grid is built before the clock starts (like the
+    library, which builds it once per grid and process)."""
+    from oracle.bie import DenseMobility, self_correction
     from oracle.contacts import contact_matrix, detect_contacts
     from oracle.lcp import kkt_abs, lcp_data, pgs
     from workloads import make_instance
 
     inst = make_instance("spheres8_grid7x14", index)
+    self_correction(inst.n_theta, inst.n_phi, inst.radius)
     t0 = time.perf_counter()
-    mob = DenseMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, mu=inst.viscosity)
+    mob = DenseMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, mu=inst.viscosity,
+                        self_quadrature=True)
     pairs, normals, gaps = detect_contacts(inst.centers, inst.contact_radius, inst.delta)
     D = contact_matrix(inst.n_bodies, pairs, normals)
     A, b = lcp_data(D, mob.matrix(), mob.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes), gaps, inst.dt)

@@ -132,7 +132,7 @@ typedef struct {
    * polar quadrature about each node and the band-limited projection of the
    * density, and applied per body as a small GEMM in the sums' precision.  It
    * makes the two-sphere mobilities converge spectrally (the isolated-sphere
-   * preconditioner includes it).  0 (default): the product rule only. */
+   * preconditioner includes it).  1 (default); 0: the product rule only. */
   int self_quadrature;
 } lcp_config;
 

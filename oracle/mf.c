@@ -71,9 +71,10 @@ void mf_rigid_coeffs(int M, int ns, const double* x, const double* w, const doub
   }
 }
 
-/* out = (K + P) phi for N = M * ns nodes. */
+/* out = (K + P) phi for N = M * ns nodes; with Cself (3 ns x 3 ns, row-major, or
+ * NULL) also out_b += Cself phi_b on every body b (the accurate self-interaction). */
 void mf_apply(int M, int ns, const double* x, const double* nrm, const double* w,
-              const double* centers, const double* phi, double* out) {
+              const double* centers, const double* Cself, const double* phi, double* out) {
   int N = M * ns;
   const double c = -3.0 / (4.0 * PI);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -109,6 +110,16 @@ void mf_apply(int M, int ns, const double* x, const double* nrm, const double* w
     }
   }
   free(coeff);
+  if (Cself) {
+    int nb = 3 * ns;
+#pragma omp parallel for
+    for (int i = 0; i < M; i++)
+      for (int r = 0; r < nb; r++) {
+        double s = 0.0;
+        for (int c2 = 0; c2 < nb; c2++) s += Cself[(size_t)r * nb + c2] * phi[(size_t)i * nb + c2];
+        out[(size_t)i * nb + r] += s;
+      }
+  }
 }
 
 /* rhs = -S[F, T] at the nodes (Stokeslet and rotlet of every body). */
@@ -137,7 +148,8 @@ void mf_stokeslet_rhs(int M, int ns, const double* x, const double* centers, con
  * Stops when ||rhs - (K+P) phi|| <= tol ||rhs||; returns the iteration count
  * (negative if maxit was reached). */
 int mf_gmres(int M, int ns, const double* x, const double* nrm, const double* w,
-             const double* centers, const double* rhs, double* phi, double tol, int m, int maxit) {
+             const double* centers, const double* Cself, const double* rhs, double* phi, double tol, int m,
+             int maxit) {
   int n = 3 * M * ns;
   double* V = (double*)malloc(sizeof(double) * (size_t)n * (m + 1));
   double* H = (double*)calloc((size_t)(m + 1) * m, sizeof(double));
@@ -153,7 +165,7 @@ int mf_gmres(int M, int ns, const double* x, const double* nrm, const double* w,
   int total = 0;
   if (bnorm == 0.0) goto done;
   for (;;) {
-    mf_apply(M, ns, x, nrm, w, centers, phi, wv);
+    mf_apply(M, ns, x, nrm, w, centers, Cself, phi, wv);
     double beta = 0;
     for (int i = 0; i < n; i++) { wv[i] = rhs[i] - wv[i]; beta += wv[i] * wv[i]; }
     beta = sqrt(beta);
@@ -163,7 +175,7 @@ int mf_gmres(int M, int ns, const double* x, const double* nrm, const double* w,
     g[0] = beta;
     int j;
     for (j = 0; j < m; j++) {
-      mf_apply(M, ns, x, nrm, w, centers, V + (size_t)j * n, wv);
+      mf_apply(M, ns, x, nrm, w, centers, Cself, V + (size_t)j * n, wv);
       total++;
       for (int k = 0; k <= j; k++) {
         double h = 0;

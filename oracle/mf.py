@@ -5,7 +5,7 @@ import subprocess
 
 import numpy as np
 
-from .bie import janus_slip
+from .bie import janus_slip, self_correction
 from .quadrature import surface_nodes
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -28,10 +28,10 @@ def _load():
         _lib = ctypes.CDLL(_SO)
         D = ctypes.POINTER(ctypes.c_double)
         i = ctypes.c_int
-        _lib.mf_apply.argtypes = [i, i, D, D, D, D, D, D]
+        _lib.mf_apply.argtypes = [i, i, D, D, D, D, D, D, D]
         _lib.mf_rigid_coeffs.argtypes = [i, i, D, D, D, D, D]
         _lib.mf_stokeslet_rhs.argtypes = [i, i, D, D, D, ctypes.c_double, D]
-        _lib.mf_gmres.argtypes = [i, i, D, D, D, D, D, D, ctypes.c_double, i, i]
+        _lib.mf_gmres.argtypes = [i, i, D, D, D, D, D, D, D, ctypes.c_double, i, i]
         _lib.mf_gmres.restype = i
     return _lib
 
@@ -41,9 +41,11 @@ def _p(a):
 
 
 class MatrixFreeMobility:
-    """Mobility of one configuration by matrix-free GMRES (same operator as DenseMobility)."""
+    """Mobility of one configuration by matrix-free GMRES (same operator as DenseMobility,
+    including its optional accurate self-interaction)."""
 
-    def __init__(self, centers, n_theta, n_phi, a=1.0, mu=1.0, tol=1e-12, restart=60, maxit=500):
+    def __init__(self, centers, n_theta, n_phi, a=1.0, mu=1.0, tol=1e-12, restart=60, maxit=500,
+                 self_quadrature=False):
         self.lib = _load()
         self.centers = np.ascontiguousarray(centers, dtype=np.float64)
         self.M = self.centers.shape[0]
@@ -55,11 +57,15 @@ class MatrixFreeMobility:
         self.w = np.ascontiguousarray(w)
         self.body = body
         self.last_iterations = 0
+        self.cself = np.ascontiguousarray(self_correction(n_theta, n_phi, a)) if self_quadrature else None
+
+    def _c(self):
+        return _p(self.cself) if self.cself is not None else None
 
     def apply_operator(self, phi):
         out = np.empty(3 * self.M * self.ns)
         phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
-        self.lib.mf_apply(self.M, self.ns, _p(self.x), _p(self.n), _p(self.w), _p(self.centers),
+        self.lib.mf_apply(self.M, self.ns, _p(self.x), _p(self.n), _p(self.w), _p(self.centers), self._c(),
                           _p(phi), _p(out))
         return out
 
@@ -74,7 +80,7 @@ class MatrixFreeMobility:
     def solve_density(self, rhs):
         phi = np.empty(3 * self.M * self.ns)
         rhs = np.ascontiguousarray(rhs, dtype=np.float64).reshape(-1)
-        it = self.lib.mf_gmres(self.M, self.ns, _p(self.x), _p(self.n), _p(self.w), _p(self.centers),
+        it = self.lib.mf_gmres(self.M, self.ns, _p(self.x), _p(self.n), _p(self.w), _p(self.centers), self._c(),
                                _p(rhs), _p(phi), self.tol, self.restart, self.maxit)
         self.last_iterations = it
         if it < 0:

@@ -63,7 +63,7 @@ extern "C" void lcp_default_config(lcp_config* c) {
   c->h0_scaling = 1;
   c->warm_start = LCP_WARM_FORCES;
   c->recycle = 0;
-  c->self_quadrature = 0;
+  c->self_quadrature = 1;
   c->cuda_stream = nullptr;
 }
 

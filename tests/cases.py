@@ -12,11 +12,17 @@ from oracle.rpy import rpy_matrix
 from workloads import make_instance
 
 
+# The library's default operator takes each sphere's self-interaction with the high-order rule
+# (cfg.self_quadrature = 1): oracles compared with default contexts do the same.
+SELF_QUADRATURE = True
+
+
 @functools.lru_cache(maxsize=8)
 def dense_case(name: str, index: int):
     """Instance plus its dense oracle: mobility, D, U_nc, A, b, A_hat, LCP solution."""
     inst = make_instance(name, index)
-    mob = DenseMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, mu=inst.viscosity)
+    mob = DenseMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, mu=inst.viscosity,
+                        self_quadrature=SELF_QUADRATURE)
     pairs, normals, gaps = detect_contacts(inst.centers, inst.contact_radius, inst.delta)
     D = contact_matrix(inst.n_bodies, pairs, normals)
     U_nc = mob.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes)

@@ -17,12 +17,13 @@ from oracle.lcp import kkt_abs  # noqa: E402
 from oracle.mf import MatrixFreeMobility  # noqa: E402
 from workloads import batched_instances  # noqa: E402
 
-from .cases import MISMATCH_REL, kkt_bound  # noqa: E402
+from .cases import MISMATCH_REL, SELF_QUADRATURE, kkt_bound  # noqa: E402
 
 
 def check_against_oracle(inst, x, g_gpu, hi_mvps):
     """KKT error of x with the matrix-free FP64 oracle's MVP and b: <= tol + eps_op."""
-    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, mu=inst.viscosity)
+    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, mu=inst.viscosity,
+                            self_quadrature=SELF_QUADRATURE)
     pairs, normals, gaps = detect_contacts(inst.centers, inst.contact_radius, inst.delta)
     D = contact_matrix(inst.n_bodies, pairs, normals)
     b = gaps / inst.dt + D.T @ mf.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes)

@@ -17,7 +17,7 @@ from oracle.lcp import kkt_abs  # noqa: E402
 from oracle.mf import MatrixFreeMobility  # noqa: E402
 from workloads import make_instance  # noqa: E402
 
-from .cases import MISMATCH_REL, kkt_bound  # noqa: E402
+from .cases import MISMATCH_REL, SELF_QUADRATURE, kkt_bound  # noqa: E402
 
 
 def rel(a, b):
@@ -27,7 +27,7 @@ def rel(a, b):
 @pytest.fixture(scope="module")
 def big():
     inst = make_instance("spheres216_grid11x22", 0)
-    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius)
+    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, self_quadrature=SELF_QUADRATURE)
     ctx = L.lcp_setup(L.config_for(inst, L.LCP_MIXED), inst.centers, inst.axes)
     yield inst, mf, ctx
     L.lcp_destroy(ctx)
@@ -69,7 +69,7 @@ def test_c2_solves_against_the_oracle(method, precision):
     """64 spheres (the Mono vs Bi, FP64 vs mixed comparison): each solution's KKT error with
     the matrix-free oracle's MVP and b stays within tol + eps_op."""
     inst = make_instance("spheres64_grid9x18", 0)
-    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius)
+    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, self_quadrature=SELF_QUADRATURE)
     pairs, normals, gaps = detect_contacts(inst.centers, inst.contact_radius, inst.delta)
     D = contact_matrix(inst.n_bodies, pairs, normals)
     b_or = gaps / inst.dt + D.T @ mf.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes)

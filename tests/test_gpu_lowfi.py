@@ -22,7 +22,7 @@ from oracle.lcp import kkt_abs  # noqa: E402
 from oracle.mf import MatrixFreeMobility  # noqa: E402
 from workloads import make_instance  # noqa: E402
 
-from .cases import MISMATCH_REL, active_set, dense_case, kkt_bound  # noqa: E402
+from .cases import MISMATCH_REL, SELF_QUADRATURE, active_set, dense_case, kkt_bound  # noqa: E402
 
 
 def rel(a, b):
@@ -33,7 +33,7 @@ def rel(a, b):
 def test_lowfi_mvp_matches_coarse_grid_oracle(grid):
     case = dense_case("spheres8_grid7x14", 1)
     inst = case["inst"]
-    coarse = DenseMobility(inst.centers, grid[0], grid[1], a=inst.radius, mu=inst.viscosity)
+    coarse = DenseMobility(inst.centers, grid[0], grid[1], a=inst.radius, mu=inst.viscosity, self_quadrature=SELF_QUADRATURE)
     A_lo = case["D"].T @ coarse.matrix() @ case["D"]
     cfg = L.config_for(inst, L.LCP_MIXED, lowfi_n_theta=grid[0], lowfi_n_phi=grid[1], lowfi_tol=1e-6)
     ctx = L.lcp_setup(cfg, inst.centers, inst.axes)
@@ -75,7 +75,7 @@ def test_bi_pqn_with_coarse_grid_low_fidelity(index, init_forcing):
 def test_bi_pqn_coarse_low_fidelity_64_spheres():
     """Fewer high-fidelity MVPs than with RPY, same solution (oracle MVP at the result)."""
     inst = make_instance("spheres64_grid9x18", 0)
-    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius)
+    mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, self_quadrature=SELF_QUADRATURE)
     pairs, normals, gaps = detect_contacts(inst.centers, inst.contact_radius, inst.delta)
     D = contact_matrix(inst.n_bodies, pairs, normals)
     res = {}

@@ -24,7 +24,7 @@ from oracle.mf import MatrixFreeMobility  # noqa: E402
 from oracle.rpy import rpy_matrix  # noqa: E402
 from workloads import make_instance  # noqa: E402
 
-from .cases import MISMATCH_REL, active_set, dense_case, kkt_bound, rhs_oracle  # noqa: E402
+from .cases import MISMATCH_REL, SELF_QUADRATURE, active_set, dense_case, kkt_bound, rhs_oracle  # noqa: E402
 
 DEV = "cuda"
 
@@ -72,7 +72,7 @@ def test_stresslet_apply_many_tiles(name, index, precision, tol):
     inst = make_instance(name, index)
     ctx = L.lcp_setup(L.config_for(inst), inst.centers, None)
     try:
-        mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius)
+        mf = MatrixFreeMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius, self_quadrature=SELF_QUADRATURE)
         phi = np.random.default_rng(5).standard_normal(mf.x.shape[0] * 3)
         ref = mf.apply_operator(phi)
         dphi = torch.tensor(phi, device=DEV)
@@ -283,7 +283,7 @@ def test_time_step_matches_oracle(method):
         # the context now holds the next LCP
         from oracle.contacts import contact_matrix, detect_contacts
         from oracle.lcp import lcp_data
-        mob = DenseMobility(c_ref, inst.n_theta, inst.n_phi, a=inst.radius)
+        mob = DenseMobility(c_ref, inst.n_theta, inst.n_phi, a=inst.radius, self_quadrature=SELF_QUADRATURE)
         pairs, normals, gaps = detect_contacts(c_ref, inst.contact_radius, inst.delta)
         D = contact_matrix(inst.n_bodies, pairs, normals)
         _, b_next = lcp_data(D, np.eye(6 * inst.n_bodies), mob.apply(np.zeros(6 * inst.n_bodies), axes=a_ref),

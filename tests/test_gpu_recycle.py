@@ -17,7 +17,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import paper_2604_10089_gb300 as L  # noqa: E402
 from oracle.bie import DenseMobility  # noqa: E402
 
-from .cases import dense_case, kkt_bound  # noqa: E402
+from .cases import SELF_QUADRATURE, dense_case, kkt_bound  # noqa: E402
 
 
 def rel(a, b):
@@ -73,7 +73,7 @@ def test_projected_start_on_the_low_fidelity_grid():
     case = dense_case("spheres8_grid7x14", 0)
     inst = case["inst"]
     lo = dict(lowfi_n_theta=5, lowfi_n_phi=10, lowfi_tol=1e-6)
-    Mlo = DenseMobility(inst.centers, 5, 10, a=inst.radius, mu=inst.viscosity).matrix()
+    Mlo = DenseMobility(inst.centers, 5, 10, a=inst.radius, mu=inst.viscosity, self_quadrature=SELF_QUADRATURE).matrix()
     seq = force_sequence(inst.n_bodies, seed=11)
     on = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, recycle=4, **lo), inst.centers, inst.axes)
     off = L.lcp_setup(L.config_for(inst, L.LCP_MIXED, recycle=0, **lo), inst.centers, inst.axes)

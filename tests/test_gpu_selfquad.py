@@ -1,7 +1,8 @@
-"""High-order self-interaction quadrature (cfg.self_quadrature) on the GPU.
+"""High-order self-interaction quadrature (cfg.self_quadrature, the default) on the GPU.
 
 The library adds one 3 ns x 3 ns correction per body to the pair sums (FP32 in FP32
-applies, FP64 in FP64 and double-FP32 applies).  Checked against the oracle's operator
+applies, FP64 in FP64 and double-FP32 applies).  The plain product rule stays available
+(self_quadrature = 0) and is checked against the plain oracle.  Checked against the oracle's operator
 with its independently built correction, against exact two-sphere Stokes flow, and
 through complete LCP solves against the corrected oracle's A and b.
 """
@@ -118,5 +119,30 @@ def test_coarse_low_fidelity_grid_gets_its_own_correction():
         FT = np.random.default_rng(7).standard_normal(6 * inst.n_bodies)
         U = L.mobility_apply(ctx, FT, fidelity=L.LCP_LOW_BIE)
         assert rel(U, coarse.apply(FT)) <= 1e-5
+    finally:
+        L.lcp_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision,tol", [(L.LCP_FP64, 1e-12), (L.LCP_MIXED, 1e-5), (L.LCP_DF64, 1e-12)])
+def test_plain_product_rule_operator_matches_the_plain_oracle(precision, tol):
+    """self_quadrature = 0 (the product rule for the self-interaction, also the operator of
+    the allocation-free entry) against the oracle without the correction, and one LCP solve."""
+    inst = make_instance("spheres8_grid7x14", 1)
+    mob = DenseMobility(inst.centers, inst.n_theta, inst.n_phi, a=inst.radius)
+    ctx = L.lcp_setup(L.config_for(inst, self_quadrature=0), inst.centers, inst.axes)
+    try:
+        phi = np.random.default_rng(4).standard_normal(mob.x.shape[0] * 3)
+        out = torch.empty(phi.size, dtype=torch.float64, device=DEV)
+        L.lcp_stokes_apply_dev(ctx, torch.tensor(phi, device=DEV), out, precision)
+        assert rel(out.cpu().numpy(), (mob.K + mob.P) @ phi) <= tol
+        if precision == L.LCP_FP64:
+            pairs, normals, gaps = detect_contacts(inst.centers, inst.contact_radius, inst.delta)
+            D = contact_matrix(inst.n_bodies, pairs, normals)
+            A, b = lcp_data(D, mob.matrix(), mob.apply(np.zeros(6 * inst.n_bodies), axes=inst.axes), gaps,
+                            inst.dt)
+            x, st, _ = L.lcp_solve(ctx, L.LCP_MONO_PQN, inst.tol)
+            g = A @ x + b
+            eps_op, _ = kkt_bound(inst.tol, x, g, L.lcp_apply_A(ctx, x) + L.lcp_get_b(ctx), b, st["hi_mvps"])
+            assert kkt_abs(x, g) <= inst.tol + eps_op
     finally:
         L.lcp_destroy(ctx)

@@ -20,7 +20,7 @@ from oracle.contacts import contact_matrix, detect_contacts  # noqa: E402
 from oracle.lcp import lcp_data  # noqa: E402
 from workloads import make_instance  # noqa: E402
 
-from .cases import dense_case, kkt_bound  # noqa: E402
+from .cases import SELF_QUADRATURE, dense_case, kkt_bound  # noqa: E402
 
 
 def rel(a, b):
@@ -81,7 +81,7 @@ def test_warm_started_step_matches_oracle():
         U = (case["U_nc"] + case["Mob"] @ (case["D"] @ x)).reshape(-1, 6)
         c_ref = inst.centers + inst.dt * U[:, :3]
         a_ref = np.array([_rotate(inst.axes[i], U[i, 3:], inst.dt) for i in range(inst.n_bodies)])
-        mob = DenseMobility(c_ref, inst.n_theta, inst.n_phi, a=inst.radius)
+        mob = DenseMobility(c_ref, inst.n_theta, inst.n_phi, a=inst.radius, self_quadrature=SELF_QUADRATURE)
         pairs, normals, gaps = detect_contacts(c_ref, inst.contact_radius, inst.delta)
         D = contact_matrix(inst.n_bodies, pairs, normals)
         u_nc = mob.apply(np.zeros(6 * inst.n_bodies), axes=a_ref)
@@ -151,7 +151,7 @@ def test_lcp_warm_started_trajectory_matches_oracle(flags):
             x, st, _ = L.lcp_solve(warm, L.LCP_BI_PQN, inst.tol)
             _, sc, _ = L.lcp_solve(cold, L.LCP_BI_PQN, inst.tol)
             assert st["warm_x0"] == 1 and sc["warm_x0"] == 0
-            mob = DenseMobility(c, inst.n_theta, inst.n_phi, a=inst.radius)
+            mob = DenseMobility(c, inst.n_theta, inst.n_phi, a=inst.radius, self_quadrature=SELF_QUADRATURE)
             pairs, normals, gaps = detect_contacts(c, inst.contact_radius, inst.delta)
             assert np.array_equal(pairs, L.lcp_get_contacts(warm)[0])
             D = contact_matrix(inst.n_bodies, pairs, normals)

@@ -28,7 +28,7 @@ def rel(a, b):
 @pytest.mark.parametrize("precision", [L.LCP_FP64, L.LCP_MIXED])
 def test_noalloc_matches_context_apply_twice(name, precision):
     inst = make_instance(name, 0)
-    ctx = L.lcp_setup(L.config_for(inst, precision), inst.centers, None)
+    ctx = L.lcp_setup(L.config_for(inst, precision, self_quadrature=0), inst.centers, None)
     try:
         M, N, _ = L.lcp_sizes(ctx)
         centers = torch.tensor(inst.centers, dtype=torch.float64, device="cuda")
@@ -65,7 +65,7 @@ def test_noalloc_at_its_maximum_sizes_on_a_caller_stream(precision):
     at the documented limits (the FP64 kernel needs a raised shared-memory
     limit there), launched on a caller-owned stream."""
     centers_h = _lattice((4, 4, 2))
-    cfg = L.lcp_default_config(n_theta=16, n_phi=32, precision=precision)
+    cfg = L.lcp_default_config(n_theta=16, n_phi=32, precision=precision, self_quadrature=0)
     ctx = L.lcp_setup(cfg, centers_h)
     try:
         M, N, _ = L.lcp_sizes(ctx)
