@@ -78,3 +78,28 @@ def test_struct_layouts_match_the_header(tmp_path):
         for field, _ in py._fields_:
             assert c_layout[(cname, field)] == getattr(py, field).offset, (cname, field)
     # equal sizes and offsets: no header field is missing from the mirror, at the end or between
+
+
+def test_footprint_estimate_counts_the_optional_buffers():
+    """Host-only: the admission estimate grows by exactly the buffers each option adds (the
+    self-interaction correction in FP32 and FP64, the carried forces and their pairs, the
+    kept solve pairs for projected starts)."""
+    import paper_2604_10089_gb300 as L
+    M, nt, nph = 20, 7, 14
+    ns, pairs = nt * nph, M * (M - 1) // 2
+    base = dict(n_theta=nt, n_phi=nph, self_quadrature=0, warm_start=0, recycle=0, precondition=1)
+
+    def est(**kw):
+        cfg = L.lcp_default_config(**{**base, **kw})
+        return L.lcp_footprint_estimate(cfg, M, 6 * M)
+
+    b0 = est()
+
+    def grows_by(added, **kw):   # the estimate keeps a 1/16 margin on top of the buffers
+        return abs((est(**kw) - b0) - (added + added // 16)) <= 2
+
+    assert grows_by(12 * 9 * ns * ns, self_quadrature=1)        # FP32 + FP64 copies of C
+    assert grows_by(24 * pairs, warm_start=L.LCP_WARM_FORCES)    # x, start, i, j per body pair
+    assert est(warm_start=L.LCP_WARM_SLIP) == b0                 # the slip start needs no extra buffer
+    L3 = 3 * M * ns
+    assert grows_by(8 * (L3 * 10 + 12), recycle=4)                # 2 x 4 pairs + 2 vectors + coefficients
